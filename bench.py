@@ -1,0 +1,456 @@
+#!/usr/bin/env python3
+"""Benchmark: exact selectivity computation and selection push-down on the
+300M-row, 8-column synthetic fact table (the table of configs 2 and 4).
+
+One step is one optimiser pass of the method over that table (Ch3; Algorithm 1
+Execute for one relation, with every probe of the pass):
+  a1  compile the probe predicates (OR of 3 ANDs mixing BETWEEN, 5-value IN and
+      prefix LIKE; selectivities 1e-4 .. 0.5);
+  a5  their exact counts in one batched scan (persistent kernel, CUDA graph,
+      autotuned shape) -- a2 is the same kernel with one program;
+  a3  maxSize = floor(n * 0.05): probes above it are not pushed down;
+  a4  push-down (fused count + stable compaction) of 4 projected columns for
+      every probe at or under maxSize.
+value = algorithmic bytes of all scans of a step / device time of the step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import datagen as dg  # noqa: E402
+
+METRIC = "exact-count scan GB/s (% HBM peak), ms/estimate; surrogate p95 q-error"
+MAX_SELECTIVITY = 0.05          # PUSH_DOWN_MAX_SELECTIVITY of Algorithm 1 (ratio form)
+WIDTH = {"i32": 4, "i64": 8, "f32": 4, "date": 4, "dict": 4}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for k, v in zip(names, r[3:]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------
+# the workload
+# ----------------------------------------------------------------------------
+
+def probe_trees(seed=0):
+    return [dg.config2_predicate(s, seed=seed) for s in dg.CONFIG2_TARGETS]
+
+
+def algorithmic_bytes(types, n, trees, counts, accepted, proj):
+    """Bytes a step must move at least: each predicate column of the batched
+    scan once, and for each push-down its predicate columns, the projected
+    values of the selected rows that are not predicate columns, and the
+    written rows (projected values + int64 row id)."""
+    union = sorted({c for t in trees for c in dg.tree_columns(t)})
+    batch = sum(WIDTH[types[c]] for c in union) * n
+    pds = []
+    for i in accepted:
+        pc = set(dg.tree_columns(trees[i]))
+        rd = sum(WIDTH[types[c]] for c in pc) * n + counts[i] * sum(WIDTH[types[c]] for c in proj if c not in pc)
+        wr = counts[i] * (sum(WIDTH[types[c]] for c in proj) + 8)
+        pds.append(rd + wr)
+    return batch, pds
+
+
+class Workload:
+    def __init__(self, n_rows: int, device, seed_offset: int = 0):
+        self.table = dg.gen_table("cfg2" if seed_offset == 0 else f"cfg2_r{seed_offset}", dg.config2_specs(),
+                                  n_rows, device, cfg_label="cfg2" if seed_offset == 0 else None)
+        self.n = n_rows
+        self.types = [c.type for c in self.table.columns]
+        self.trees = probe_trees()
+        self.proj = [self.table.index(c) for c in dg.CONFIG2_PROJECTION]
+        self.max_rows = int(math.floor(n_rows * MAX_SELECTIVITY))
+
+
+class OurStep:
+    def __init__(self, w: Workload, sel):
+        self.w, self.sel = w, sel
+        self.ctx = sel.Context()
+        self.T = sel.Table(w.table.columns)
+        dev = w.table.columns[0].data.device
+        P = len(w.trees)
+        self.counts_dev = torch.zeros(P, dtype=torch.int64, device=dev)
+        self.pd_counts = torch.zeros(P, dtype=torch.int64, device=dev)
+        cap = max(1, w.max_rows)
+        self.out_cols = [torch.empty(cap, dtype=w.table.columns[c].data.dtype, device=dev) for c in w.proj]
+        self.out_ids = torch.empty(cap, dtype=torch.int64, device=dev)
+        self.events = []            # (kind, start, end) of the timed steps
+        self.host_out = None
+
+    def run(self, record=False, e2e=False):
+        w, sel, ctx = self.w, self.sel, self.ctx
+        preds = [sel.Predicate(self.T, t) for t in w.trees]                     # a1
+        ev = lambda: torch.cuda.Event(enable_timing=True) if record else None
+        e0, e1 = ev(), ev()
+        if record:
+            e0.record()
+        ctx.count_batch_async(preds, [self.T] * len(preds), self.counts_dev)    # a5 (a2)
+        if record:
+            e1.record()
+            self.events.append(("count", e0, e1))
+        counts = self.counts_dev.tolist()                                       # exact counts on the host
+        accepted = [i for i, c in enumerate(counts) if c <= w.max_rows]         # a3
+        d2h = 8 * len(counts)
+        for i in accepted:                                                      # a4
+            a, b = ev(), ev()
+            if record:
+                a.record()
+            ctx.pushdown_async(preds[i], self.T, w.proj, w.max_rows, self.out_cols, self.out_ids,
+                               self.pd_counts[i:i + 1])
+            if record:
+                b.record()
+                self.events.append(("pushdown", a, b))
+            if e2e:
+                for o, h in zip(self.out_cols + [self.out_ids], self.host_out):
+                    h[:counts[i]].copy_(o[:counts[i]], non_blocking=True)
+                d2h += counts[i] * (sum(o.element_size() for o in self.out_cols) + 8)
+        ctx.synchronize()
+        return counts, accepted, d2h
+
+
+def time_separate_vs_batched(step: OurStep, reps=5):
+    """The same probes as one batched launch vs one launch per probe."""
+    sel, w = step.sel, step.w
+    preds = [sel.Predicate(step.T, t) for t in w.trees]
+    outs = torch.zeros(len(preds), dtype=torch.int64, device=step.counts_dev.device)
+    res = {}
+    for mode in ("batched", "separate"):
+        for r in range(reps + 1):
+            if r == 1:
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t0.record()
+            if mode == "batched":
+                step.ctx.count_batch_async(preds, [step.T] * len(preds), outs)
+            else:
+                for i, p in enumerate(preds):
+                    step.ctx.count_async(p, step.T, outs[i:i + 1])
+        t1 = torch.cuda.Event(enable_timing=True)
+        t1.record()
+        torch.cuda.synchronize()
+        res[mode + "_ms"] = t0.elapsed_time(t1) / reps
+    res["speedup"] = res["separate_ms"] / res["batched_ms"]
+    return res
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and --impl reference)
+# ----------------------------------------------------------------------------
+
+def oracle_step(ot, trees, max_rows_ratio, threads):
+    import oracle
+    counts = [oracle.count(ot, t, threads=threads) for t in trees]
+    mr = int(math.floor(ot.n_rows * max_rows_ratio))
+    accepted = [i for i, c in enumerate(counts) if c <= mr]
+    for i in accepted:
+        oracle.select(ot, trees[i], threads=threads)
+    return counts, accepted
+
+
+def oracle_sample(table, trees, target_s: float, threads: int):
+    """A prefix of the table sized so that one oracle step takes about target_s."""
+    import oracle
+    n = table.n_rows
+    m0 = min(n, 1_000_000)
+    ot = oracle.OTable([c.data[:m0].cpu().numpy() for c in table.columns], [c.type for c in table.columns],
+                       [c.dictionary for c in table.columns])
+    t0 = time.perf_counter()
+    oracle_step(ot, trees, MAX_SELECTIVITY, threads)
+    dt = time.perf_counter() - t0
+    m = int(min(n, max(m0, m0 * target_s / max(dt, 1e-6))))
+    return oracle.OTable([c.data[:m].cpu().numpy() for c in table.columns], [c.type for c in table.columns],
+                         [c.dictionary for c in table.columns])
+
+
+def cpu_rate(ot, types, trees, proj, threads, reps=1):
+    best = 1e30
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        counts, accepted = oracle_step(ot, trees, MAX_SELECTIVITY, threads)
+        best = min(best, time.perf_counter() - t0)
+    b, pds = algorithmic_bytes(types, ot.n_rows, trees, counts, accepted, proj)
+    return (b + sum(pds)) / best / 1e9, best
+
+
+# ----------------------------------------------------------------------------
+# traffic from the committed ncu summary (null if the kernel changed since)
+# ----------------------------------------------------------------------------
+
+def kernel_source_hash(name):
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("scan.cuh", "program.h", "kernels.h", name):
+        with open(os.path.join(ROOT, "paper_1806_08384_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, source: str, rows: int):
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash(source):
+        return None
+    return e["dram_bytes_per_row"] * rows
+
+
+# ----------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rows", type=int, default=300_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.steps <= 2, "at least 3 warm-up steps"
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    threads = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, threads)
+        return
+
+    import paper_1806_08384_b300 as sel
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = Workload(args.rows, dev, seed_offset=rank)
+    step = OurStep(w, sel)
+    for _ in range(args.warmup):
+        step.run()
+    # per-step bytes are fixed (same probes, same data)
+    counts, accepted, _ = step.run()
+    b_batch, b_pds = algorithmic_bytes(w.types, w.n, w.trees, counts, accepted, w.proj)
+    step_bytes = b_batch + sum(b_pds)
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = step.ctx.launches
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step.run(record=True)
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = step.ctx.launches - launches0
+    elapsed_ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+        dist.barrier()
+    total_bytes = step_bytes * args.steps * world
+    value = total_bytes / (elapsed_ms / 1e3) / 1e9
+
+    # per-kernel durations inside the timed region
+    dur = {"count": [], "pushdown": []}
+    for kind, a, b in step.events:
+        dur[kind].append(a.elapsed_time(b))
+    count_ms = statistics.mean(dur["count"])
+    pd_ms = statistics.mean(dur["pushdown"]) if dur["pushdown"] else 0.0
+    peak, peak_kind = load_peaks()
+    kernels = {
+        "count": {"name": "scan_count_kernel", "ms": count_ms, "bytes": b_batch, "launches": len(dur["count"]),
+                  "total_ms": sum(dur["count"]), "source": "count.cu"},
+        "pushdown": {"name": "pushdown_kernel", "ms": pd_ms, "bytes": (sum(b_pds) / len(b_pds)) if b_pds else 0,
+                     "launches": len(dur["pushdown"]), "total_ms": sum(dur["pushdown"]), "source": "pushdown.cu"},
+    }
+
+    def roof(k):
+        kk = kernels[k]
+        ach = kk["bytes"] / (kk["ms"] / 1e3) / 1e9 if kk["ms"] > 0 else 0.0
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": traffic_for(kk["name"], kk["source"], w.n), "kernel": kk["name"],
+                "algorithmic_bytes_per_launch": int(kk["bytes"]), "avg_launch_ms": round(kk["ms"], 4),
+                "launches_timed": kk["launches"]}
+    dominant = max(kernels, key=lambda k: kernels[k]["total_ms"])
+    other = "count" if dominant == "pushdown" else "pushdown"
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64/f32 compares, u64 counts",
+        "data": "synthetic, seeded (datagen; shapes of the paper's fact tables), resident in HBM",
+        "config": {"workload": f"config2 fact table: {w.n} rows x 8 cols (2 i32 U, i64 Zipf1.1, f32 U, f32 LogN, "
+                               f"date, dict-25, dict-10k), {len(w.trees)} probes OR-of-3-ANDs "
+                               f"s={list(dg.CONFIG2_TARGETS)}, push-down of {list(dg.CONFIG2_PROJECTION)} "
+                               f"when count <= floor(n*{MAX_SELECTIVITY})",
+                   "n_rows": w.n, "table_bytes": w.table.nbytes(), "probes": len(w.trees),
+                   "pushed_down": len(accepted), "max_rows": w.max_rows,
+                   "l2": "inputs larger than L2 (table 10.8 GB vs 126 MB L2), no flush needed",
+                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "ms_per_estimate": round(elapsed_ms / args.steps / len(w.trees), 4),
+        "roofline": roof(dominant),
+        "roofline_other": roof(other),
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0:
+        out["batched_vs_separate"] = time_separate_vs_batched(step)
+    if rank == 0 and not args.no_e2e:
+        out["e2e"] = run_e2e(step, args, step_bytes)
+    if rank == 0 and not args.no_cpu:
+        ot = oracle_sample(w.table, w.trees, args.cpu_seconds, threads)
+        gbs, secs = cpu_rate(ot, w.types, w.trees, w.proj, threads)
+        out["cpu_baseline"] = {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                               "sample": f"first {ot.n_rows} rows of the same table, the same step "
+                                         f"(5 counts + push-down row ids), {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(step: OurStep, args, step_bytes):
+    """The same step through the C ABI with the table in pinned HOST memory:
+    every step copies the 8 columns host->device and the results back."""
+    w = step.w
+    host_cols = [torch.empty_like(c.data, device="cpu").pin_memory() for c in w.table.columns]
+    for h, c in zip(host_cols, w.table.columns):
+        h.copy_(c.data)
+    step.host_out = [torch.empty(o.numel(), dtype=o.dtype).pin_memory() for o in step.out_cols + [step.out_ids]]
+    h2d = sum(h.numel() * h.element_size() for h in host_cols)
+    k = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    d2h = 0
+    for _ in range(k):
+        for h, c in zip(host_cols, w.table.columns):
+            c.data.copy_(h, non_blocking=True)
+        _, _, d2h = step.run(e2e=True)
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / k
+    return {"value": round(step_bytes / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": k}
+
+
+def run_reference(args, threads):
+    """The oracle as it stands, on the host cores, on a bounded sample per step."""
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    n = args.rows
+    w_tab = dg.gen_table("cfg2", dg.config2_specs(), n if dev == "cuda" else min(n, 20_000_000), dev)
+    trees = probe_trees()
+    types = [c.type for c in w_tab.columns]
+    proj = [w_tab.index(c) for c in dg.CONFIG2_PROJECTION]
+    per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    ot = oracle_sample(w_tab, trees, per_step, threads)
+    del w_tab
+    for _ in range(args.warmup):
+        oracle_step(ot, trees, MAX_SELECTIVITY, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        counts, accepted = oracle_step(ot, trees, MAX_SELECTIVITY, threads)
+    dt = (time.perf_counter() - t0) / args.steps
+    b, pds = algorithmic_bytes(types, ot.n_rows, trees, counts, accepted, proj)
+    gbs = (b + sum(pds)) / dt / 1e9
+    sample = f"first {ot.n_rows} of {n} rows of the config 2 table per step, 5 counts + push-down row ids"
+    out = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64/f32 compares, u64 counts",
+           "data": "synthetic, seeded (datagen)",
+           "config": {"workload": f"config2 fact table (sampled prefix of {n} rows)", "n_rows": ot.n_rows},
+           "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

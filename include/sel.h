@@ -1,0 +1,233 @@
+/*
+ * sel.h -- exact selectivity computation and selection push-down on one GPU.
+ *
+ * The method (Ch3 "A Novel Query Optimization Paradigm"): instead of
+ * estimating the cardinality of a pushed-down selection from statistics, the
+ * optimiser runs SELECT COUNT(*) FROM R WHERE <pushed-down predicates> during
+ * optimisation (§3.1 "Selectivity Computation"), compares the exact count with
+ * maxSize = R.size * PUSH_DOWN_MAX_SELECTIVITY and, if the count is not above
+ * it, materialises sigma_P(pi_cols(R)) right away while R's scan is still on
+ * the GPU (§3.3 "Materialization"; Algorithm 1, functions Execute and
+ * EvaluateAndPushDown).
+ *
+ * Conventions for every entry point:
+ *  - All functions return sel_status; no exception ever crosses this ABI.
+ *    sel_last_error() gives a human-readable reason for the last non-OK
+ *    status on the calling host thread.
+ *  - Column data are BORROWED device pointers (e.g. from torch tensors); the
+ *    library never frees them.  Columns are plain arrays of n_rows elements:
+ *    int32 (SEL_I32, SEL_DATE, SEL_DICT) / int64 (SEL_I64) / binary32
+ *    (SEL_F32).  A base address that is 16-byte aligned takes the fast bulk
+ *    (TMA) path; any element-aligned address is accepted.
+ *  - sel_ctx, sel_pred and sel_batch_plan are library-owned handles, released
+ *    with sel_ctx_destroy / sel_pred_free / sel_batch_plan_free.
+ *  - A context binds one CUDA stream; all device work of a call is enqueued
+ *    on it.  Synchronous calls (sel_count, sel_pushdown, sel_count_batch,
+ *    sel_batch_plan_run with host output) return after the result is on the
+ *    host.  Use one context per host thread.
+ *  - Row counts and row ids are 64-bit everywhere.
+ */
+#ifndef SEL_H
+#define SEL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sel_status {
+    SEL_OK = 0,
+    SEL_ERR_INVALID_ARG = 1,   /* null pointer, bad size, malformed tree, bad column index   */
+    SEL_ERR_TYPE = 2,          /* constant or operator does not fit the column's type        */
+    SEL_ERR_UNSUPPORTED = 3,   /* a documented limit is exceeded (tree depth, list sizes ...) */
+    SEL_ERR_OOM = 4,           /* a device or pinned-host allocation failed                  */
+    SEL_ERR_CUDA = 5,          /* a CUDA runtime call failed (no device, launch error ...)    */
+    SEL_ERR_TOO_LARGE = 6,     /* push-down: count > max_rows (Algorithm 1's thrown exception) */
+    SEL_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up; results are invalid      */
+} sel_status;
+
+typedef enum sel_type {
+    SEL_I32 = 0,   /* int32                                                          */
+    SEL_I64 = 1,   /* int64                                                          */
+    SEL_F32 = 2,   /* IEEE-754 binary32; compared in binary32 without promotion       */
+    SEL_DATE = 3,  /* int32 days since 1970-01-01, compared as an integer             */
+    SEL_DICT = 4   /* int32 code into a dictionary of strings (code -> string)         */
+} sel_type;
+
+/* One column.  dict/dict_size describe a SEL_DICT column's dictionary (host
+ * strings, NUL-terminated, entry i is the string of code i); they are only
+ * read by sel_compile_predicate (to resolve LIKE) and may be NULL when no
+ * LIKE refers to the column.  A byte-wise sorted dictionary turns a prefix
+ * into one code range; an unsorted one into a code bitmap. */
+typedef struct sel_column {
+    int32_t type;                 /* sel_type                                   */
+    int32_t dict_size;            /* SEL_DICT only                              */
+    const void* data;             /* device pointer to n_rows elements          */
+    const char* const* dict;      /* SEL_DICT only, host, may be NULL           */
+} sel_column;
+
+typedef struct sel_table {
+    const sel_column* cols;       /* host array of n_cols descriptors           */
+    int32_t n_cols;
+    int64_t n_rows;               /* >= 0                                       */
+} sel_table;
+
+/* Predicate trees are passed as a flat POSTFIX array of nodes (children
+ * before their parent), the WHERE clause of the COUNT query of §3.1.
+ * Leaves: comparison with a constant, BETWEEN (inclusive both ends), IN-list
+ * and prefix LIKE ('prefix%': byte-wise, case-sensitive) on dictionary
+ * columns.  Inner nodes: n-ary AND / OR (n_children >= 1 operands popped),
+ * NOT.  Logic is two-valued (columns hold no NULLs). */
+typedef enum sel_node_kind {
+    SEL_N_CMP = 1,      /* col op i_lo (integer-like) / col op f_lo (SEL_F32)          */
+    SEL_N_BETWEEN = 2,  /* i_lo <= col <= i_hi  /  f_lo <= col <= f_hi                 */
+    SEL_N_IN = 3,       /* col in values[0 .. n_values)  (empty list: FALSE)           */
+    SEL_N_LIKE = 4,     /* dictionary string of col starts with prefix                 */
+    SEL_N_AND = 5,
+    SEL_N_OR = 6,
+    SEL_N_NOT = 7,
+    SEL_N_TRUE = 8,
+    SEL_N_FALSE = 9
+} sel_node_kind;
+
+typedef enum sel_op { SEL_EQ = 0, SEL_NE = 1, SEL_LT = 2, SEL_LE = 3, SEL_GT = 4, SEL_GE = 5 } sel_op;
+
+typedef struct sel_node {
+    int32_t kind;          /* sel_node_kind                                          */
+    int32_t col;           /* leaves: column index in the table                      */
+    int32_t op;            /* SEL_N_CMP: sel_op                                       */
+    int32_t n_children;    /* SEL_N_AND / SEL_N_OR: operands popped (>= 1)            */
+    int64_t i_lo, i_hi;    /* integer constants (int32/int64/date/dict columns)      */
+    float f_lo, f_hi;      /* binary32 constants (SEL_F32 columns)                    */
+    int32_t n_values;      /* SEL_N_IN: number of values (<= SEL_MAX_IN_VALUES)       */
+    int32_t reserved;
+    const void* values;    /* SEL_N_IN: host int64_t[] (integer-like) / float[] (F32) */
+    const char* prefix;    /* SEL_N_LIKE: NUL-terminated literal prefix (no wildcard)  */
+} sel_node;
+
+#define SEL_MAX_NODES 512         /* postfix nodes per predicate                       */
+#define SEL_MAX_LEAVES 64         /* leaves per predicate                              */
+#define SEL_MAX_IN_VALUES 4096    /* values per IN list                                */
+#define SEL_MAX_SLOTS 16          /* distinct columns referenced by one predicate      */
+
+typedef struct sel_ctx sel_ctx;
+typedef struct sel_pred sel_pred;
+typedef struct sel_batch_plan sel_batch_plan;
+
+/* Last error message of the calling host thread ("" if none). */
+const char* sel_last_error(void);
+const char* sel_status_str(sel_status s);
+
+/* Create a context bound to a CUDA stream (a cudaStream_t; NULL = the legacy
+ * default stream) on the current device.  The context owns small device
+ * scratch (result counters, error flag, tile status of the push-down scan,
+ * grown on demand) and pinned host buffers for results. */
+sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out);
+void sel_ctx_destroy(sel_ctx* ctx);
+
+/* a1 -- compile a postfix tree against a table schema (column types and
+ * dictionaries; data pointers and n_rows are not read).  Host-only work: NOT
+ * is pushed to the leaves (negation normal form), comparisons become
+ * inclusive ranges of the column's type, LIKE becomes a code range or bitmap,
+ * operands are ordered to bound the evaluation stack.  The program is
+ * uploaded to the device on first use.  Errors: SEL_ERR_INVALID_ARG
+ * (malformed postfix, column out of range), SEL_ERR_TYPE (LIKE on a non-dict
+ * column, dict needed but absent), SEL_ERR_UNSUPPORTED (limits above). */
+sel_status sel_compile_predicate(const sel_table* schema, const sel_node* postfix, int32_t n_nodes,
+                                 sel_pred** out);
+void sel_pred_free(sel_pred* pred);
+
+/* Text dump of the compiled program (for tests and debugging); writes at most
+ * cap bytes including the terminating NUL and returns SEL_OK. */
+sel_status sel_pred_describe(const sel_pred* pred, char* buf, int64_t cap);
+
+/* a2 -- exact count = |{ i in [0, n_rows) : P(row i) }| (§3.1 COUNT query).
+ * The table must have the column types the predicate was compiled for.
+ * Synchronous: *out_count (host) holds the count on SEL_OK. */
+sel_status sel_count(sel_ctx* ctx, const sel_pred* pred, const sel_table* table, uint64_t* out_count);
+
+/* Same scan, enqueued only: the count is written to dev_out_count (device,
+ * 8 bytes, caller-owned) when the stream reaches it.  A timed-out device wait
+ * is reported by the next synchronous call on this context. */
+sel_status sel_count_async(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                           uint64_t* dev_out_count);
+
+/* a3 + a4 -- selection push-down (Algorithm 1, Execute with isSPD = true):
+ * one fused pass computes the exact count and writes the rows of
+ * sigma_P(R), projected on proj_cols[0 .. n_proj), in ascending row order
+ * into caller-allocated device buffers dev_out_cols[j] (capacity max_rows
+ * elements of column proj_cols[j]'s type), plus their int64 row ids into
+ * dev_out_rowids when it is not NULL.  *out_count (host) always receives the
+ * exact count.  If count > max_rows the call returns SEL_ERR_TOO_LARGE (the
+ * paper's thrown exception: the caller reverts the push-down) and the output
+ * buffers hold unspecified data; nothing is written beyond max_rows
+ * elements.  Synchronous. */
+sel_status sel_pushdown(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                        const int32_t* proj_cols, int32_t n_proj, void* const* dev_out_cols,
+                        int64_t* dev_out_rowids, uint64_t max_rows, uint64_t* out_count);
+
+/* Same push-down, enqueued only: the exact count is written to dev_out_count
+ * (device, 8 bytes) and nothing waits for it; the caller compares it with
+ * max_rows (rows past max_rows are never written).  A timed-out look-back
+ * wait is reported by sel_ctx_synchronize. */
+sel_status sel_pushdown_async(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                              const int32_t* proj_cols, int32_t n_proj, void* const* dev_out_cols,
+                              int64_t* dev_out_rowids, uint64_t max_rows, uint64_t* dev_out_count);
+
+/* a5 -- batched probes: counts of n predicates, preds[i] evaluated over
+ * tables[i], in one persistent launch that reads every referenced column of
+ * each distinct table once for all predicates on that table (tables are the
+ * same when their descriptors point to the same column data and n_rows).
+ * The launch shape (tile rows, pipeline stages, CTAs per SM) is picked by
+ * the library's autotuner on first use of the plan and the launch is
+ * captured in a CUDA graph that later runs replay.  out_counts: host, n. */
+sel_status sel_count_batch(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
+                           int32_t n, uint64_t* out_counts);
+
+/* Same as sel_count_batch, enqueued only: counts go to dev_out_counts
+ * (device, n u64).  Plans are cached per context by the compiled programs'
+ * content and the tables' column pointers, so recompiling the same probes
+ * reuses the tuned shape and the captured graph. */
+sel_status sel_count_batch_async(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
+                                 int32_t n, uint64_t* dev_out_counts);
+
+/* Waits for all work enqueued on the context's stream and reports (then
+ * clears) a device wait that timed out in an enqueue-only call since the
+ * last check: SEL_ERR_TIMEOUT. */
+sel_status sel_ctx_synchronize(sel_ctx* ctx);
+
+/* The plan behind sel_count_batch, for callers that run the same probe set
+ * many times.  The predicates and table descriptors must outlive the plan.
+ * autotune: 1 = time the candidate launch shapes now and keep the fastest,
+ * 0 = use the default shape. */
+sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
+                                 int32_t n, int32_t autotune, sel_batch_plan** out);
+/* Runs the plan: counts to dev_out_counts (device, n u64, enqueue only) when
+ * it is not NULL, else to host_out_counts (synchronous). */
+sel_status sel_batch_plan_run(sel_batch_plan* plan, uint64_t* dev_out_counts, uint64_t* host_out_counts);
+/* Launch shape chosen by the plan and its measured time per launch (ms, 0 if
+ * not autotuned). */
+sel_status sel_batch_plan_info(const sel_batch_plan* plan, int32_t* tile_rows, int32_t* stages,
+                               int32_t* ctas_per_sm, float* ms);
+void sel_batch_plan_free(sel_batch_plan* plan);
+
+/* Launch configuration override for sel_count / sel_count_async / sel_pushdown
+ * (0 = keep the library default).  tile_rows must be a multiple of 256. */
+sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm);
+
+/* Number of kernels this context has launched so far (all entry points). */
+uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
+
+/* Test hook for the bounded waits of the push-down look-back: tile skip_tile
+ * (-1: none) never publishes its prefix, and a waiting tile gives up after
+ * wait_ns nanoseconds (0: the default of 2 s), so that later sel_pushdown
+ * calls on this context return SEL_ERR_TIMEOUT instead of waiting forever.
+ * The context stays usable; set skip_tile back to -1 to disarm. */
+sel_status sel_ctx_debug_pushdown_fault(sel_ctx* ctx, int64_t skip_tile, uint64_t wait_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEL_H */

@@ -1,0 +1,390 @@
+"""Python binding of libsel.so (include/sel.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+converts predicate trees and torch-tensor tables into the C structs of the
+ABI and calls it.  There is no fallback: if libsel.so is missing or fails to
+load, importing this package raises.
+
+Predicate trees use the neutral nested-tuple form (see ``tree_to_postfix``):
+("and", [...]), ("or", [...]), ("not", x), ("cmp", col, op, v),
+("between", col, lo, hi), ("in", col, [v...]), ("like", col, "prefix"),
+("true",), ("false",).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsel.so")
+
+SEL_OK, SEL_ERR_INVALID_ARG, SEL_ERR_TYPE, SEL_ERR_UNSUPPORTED, SEL_ERR_OOM, SEL_ERR_CUDA, \
+    SEL_ERR_TOO_LARGE, SEL_ERR_TIMEOUT = range(8)
+STATUS_NAMES = ["SEL_OK", "SEL_ERR_INVALID_ARG", "SEL_ERR_TYPE", "SEL_ERR_UNSUPPORTED", "SEL_ERR_OOM",
+                "SEL_ERR_CUDA", "SEL_ERR_TOO_LARGE", "SEL_ERR_TIMEOUT"]
+TYPE_CODES = {"i32": 0, "i64": 1, "f32": 2, "date": 3, "dict": 4}
+TORCH_TYPES = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32, "date": torch.int32,
+               "dict": torch.int32}
+N_CMP, N_BETWEEN, N_IN, N_LIKE, N_AND, N_OR, N_NOT, N_TRUE, N_FALSE = range(1, 10)
+OPS = {"=": 0, "<>": 1, "<": 2, "<=": 3, ">": 4, ">=": 5}
+
+
+class sel_column(C.Structure):
+    _fields_ = [("type", C.c_int32), ("dict_size", C.c_int32), ("data", C.c_void_p),
+                ("dict", C.POINTER(C.c_char_p))]
+
+
+class sel_table(C.Structure):
+    _fields_ = [("cols", C.POINTER(sel_column)), ("n_cols", C.c_int32), ("n_rows", C.c_int64)]
+
+
+class sel_node(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("col", C.c_int32), ("op", C.c_int32), ("n_children", C.c_int32),
+                ("i_lo", C.c_int64), ("i_hi", C.c_int64), ("f_lo", C.c_float), ("f_hi", C.c_float),
+                ("n_values", C.c_int32), ("reserved", C.c_int32), ("values", C.c_void_p),
+                ("prefix", C.c_char_p)]
+
+
+class SelError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built (python {os.path.join(_HERE, 'build.py')})")
+    lib = C.CDLL(LIB_PATH)
+    P, V = C.POINTER, C.c_void_p
+    sigs = {
+        "sel_last_error": (C.c_char_p, []),
+        "sel_status_str": (C.c_char_p, [C.c_int]),
+        "sel_ctx_create": (C.c_int, [V, P(V)]),
+        "sel_ctx_destroy": (None, [V]),
+        "sel_compile_predicate": (C.c_int, [P(sel_table), P(sel_node), C.c_int32, P(V)]),
+        "sel_pred_free": (None, [V]),
+        "sel_pred_describe": (C.c_int, [V, C.c_char_p, C.c_int64]),
+        "sel_count": (C.c_int, [V, V, P(sel_table), P(C.c_uint64)]),
+        "sel_count_async": (C.c_int, [V, V, P(sel_table), V]),
+        "sel_pushdown": (C.c_int, [V, V, P(sel_table), P(C.c_int32), C.c_int32, P(V), V, C.c_uint64,
+                                   P(C.c_uint64)]),
+        "sel_count_batch": (C.c_int, [V, P(V), P(P(sel_table)), C.c_int32, P(C.c_uint64)]),
+        "sel_count_batch_async": (C.c_int, [V, P(V), P(P(sel_table)), C.c_int32, V]),
+        "sel_pushdown_async": (C.c_int, [V, V, P(sel_table), P(C.c_int32), C.c_int32, P(V), V, C.c_uint64, V]),
+        "sel_ctx_synchronize": (C.c_int, [V]),
+        "sel_batch_plan_create": (C.c_int, [V, P(V), P(P(sel_table)), C.c_int32, C.c_int32, P(V)]),
+        "sel_batch_plan_run": (C.c_int, [V, V, P(C.c_uint64)]),
+        "sel_batch_plan_info": (C.c_int, [V, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_float)]),
+        "sel_batch_plan_free": (None, [V]),
+        "sel_ctx_set_scan_shape": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32]),
+        "sel_ctx_launch_count": (C.c_uint64, [V]),
+        "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int, where: str):
+    if status != SEL_OK:
+        raise SelError(status, where, lib.sel_last_error().decode(errors="replace"))
+
+
+# ----------------------------------------------------------------------------
+# tables
+# ----------------------------------------------------------------------------
+
+class Table:
+    """A sel_table over torch tensors (device columns) plus host dictionaries.
+
+    ``columns``: sequence of objects with ``.data`` (1-D torch tensor),
+    ``.type`` (one of i32 i64 f32 date dict) and ``.dictionary`` (list of
+    bytes or None) -- e.g. a ``datagen.Table``'s columns."""
+
+    def __init__(self, columns, n_rows: Optional[int] = None):
+        self.columns = list(columns)
+        self.types = [c.type for c in self.columns]
+        self._keep = []
+        arr = (sel_column * max(1, len(self.columns)))()
+        rows = None
+        for i, c in enumerate(self.columns):
+            t = c.data
+            if t.dtype != TORCH_TYPES[c.type] or t.dim() != 1 or not t.is_contiguous():
+                raise TypeError(f"column {i}: need a contiguous 1-D {TORCH_TYPES[c.type]} tensor")
+            rows = t.numel() if rows is None else rows
+            if t.numel() != rows:
+                raise ValueError("columns differ in length")
+            arr[i].type = TYPE_CODES[c.type]
+            arr[i].data = t.data_ptr() if t.numel() else None
+            d = getattr(c, "dictionary", None)
+            if d is not None:
+                darr = (C.c_char_p * len(d))(*d)
+                self._keep.append(darr)
+                arr[i].dict = C.cast(darr, C.POINTER(C.c_char_p))
+                arr[i].dict_size = len(d)
+        self.cols = arr
+        self.n_rows = int(rows or 0) if n_rows is None else int(n_rows)
+        self.desc = sel_table(C.cast(arr, C.POINTER(sel_column)), len(self.columns), self.n_rows)
+
+    @classmethod
+    def of(cls, t) -> "Table":
+        return t if isinstance(t, Table) else cls(t.columns)
+
+    def ref(self):
+        return C.byref(self.desc)
+
+
+# ----------------------------------------------------------------------------
+# predicates
+# ----------------------------------------------------------------------------
+
+def _f32(v) -> float:
+    f = np.float32(v)
+    if not (float(f) == float(v) or (np.isnan(f) and np.isnan(float(v)))):
+        raise TypeError(f"constant {v!r} is not exactly representable as float32")
+    return float(f)
+
+
+def _int(v) -> int:
+    if isinstance(v, (float, np.floating)):
+        raise TypeError(f"integer-like column compared with float constant {v!r}")
+    return int(v)
+
+
+def tree_to_postfix(tree, types: Sequence[str]):
+    """Neutral tree -> (ctypes array of sel_node, keep-alive list)."""
+    nodes, keep = [], []
+
+    def leaf(kind, col):
+        n = sel_node()
+        n.kind, n.col = kind, int(col)
+        return n
+
+    def walk(t):
+        k = t[0]
+        if k in ("and", "or"):
+            for c in t[1]:
+                walk(c)
+            if not t[1]:                      # empty AND is TRUE, empty OR is FALSE
+                n = sel_node()
+                n.kind = N_TRUE if k == "and" else N_FALSE
+                nodes.append(n)
+                return
+            n = sel_node()
+            n.kind, n.n_children = (N_AND if k == "and" else N_OR), len(t[1])
+            nodes.append(n)
+        elif k == "not":
+            walk(t[1])
+            n = sel_node()
+            n.kind = N_NOT
+            nodes.append(n)
+        elif k in ("true", "false"):
+            n = sel_node()
+            n.kind = N_TRUE if k == "true" else N_FALSE
+            nodes.append(n)
+        else:
+            col = int(t[1])
+            isf = 0 <= col < len(types) and types[col] == "f32"
+            if k == "cmp":
+                n = leaf(N_CMP, col)
+                n.op = OPS[t[2]]
+                if isf:
+                    n.f_lo = _f32(t[3])
+                else:
+                    n.i_lo = _int(t[3])
+            elif k == "between":
+                n = leaf(N_BETWEEN, col)
+                if isf:
+                    n.f_lo, n.f_hi = _f32(t[2]), _f32(t[3])
+                else:
+                    n.i_lo, n.i_hi = _int(t[2]), _int(t[3])
+            elif k == "in":
+                vals = list(t[2])
+                n = leaf(N_IN, col)
+                n.n_values = len(vals)
+                if vals:
+                    a = np.array([_f32(v) for v in vals], np.float32) if isf else \
+                        np.array([_int(v) for v in vals], np.int64)
+                    keep.append(a)
+                    n.values = a.ctypes.data
+            elif k == "like":
+                n = leaf(N_LIKE, col)
+                b = t[2].encode() if isinstance(t[2], str) else bytes(t[2])
+                keep.append(b)
+                n.prefix = b
+            else:
+                raise ValueError(f"unknown node {k!r}")
+            nodes.append(n)
+
+    walk(tree)
+    arr = (sel_node * len(nodes))(*nodes)
+    return arr, keep
+
+
+class Predicate:
+    """A compiled predicate (sel_pred); compiled against a table schema."""
+
+    def __init__(self, schema, tree):
+        schema = Table.of(schema)
+        self.tree = tree
+        arr, keep = tree_to_postfix(tree, schema.types)
+        h = C.c_void_p()
+        _check(lib.sel_compile_predicate(schema.ref(), arr, len(arr), C.byref(h)), "sel_compile_predicate")
+        self.h = h
+
+    def describe(self) -> str:
+        buf = C.create_string_buffer(1 << 16)
+        _check(lib.sel_pred_describe(self.h, buf, len(buf)), "sel_pred_describe")
+        return buf.value.decode()
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and h.value and lib is not None:
+            lib.sel_pred_free(h)
+            self.h = None
+
+
+def compile_predicate(schema, tree) -> Predicate:
+    return Predicate(schema, tree)
+
+
+# ----------------------------------------------------------------------------
+# context and calls
+# ----------------------------------------------------------------------------
+
+class Context:
+    """A sel_ctx bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream: Optional[torch.cuda.Stream] = None):
+        self.stream = stream or torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib.sel_ctx_create(C.c_void_p(self.stream.cuda_stream), C.byref(h)), "sel_ctx_create")
+        self.h = h
+
+    def set_scan_shape(self, tile_rows=0, stages=0, ctas_per_sm=0):
+        _check(lib.sel_ctx_set_scan_shape(self.h, tile_rows, stages, ctas_per_sm), "sel_ctx_set_scan_shape")
+
+    def debug_pushdown_fault(self, skip_tile: int, wait_ns: int = 0):
+        _check(lib.sel_ctx_debug_pushdown_fault(self.h, skip_tile, wait_ns), "sel_ctx_debug_pushdown_fault")
+
+    @property
+    def launches(self) -> int:
+        return int(lib.sel_ctx_launch_count(self.h))
+
+    def count(self, pred: Predicate, table) -> int:
+        table = Table.of(table)
+        out = C.c_uint64()
+        _check(lib.sel_count(self.h, pred.h, table.ref(), C.byref(out)), "sel_count")
+        return int(out.value)
+
+    def count_async(self, pred: Predicate, table, out: torch.Tensor):
+        """Enqueues the count into out (a 1-element int64 device tensor)."""
+        table = Table.of(table)
+        _check(lib.sel_count_async(self.h, pred.h, table.ref(), C.c_void_p(out.data_ptr())), "sel_count_async")
+
+    def pushdown(self, pred: Predicate, table, proj: Sequence[int], max_rows: int, rowids: bool = True,
+                 out_cols: Optional[List[torch.Tensor]] = None, out_rowids: Optional[torch.Tensor] = None,
+                 raise_too_large: bool = False):
+        """Selection push-down (Algorithm 1 Execute).  Returns (status, count,
+        [projected columns truncated to count], row ids or None); status is
+        SEL_OK or SEL_ERR_TOO_LARGE."""
+        table = Table.of(table)
+        dev = table.columns[0].data.device if table.columns else torch.device("cuda")
+        cap = max(int(max_rows), 0)
+        if out_cols is None:
+            out_cols = [torch.empty(max(cap, 1), dtype=TORCH_TYPES[table.types[c]], device=dev) for c in proj]
+        if rowids and out_rowids is None:
+            out_rowids = torch.empty(max(cap, 1), dtype=torch.int64, device=dev)
+        pc = (C.c_int32 * max(1, len(proj)))(*proj)
+        po = (C.c_void_p * max(1, len(proj)))(*[t.data_ptr() for t in out_cols])
+        out = C.c_uint64()
+        st = lib.sel_pushdown(self.h, pred.h, table.ref(), pc, len(proj), po,
+                              C.c_void_p(out_rowids.data_ptr()) if rowids else None, cap, C.byref(out))
+        n = int(out.value)
+        if st == SEL_ERR_TOO_LARGE and not raise_too_large:
+            return st, n, None, None
+        _check(st, "sel_pushdown")
+        return st, n, [t[:n] for t in out_cols], (out_rowids[:n] if rowids else None)
+
+    def pushdown_async(self, pred: Predicate, table, proj: Sequence[int], max_rows: int,
+                       out_cols: List[torch.Tensor], out_rowids: Optional[torch.Tensor], out_count: torch.Tensor):
+        """Enqueues the push-down; the exact count goes to out_count (int64 device tensor)."""
+        table = Table.of(table)
+        pc = (C.c_int32 * max(1, len(proj)))(*proj)
+        po = (C.c_void_p * max(1, len(proj)))(*[t.data_ptr() for t in out_cols])
+        _check(lib.sel_pushdown_async(self.h, pred.h, table.ref(), pc, len(proj), po,
+                                      C.c_void_p(out_rowids.data_ptr()) if out_rowids is not None else None,
+                                      int(max_rows), C.c_void_p(out_count.data_ptr())), "sel_pushdown_async")
+
+    def count_batch_async(self, preds: Sequence[Predicate], tables, out: torch.Tensor):
+        """Enqueues the batched counts into out (int64 device tensor of len(preds))."""
+        tabs = [Table.of(t) for t in tables]
+        n = len(preds)
+        pa = (C.c_void_p * n)(*[p.h.value for p in preds])
+        ta = (C.POINTER(sel_table) * n)(*[C.pointer(t.desc) for t in tabs])
+        _check(lib.sel_count_batch_async(self.h, pa, ta, n, C.c_void_p(out.data_ptr())), "sel_count_batch_async")
+
+    def synchronize(self):
+        _check(lib.sel_ctx_synchronize(self.h), "sel_ctx_synchronize")
+
+    def count_batch(self, preds: Sequence[Predicate], tables) -> List[int]:
+        tabs = [Table.of(t) for t in tables]
+        n = len(preds)
+        pa = (C.c_void_p * n)(*[p.h.value for p in preds])
+        ta = (C.POINTER(sel_table) * n)(*[C.pointer(t.desc) for t in tabs])
+        out = (C.c_uint64 * n)()
+        _check(lib.sel_count_batch(self.h, pa, ta, n, out), "sel_count_batch")
+        return [int(x) for x in out]
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and h.value and lib is not None:
+            lib.sel_ctx_destroy(h)
+            self.h = None
+
+
+class BatchPlan:
+    """sel_batch_plan: the predicates and tables must outlive the plan."""
+
+    def __init__(self, ctx: Context, preds: Sequence[Predicate], tables, autotune: bool = True):
+        self.ctx = ctx
+        self.preds = list(preds)
+        self.tables = [Table.of(t) for t in tables]
+        n = len(self.preds)
+        self.n = n
+        pa = (C.c_void_p * n)(*[p.h.value for p in self.preds])
+        ta = (C.POINTER(sel_table) * n)(*[C.pointer(t.desc) for t in self.tables])
+        self._keep = (pa, ta)
+        h = C.c_void_p()
+        _check(lib.sel_batch_plan_create(ctx.h, pa, ta, n, 1 if autotune else 0, C.byref(h)),
+               "sel_batch_plan_create")
+        self.h = h
+
+    def run(self, device_out: Optional[torch.Tensor] = None) -> Optional[List[int]]:
+        if device_out is not None:
+            _check(lib.sel_batch_plan_run(self.h, C.c_void_p(device_out.data_ptr()), None), "sel_batch_plan_run")
+            return None
+        out = (C.c_uint64 * self.n)()
+        _check(lib.sel_batch_plan_run(self.h, None, out), "sel_batch_plan_run")
+        return [int(x) for x in out]
+
+    def info(self):
+        tr, st, cp, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
+        _check(lib.sel_batch_plan_info(self.h, C.byref(tr), C.byref(st), C.byref(cp), C.byref(ms)),
+               "sel_batch_plan_info")
+        return {"tile_rows": tr.value, "stages": st.value, "ctas_per_sm": cp.value, "ms": ms.value}
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and h.value and lib is not None:
+            lib.sel_batch_plan_free(h)
+            self.h = None

@@ -1,0 +1,821 @@
+// api.cpp -- the C ABI of include/sel.h: contexts, argument checks, the
+// exact count (§3.1), the push-down with its maxSize contract (Algorithm 1,
+// Execute), and batched probe plans with autotuned launch shapes replayed
+// from CUDA graphs.
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace sel {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+static sel_status cuda_fail(const char* where, cudaError_t e) {
+    set_error("%s: %s", where, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SEL_ERR_OOM : SEL_ERR_CUDA;
+}
+
+#define SEL_CUDA(where, call)                          \
+    do {                                               \
+        cudaError_t e__ = (call);                      \
+        if (e__ != cudaSuccess) return cuda_fail(where, e__); \
+    } while (0)
+
+// A device buffer that only grows.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    sel_status ensure(size_t bytes, const char* what) {
+        if (bytes <= cap) return SEL_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 256));
+        if (e != cudaSuccess) return cuda_fail(what, e);
+        cap = std::max<size_t>(bytes, 256);
+        return SEL_OK;
+    }
+    ~DevBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+struct Shape {
+    int tile_rows = 0, stages = 0, ctas_per_sm = 0;
+};
+
+}  // namespace sel
+
+using namespace sel;
+
+struct sel_ctx {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int n_sm = 0;
+    int max_smem = 0;
+    DevBuf counts;            // sel_count / batch staging
+    DevBuf err;               // 4 bytes: error flag of the last launches
+    DevBuf pd_scratch;        // push-down: tile status | tile counter | total
+    unsigned long long* h_pinned = nullptr;   // pinned host results (count, total)
+    unsigned int* h_err = nullptr;
+    size_t h_cap = 0;
+    Shape shape;              // overrides for single-predicate scans
+    uint64_t launches = 0;
+    std::map<std::string, sel_batch_plan*> plans;   // sel_count_batch cache
+    long long debug_skip_tile = -1;
+    unsigned long long debug_wait_ns = kWaitNs;
+};
+
+struct sel_batch_plan {
+    sel_ctx* ctx = nullptr;
+    int n = 0;
+    void* d_blob = nullptr;
+    void* d_counts = nullptr;
+    uint32_t blob_bytes = 0, instr_off = 0, pool_off = 0;
+    std::vector<TableArg> tables;      // slot pointers, programs per table
+    uint32_t n_progs = 0;
+    Shape shape;
+    float ms = 0.f;
+    cudaGraphExec_t graph = nullptr;
+    int launches_per_run = 0;
+};
+
+namespace sel {
+
+static sel_status ensure_host(sel_ctx* c, size_t n) {
+    if (n <= c->h_cap) return SEL_OK;
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    c->h_pinned = nullptr;
+    c->h_cap = 0;
+    SEL_CUDA("cudaMallocHost", cudaMallocHost(reinterpret_cast<void**>(&c->h_pinned), n * 8 + 64));
+    c->h_cap = n;
+    return SEL_OK;
+}
+
+static sel_status check_table(const sel_table* t, const char* who) {
+    if (!t || (t->n_cols > 0 && !t->cols) || t->n_cols < 0 || t->n_rows < 0) {
+        set_error("%s: bad table descriptor", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    return SEL_OK;
+}
+
+// The columns a program reads must exist with the compiled types, be non-null
+// and element-aligned.
+static sel_status check_pred_on_table(const sel_pred* p, const sel_table* t, const char* who) {
+    sel_status s = check_table(t, who);
+    if (s != SEL_OK) return s;
+    if (!p) {
+        set_error("%s: predicate is NULL", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    for (size_t j = 0; j < p->prog.slot_col.size(); ++j) {
+        const int c = p->prog.slot_col[j];
+        if (c >= t->n_cols) {
+            set_error("%s: predicate reads column %d, table has %d", who, c, t->n_cols);
+            return SEL_ERR_INVALID_ARG;
+        }
+        if (t->cols[c].type != p->col_types[c]) {
+            set_error("%s: column %d has type %d, predicate was compiled for %d", who, c, t->cols[c].type,
+                      p->col_types[c]);
+            return SEL_ERR_TYPE;
+        }
+        if (t->n_rows > 0) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(t->cols[c].data);
+            if (!a || a % p->prog.slot_width[j]) {
+                set_error("%s: column %d data pointer is null or not element-aligned", who, c);
+                return SEL_ERR_INVALID_ARG;
+            }
+        }
+    }
+    return SEL_OK;
+}
+
+static void fill_table_arg(TableArg& ta, const std::vector<int32_t>& slot_col, const sel_table* t) {
+    std::memset(&ta, 0, sizeof(ta));
+    ta.n_rows = t->n_rows;
+    ta.n_slots = (uint32_t)slot_col.size();
+    ta.tma = 1;
+    uint32_t rb = 0;
+    for (size_t j = 0; j < slot_col.size(); ++j) {
+        const sel_column& c = t->cols[slot_col[j]];
+        ta.col[j] = static_cast<const uint8_t*>(c.data);
+        ta.width[j] = c.type == SEL_I64 ? 8u : 4u;
+        rb += ta.width[j];
+        if (reinterpret_cast<uintptr_t>(c.data) % 16) ta.tma = 0;
+    }
+    ta.row_bytes = rb;
+}
+
+static int default_tile_rows(uint32_t row_bytes, int stage_target) {
+    if (row_bytes == 0) return 2048;
+    int r = (int)(stage_target / row_bytes) / kChunkRows * kChunkRows;
+    return std::max(kChunkRows, std::min(8192, r));
+}
+
+// Fills shape-dependent fields and launches (several launches when the
+// tables do not fit in one).
+static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_bytes, uint32_t instr_off,
+                           uint32_t pool_off, uint32_t n_progs, std::vector<TableArg> tables,
+                           unsigned long long* d_counts, const Shape& sh_in, int* n_launches) {
+    int launches = 0;
+    // largest tile (multiple of 256 rows, at most the requested one) whose
+    // stages fit in shared memory next to the counters and the programs
+    Shape sh = sh_in;
+    {
+        uint32_t max_rb = 0;
+        for (auto& t : tables) max_rb = std::max(max_rb, t.row_bytes);
+        ScanArgs probe;
+        std::memset(&probe, 0, sizeof(probe));
+        probe.n_progs = n_progs;
+        probe.stages = (uint32_t)sh.stages;
+        probe.blob_bytes = blob_bytes;
+        probe.prog_in_smem = blob_bytes <= 48u * 1024u ? 1u : 0u;
+        const size_t fixed = scan_layout(probe);
+        if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem || sh.stages < 1) {
+            set_error("scan: %u programs and %d stages do not fit in shared memory", n_progs, sh.stages);
+            return SEL_ERR_UNSUPPORTED;
+        }
+        if (max_rb > 0) {
+            const size_t per_stage = ((size_t)ctx->max_smem - fixed) / (size_t)sh.stages;
+            const int fit = (int)(per_stage / max_rb) / kChunkRows * kChunkRows;
+            if (fit < kChunkRows) {
+                set_error("scan: %d stages of 256 rows x %u bytes do not fit in shared memory", sh.stages, max_rb);
+                return SEL_ERR_UNSUPPORTED;
+            }
+            sh.tile_rows = std::min(sh.tile_rows, fit);
+        }
+    }
+    for (size_t t0 = 0; t0 < tables.size(); t0 += kMaxTables) {
+        ScanArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.blob = d_blob;
+        a.n_progs = n_progs;
+        a.instr_off = instr_off;
+        a.pool_off = pool_off;
+        a.blob_bytes = blob_bytes;
+        a.tile_rows = (uint32_t)sh.tile_rows;
+        a.stages = (uint32_t)sh.stages;
+        a.counts = d_counts;
+        a.err = static_cast<unsigned int*>(ctx->err.p);
+        const size_t t1 = std::min(tables.size(), t0 + kMaxTables);
+        a.n_tables = (uint32_t)(t1 - t0);
+        uint32_t max_rb = 0;
+        int64_t tiles = 0;
+        for (size_t i = t0; i < t1; ++i) {
+            TableArg ta = tables[i];
+            ta.n_tiles = (ta.n_rows + sh.tile_rows - 1) / sh.tile_rows;
+            ta.tile_begin = tiles;
+            tiles += ta.n_tiles;
+            uint32_t off = 0;
+            for (uint32_t j = 0; j < ta.n_slots; ++j) {
+                ta.slot_off[j] = off;
+                off += (uint32_t)sh.tile_rows * ta.width[j];
+            }
+            max_rb = std::max(max_rb, ta.row_bytes);
+            a.t[i - t0] = ta;
+        }
+        a.total_tiles = tiles;
+        a.stage_bytes = ((uint32_t)sh.tile_rows * max_rb + 127u) / 128u * 128u;
+        a.prog_in_smem = blob_bytes <= 48u * 1024u ? 1u : 0u;
+        size_t smem = scan_layout(a);
+        if (smem > (size_t)ctx->max_smem) {
+            set_error("scan: %zu bytes of shared memory needed (tile_rows %d, stages %d)", smem, sh.tile_rows,
+                      sh.stages);
+            return SEL_ERR_UNSUPPORTED;
+        }
+        if (tiles == 0) continue;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->n_sm * sh.ctas_per_sm));
+        cudaError_t e = launch_scan_count(a, (int)grid, smem, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail("scan launch", e);
+        ++launches;
+        ctx->launches++;
+    }
+    if (n_launches) *n_launches = launches;
+    return SEL_OK;
+}
+
+static Shape single_shape(sel_ctx* ctx, uint32_t row_bytes) {
+    Shape s;
+    s.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 4;
+    s.ctas_per_sm = ctx->shape.ctas_per_sm > 0 ? ctx->shape.ctas_per_sm : 1;
+    s.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : default_tile_rows(row_bytes, 40 * 1024);
+    return s;
+}
+
+static sel_status sync_and_check(sel_ctx* ctx, const char* who) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(who, e);
+    return SEL_OK;
+}
+
+}  // namespace sel
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" const char* sel_last_error(void) { return sel::g_err.c_str(); }
+
+extern "C" const char* sel_status_str(sel_status s) {
+    switch (s) {
+    case SEL_OK: return "SEL_OK";
+    case SEL_ERR_INVALID_ARG: return "SEL_ERR_INVALID_ARG";
+    case SEL_ERR_TYPE: return "SEL_ERR_TYPE";
+    case SEL_ERR_UNSUPPORTED: return "SEL_ERR_UNSUPPORTED";
+    case SEL_ERR_OOM: return "SEL_ERR_OOM";
+    case SEL_ERR_CUDA: return "SEL_ERR_CUDA";
+    case SEL_ERR_TOO_LARGE: return "SEL_ERR_TOO_LARGE";
+    case SEL_ERR_TIMEOUT: return "SEL_ERR_TIMEOUT";
+    }
+    return "SEL_ERR_UNKNOWN";
+}
+
+extern "C" sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out) {
+    if (!out) {
+        set_error("sel_ctx_create: out is NULL");
+        return SEL_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int dev = 0;
+    SEL_CUDA("cudaGetDevice", cudaGetDevice(&dev));
+    std::unique_ptr<sel_ctx> c(new sel_ctx());
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->device = dev;
+    SEL_CUDA("cudaDeviceGetAttribute", cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev));
+    SEL_CUDA("cudaDeviceGetAttribute",
+             cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    SEL_CUDA("scan smem attribute", scan_kernel_max_smem(c->max_smem));
+    sel_status s = c->err.ensure(256, "error flag");
+    if (s != SEL_OK) return s;
+    SEL_CUDA("cudaMemset", cudaMemset(c->err.p, 0, 256));
+    s = ensure_host(c.get(), 64);
+    if (s != SEL_OK) return s;
+    SEL_CUDA("cudaMallocHost", cudaMallocHost(reinterpret_cast<void**>(&c->h_err), 64));
+    *out = c.release();
+    return SEL_OK;
+}
+
+extern "C" void sel_ctx_destroy(sel_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->plans) sel_batch_plan_free(kv.second);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    delete c;
+}
+
+extern "C" sel_status sel_ctx_set_scan_shape(sel_ctx* c, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm) {
+    if (!c || tile_rows < 0 || tile_rows % kChunkRows || tile_rows > 8192 || stages < 0 || stages > 16 ||
+        ctas_per_sm < 0 || ctas_per_sm > 8) {
+        set_error("sel_ctx_set_scan_shape: bad arguments");
+        return SEL_ERR_INVALID_ARG;
+    }
+    c->shape.tile_rows = tile_rows;
+    c->shape.stages = stages;
+    c->shape.ctas_per_sm = ctas_per_sm;
+    return SEL_OK;
+}
+
+extern "C" uint64_t sel_ctx_launch_count(const sel_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" sel_status sel_ctx_debug_pushdown_fault(sel_ctx* c, int64_t skip_tile, uint64_t wait_ns) {
+    if (!c) {
+        set_error("sel_ctx_debug_pushdown_fault: ctx is NULL");
+        return SEL_ERR_INVALID_ARG;
+    }
+    c->debug_skip_tile = skip_tile;
+    c->debug_wait_ns = wait_ns ? wait_ns : kWaitNs;
+    return SEL_OK;
+}
+
+static sel_status count_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                                unsigned long long* d_out, const char* who) {
+    sel_status s = check_pred_on_table(pred, table, who);
+    if (s != SEL_OK) return s;
+    s = pred_upload(pred);
+    if (s != SEL_OK) return s;
+    TableArg ta;
+    fill_table_arg(ta, pred->prog.slot_col, table);
+    ta.prog_begin = 0;
+    ta.prog_end = 1;
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(d_out, 0, 8, ctx->stream));
+    const Shape sh = single_shape(ctx, ta.row_bytes);
+    return run_scan(ctx, static_cast<const uint8_t*>(pred->d_blob), pred->blob_bytes, pred->instr_off,
+                    pred->pool_off, 1, {ta}, d_out, sh, nullptr);
+}
+
+extern "C" sel_status sel_count_async(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                                      uint64_t* dev_out_count) {
+    if (!ctx || !dev_out_count) {
+        set_error("sel_count_async: null context or output");
+        return SEL_ERR_INVALID_ARG;
+    }
+    return count_enqueue(ctx, pred, table, reinterpret_cast<unsigned long long*>(dev_out_count), "sel_count_async");
+}
+
+extern "C" sel_status sel_count(sel_ctx* ctx, const sel_pred* pred, const sel_table* table, uint64_t* out_count) {
+    if (!ctx || !out_count) {
+        set_error("sel_count: null context or output");
+        return SEL_ERR_INVALID_ARG;
+    }
+    sel_status s = ctx->counts.ensure(64, "count buffer");
+    if (s != SEL_OK) return s;
+    unsigned long long* d = static_cast<unsigned long long*>(ctx->counts.p);
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(ctx->err.p, 0, 4, ctx->stream));
+    s = count_enqueue(ctx, pred, table, d, "sel_count");
+    if (s != SEL_OK) return s;
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_pinned, d, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_err, ctx->err.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_and_check(ctx, "sel_count");
+    if (s != SEL_OK) return s;
+    if (*ctx->h_err) {
+        set_error("sel_count: a device wait timed out");
+        return SEL_ERR_TIMEOUT;
+    }
+    *out_count = ctx->h_pinned[0];
+    return SEL_OK;
+}
+
+// Enqueues the push-down; the exact count lands in d_total (device).
+static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                                   const int32_t* proj_cols, int32_t n_proj, void* const* dev_out_cols,
+                                   int64_t* dev_out_rowids, uint64_t max_rows, unsigned long long* d_total,
+                                   const char* who) {
+    if (!ctx || n_proj < 0 || n_proj > kPdMaxProj || (n_proj > 0 && (!proj_cols || !dev_out_cols))) {
+        set_error("%s: bad arguments", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    sel_status s = check_pred_on_table(pred, table, who);
+    if (s != SEL_OK) return s;
+    PushdownArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int32_t j = 0; j < n_proj; ++j) {
+        const int c = proj_cols[j];
+        if (c < 0 || c >= table->n_cols) {
+            set_error("%s: projected column %d out of range", who, c);
+            return SEL_ERR_INVALID_ARG;
+        }
+        const sel_column& col = table->cols[c];
+        if (col.type < SEL_I32 || col.type > SEL_DICT) {
+            set_error("%s: projected column %d has an unknown type", who, c);
+            return SEL_ERR_TYPE;
+        }
+        const uint32_t w = col.type == SEL_I64 ? 8u : 4u;
+        const uintptr_t src = reinterpret_cast<uintptr_t>(col.data);
+        const uintptr_t dst = reinterpret_cast<uintptr_t>(dev_out_cols[j]);
+        if ((table->n_rows > 0 && (!src || src % w)) || (max_rows > 0 && (!dst || dst % w))) {
+            set_error("%s: projected column %d: null or misaligned source/output pointer", who, c);
+            return SEL_ERR_INVALID_ARG;
+        }
+        a.proj_src[j] = reinterpret_cast<const uint8_t*>(col.data);
+        a.proj_dst[j] = static_cast<uint8_t*>(dev_out_cols[j]);
+        a.proj_width[j] = w;
+        a.proj_slot[j] = -1;
+        for (size_t k = 0; k < pred->prog.slot_col.size(); ++k)
+            if (pred->prog.slot_col[k] == c) a.proj_slot[j] = (int32_t)k;
+    }
+    if (dev_out_rowids && reinterpret_cast<uintptr_t>(dev_out_rowids) % 8) {
+        set_error("%s: row id output is not 8-byte aligned", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    s = pred_upload(pred);
+    if (s != SEL_OK) return s;
+    TableArg ta;
+    fill_table_arg(ta, pred->prog.slot_col, table);
+    a.blob = static_cast<const uint8_t*>(pred->d_blob);
+    a.instr_off = pred->instr_off;
+    a.pool_off = pred->pool_off;
+    a.blob_bytes = pred->blob_bytes;
+    a.n_instr = (uint32_t)pred->prog.instrs.size();
+    a.n_slots = ta.n_slots;
+    a.row_bytes = ta.row_bytes;
+    a.tma = ta.tma;
+    a.tile_rows = ctx->shape.tile_rows > 0 ? (uint32_t)ctx->shape.tile_rows : 1024u;
+    {   // shrink the tile until its stage and its output staging fit in shared memory
+        uint32_t proj_bytes = dev_out_rowids ? 8u : 0u;
+        for (int32_t j = 0; j < n_proj; ++j) proj_bytes += a.proj_width[j];
+        const size_t fixed = ((size_t)pred->blob_bytes + 127) / 128 * 128 + 1024 + 16 * (size_t)(n_proj + 1);
+        while (a.tile_rows > (uint32_t)kChunkRows &&
+               fixed + (size_t)a.tile_rows * (ta.row_bytes + proj_bytes) > (size_t)ctx->max_smem)
+            a.tile_rows -= kChunkRows;
+    }
+    uint32_t off = 0;
+    for (uint32_t j = 0; j < ta.n_slots; ++j) {
+        a.col[j] = ta.col[j];
+        a.width[j] = ta.width[j];
+        a.slot_off[j] = off;
+        off += a.tile_rows * ta.width[j];
+    }
+    a.n_rows = table->n_rows;
+    a.n_tiles = (table->n_rows + a.tile_rows - 1) / a.tile_rows;
+    a.n_proj = (uint32_t)n_proj;
+    a.rowids = reinterpret_cast<long long*>(dev_out_rowids);
+    a.max_rows = max_rows;
+    a.skip_publish_tile = ctx->debug_skip_tile;
+    a.wait_ns = ctx->debug_wait_ns;
+    const size_t smem = pushdown_layout(a);
+    if (smem > (size_t)ctx->max_smem) {
+        set_error("%s: %zu bytes of shared memory needed", who, smem);
+        return SEL_ERR_UNSUPPORTED;
+    }
+    // scratch: status[n_tiles] | tile counter
+    const size_t status_bytes = (size_t)a.n_tiles * 8;
+    s = ctx->pd_scratch.ensure(status_bytes + 64, "push-down scratch");
+    if (s != SEL_OK) return s;
+    uint8_t* scr = static_cast<uint8_t*>(ctx->pd_scratch.p);
+    a.status = reinterpret_cast<unsigned long long*>(scr);
+    a.tile_counter = reinterpret_cast<unsigned int*>(scr + status_bytes);
+    a.total = d_total;
+    a.err = static_cast<unsigned int*>(ctx->err.p);
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(scr, 0, status_bytes + 64, ctx->stream));
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(d_total, 0, 8, ctx->stream));
+    cudaError_t e = launch_pushdown(a, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail("push-down launch", e);
+    if (a.n_tiles > 0) ctx->launches++;
+    return SEL_OK;
+}
+
+extern "C" sel_status sel_pushdown_async(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                                         const int32_t* proj_cols, int32_t n_proj, void* const* dev_out_cols,
+                                         int64_t* dev_out_rowids, uint64_t max_rows, uint64_t* dev_out_count) {
+    if (!dev_out_count) {
+        set_error("sel_pushdown_async: dev_out_count is NULL");
+        return SEL_ERR_INVALID_ARG;
+    }
+    return pushdown_enqueue(ctx, pred, table, proj_cols, n_proj, dev_out_cols, dev_out_rowids, max_rows,
+                            reinterpret_cast<unsigned long long*>(dev_out_count), "sel_pushdown_async");
+}
+
+extern "C" sel_status sel_pushdown(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                                   const int32_t* proj_cols, int32_t n_proj, void* const* dev_out_cols,
+                                   int64_t* dev_out_rowids, uint64_t max_rows, uint64_t* out_count) {
+    const char* who = "sel_pushdown";
+    if (!ctx || !out_count) {
+        set_error("%s: bad arguments", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    sel_status s = ctx->counts.ensure(64, "count buffer");
+    if (s != SEL_OK) return s;
+    unsigned long long* d_total = static_cast<unsigned long long*>(ctx->counts.p);
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(ctx->err.p, 0, 4, ctx->stream));
+    s = pushdown_enqueue(ctx, pred, table, proj_cols, n_proj, dev_out_cols, dev_out_rowids, max_rows, d_total, who);
+    if (s != SEL_OK) return s;
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_pinned, d_total, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_err, ctx->err.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_and_check(ctx, who);
+    if (s != SEL_OK) return s;
+    if (*ctx->h_err) {
+        set_error("%s: a look-back wait timed out", who);
+        return SEL_ERR_TIMEOUT;
+    }
+    *out_count = ctx->h_pinned[0];
+    if (*out_count > max_rows) {
+        set_error("%s: count %llu > max_rows %llu", who, (unsigned long long)*out_count,
+                  (unsigned long long)max_rows);
+        return SEL_ERR_TOO_LARGE;
+    }
+    return SEL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched probes
+// ---------------------------------------------------------------------------
+
+namespace sel {
+
+static std::string table_key(const sel_table* t) {
+    std::string k = std::to_string(t->n_rows) + ":";
+    for (int32_t c = 0; c < t->n_cols; ++c) {
+        char b[48];
+        std::snprintf(b, sizeof(b), "%p/%d,", t->cols[c].data, t->cols[c].type);
+        k += b;
+    }
+    return k;
+}
+
+static sel_status plan_time(sel_batch_plan* p, const Shape& sh, int reps, float* ms) {
+    sel_ctx* ctx = p->ctx;
+    cudaEvent_t e0, e1;
+    SEL_CUDA("cudaEventCreate", cudaEventCreate(&e0));
+    SEL_CUDA("cudaEventCreate", cudaEventCreate(&e1));
+    float best = 1e30f;
+    sel_status s = SEL_OK;
+    for (int r = 0; r <= reps && s == SEL_OK; ++r) {
+        cudaEventRecord(e0, ctx->stream);
+        cudaMemsetAsync(p->d_counts, 0, (size_t)p->n * 8, ctx->stream);
+        s = run_scan(ctx, static_cast<const uint8_t*>(p->d_blob), p->blob_bytes, p->instr_off, p->pool_off,
+                     p->n_progs, p->tables, static_cast<unsigned long long*>(p->d_counts), sh, nullptr);
+        cudaEventRecord(e1, ctx->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) s = cuda_fail("autotune", e);
+        float t = 0;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (r > 0 || reps == 0) best = std::min(best, t);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = best;
+    return s;
+}
+
+static sel_status plan_capture(sel_batch_plan* p) {
+    sel_ctx* ctx = p->ctx;
+    cudaStream_t cs;
+    SEL_CUDA("cudaStreamCreate", cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = ctx->stream;
+    const uint64_t saved_launches = ctx->launches;
+    ctx->stream = cs;
+    cudaGraph_t g = nullptr;
+    sel_status s = SEL_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) s = cuda_fail("cudaStreamBeginCapture", e);
+    int nl = 0;
+    if (s == SEL_OK) {
+        cudaMemsetAsync(p->d_counts, 0, (size_t)p->n * 8, cs);
+        s = run_scan(ctx, static_cast<const uint8_t*>(p->d_blob), p->blob_bytes, p->instr_off, p->pool_off,
+                     p->n_progs, p->tables, static_cast<unsigned long long*>(p->d_counts), p->shape, &nl);
+        e = cudaStreamEndCapture(cs, &g);
+        if (s == SEL_OK && e != cudaSuccess) s = cuda_fail("cudaStreamEndCapture", e);
+    }
+    ctx->stream = saved;
+    ctx->launches = saved_launches;
+    if (s == SEL_OK) {
+        e = cudaGraphInstantiate(&p->graph, g, 0);
+        if (e != cudaSuccess) s = cuda_fail("cudaGraphInstantiate", e);
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    p->launches_per_run = nl;
+    return s;
+}
+
+}  // namespace sel
+
+extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const* preds,
+                                            const sel_table* const* tables, int32_t n, int32_t autotune,
+                                            sel_batch_plan** out) {
+    const char* who = "sel_batch_plan_create";
+    if (!ctx || !out || n <= 0 || !preds || !tables) {
+        set_error("%s: bad arguments", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    for (int32_t i = 0; i < n; ++i) {
+        sel_status s = check_pred_on_table(preds[i], tables[i], who);
+        if (s != SEL_OK) return s;
+    }
+    // group predicates by table (same data pointers and row count)
+    std::vector<std::string> keys;
+    std::map<std::string, int> gid;
+    std::vector<int> group(n);
+    std::vector<const sel_table*> gtab;
+    for (int32_t i = 0; i < n; ++i) {
+        const std::string k = table_key(tables[i]);
+        auto it = gid.find(k);
+        if (it == gid.end()) {
+            it = gid.emplace(k, (int)gtab.size()).first;
+            gtab.push_back(tables[i]);
+        }
+        group[i] = it->second;
+    }
+    std::unique_ptr<sel_batch_plan> p(new sel_batch_plan());
+    p->ctx = ctx;
+    p->n = n;
+    std::vector<const Program*> progs;
+    std::vector<std::vector<int32_t>> maps;
+    std::vector<uint32_t> outs;
+    for (size_t g = 0; g < gtab.size(); ++g) {
+        std::vector<int32_t> cols;
+        for (int32_t i = 0; i < n; ++i)
+            if (group[i] == (int)g)
+                for (int32_t c : preds[i]->prog.slot_col) cols.push_back(c);
+        std::sort(cols.begin(), cols.end());
+        cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+        if ((int)cols.size() > kMaxSlots) {
+            set_error("%s: predicates on one table read more than 16 distinct columns", who);
+            return SEL_ERR_UNSUPPORTED;
+        }
+        TableArg ta;
+        fill_table_arg(ta, cols, gtab[g]);
+        ta.prog_begin = (uint32_t)progs.size();
+        for (int32_t i = 0; i < n; ++i) {
+            if (group[i] != (int)g) continue;
+            std::vector<int32_t> m;
+            for (int32_t c : preds[i]->prog.slot_col)
+                m.push_back((int32_t)(std::lower_bound(cols.begin(), cols.end(), c) - cols.begin()));
+            progs.push_back(&preds[i]->prog);
+            maps.push_back(m);
+            outs.push_back((uint32_t)i);
+        }
+        ta.prog_end = (uint32_t)progs.size();
+        p->tables.push_back(ta);
+    }
+    p->n_progs = (uint32_t)progs.size();
+    std::vector<uint8_t> blob;
+    build_blob(progs, maps, blob, p->instr_off, p->pool_off, outs);
+    p->blob_bytes = (uint32_t)blob.size();
+    SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_blob, blob.size()));
+    SEL_CUDA("cudaMemcpy", cudaMemcpy(p->d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
+    SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_counts, (size_t)n * 8));
+    uint32_t max_rb = 0;
+    for (auto& t : p->tables) max_rb = std::max(max_rb, t.row_bytes);
+    // default shape, then the autotuner's candidates
+    Shape best;
+    best.stages = 4;
+    best.ctas_per_sm = 2;
+    best.tile_rows = default_tile_rows(max_rb, 24 * 1024);
+    float best_ms = 0.f;
+    if (autotune) {
+        struct Cand { int stage_kb, stages, ctas; };
+        const Cand cands[] = {{24, 4, 2}, {16, 4, 2}, {32, 3, 2}, {40, 4, 1}, {16, 6, 2},
+                              {12, 4, 3}, {8, 4, 4}, {48, 3, 1}, {32, 5, 1}};
+        best_ms = 1e30f;
+        for (const Cand& c : cands) {
+            Shape sh;
+            sh.stages = c.stages;
+            sh.ctas_per_sm = c.ctas;
+            sh.tile_rows = default_tile_rows(max_rb, c.stage_kb * 1024);
+            float ms = 0;
+            sel_status s = plan_time(p.get(), sh, 2, &ms);
+            if (s == SEL_ERR_UNSUPPORTED) continue;
+            if (s != SEL_OK) return s;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+            }
+        }
+    }
+    p->shape = best;
+    p->ms = best_ms;
+    sel_status s = plan_capture(p.get());
+    if (s != SEL_OK) return s;
+    *out = p.release();
+    return SEL_OK;
+}
+
+extern "C" sel_status sel_batch_plan_run(sel_batch_plan* p, uint64_t* dev_out_counts, uint64_t* host_out_counts) {
+    if (!p || (!dev_out_counts && !host_out_counts)) {
+        set_error("sel_batch_plan_run: bad arguments");
+        return SEL_ERR_INVALID_ARG;
+    }
+    sel_ctx* ctx = p->ctx;
+    if (!dev_out_counts) SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(ctx->err.p, 0, 4, ctx->stream));
+    SEL_CUDA("cudaGraphLaunch", cudaGraphLaunch(p->graph, ctx->stream));
+    ctx->launches += (uint64_t)p->launches_per_run;
+    const size_t bytes = (size_t)p->n * 8;
+    if (dev_out_counts) {
+        SEL_CUDA("cudaMemcpyAsync",
+                 cudaMemcpyAsync(dev_out_counts, p->d_counts, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        return SEL_OK;
+    }
+    sel_status s = ensure_host(ctx, (size_t)p->n);
+    if (s != SEL_OK) return s;
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_pinned, p->d_counts, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_err, ctx->err.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_and_check(ctx, "sel_batch_plan_run");
+    if (s != SEL_OK) return s;
+    if (*ctx->h_err) {
+        set_error("sel_batch_plan_run: a device wait timed out");
+        return SEL_ERR_TIMEOUT;
+    }
+    std::memcpy(host_out_counts, ctx->h_pinned, bytes);
+    return SEL_OK;
+}
+
+extern "C" sel_status sel_batch_plan_info(const sel_batch_plan* p, int32_t* tile_rows, int32_t* stages,
+                                          int32_t* ctas_per_sm, float* ms) {
+    if (!p) {
+        set_error("sel_batch_plan_info: plan is NULL");
+        return SEL_ERR_INVALID_ARG;
+    }
+    if (tile_rows) *tile_rows = p->shape.tile_rows;
+    if (stages) *stages = p->shape.stages;
+    if (ctas_per_sm) *ctas_per_sm = p->shape.ctas_per_sm;
+    if (ms) *ms = p->ms;
+    return SEL_OK;
+}
+
+extern "C" void sel_batch_plan_free(sel_batch_plan* p) {
+    if (!p) return;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->d_blob) cudaFree(p->d_blob);
+    if (p->d_counts) cudaFree(p->d_counts);
+    delete p;
+}
+
+static sel_status batch_cached(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
+                               int32_t n, uint64_t* dev_out, uint64_t* host_out) {
+    std::string key;
+    for (int32_t i = 0; i < n; ++i) {
+        if (!preds[i] || !tables[i]) {
+            set_error("sel_count_batch: null predicate or table %d", i);
+            return SEL_ERR_INVALID_ARG;
+        }
+        key += std::to_string(preds[i]->content) + "@" + table_key(tables[i]) + ";";
+    }
+    auto it = ctx->plans.find(key);
+    if (it == ctx->plans.end()) {
+        sel_batch_plan* p = nullptr;
+        sel_status s = sel_batch_plan_create(ctx, preds, tables, n, 1, &p);
+        if (s != SEL_OK) return s;
+        if (ctx->plans.size() > 64) {   // bounded cache
+            for (auto& kv : ctx->plans) sel_batch_plan_free(kv.second);
+            ctx->plans.clear();
+        }
+        it = ctx->plans.emplace(key, p).first;
+    }
+    return sel_batch_plan_run(it->second, dev_out, host_out);
+}
+
+extern "C" sel_status sel_count_batch(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
+                                      int32_t n, uint64_t* out_counts) {
+    if (!ctx || !preds || !tables || n <= 0 || !out_counts) {
+        set_error("sel_count_batch: bad arguments");
+        return SEL_ERR_INVALID_ARG;
+    }
+    return batch_cached(ctx, preds, tables, n, nullptr, out_counts);
+}
+
+extern "C" sel_status sel_count_batch_async(sel_ctx* ctx, const sel_pred* const* preds,
+                                            const sel_table* const* tables, int32_t n, uint64_t* dev_out_counts) {
+    if (!ctx || !preds || !tables || n <= 0 || !dev_out_counts) {
+        set_error("sel_count_batch_async: bad arguments");
+        return SEL_ERR_INVALID_ARG;
+    }
+    return batch_cached(ctx, preds, tables, n, dev_out_counts, nullptr);
+}
+
+extern "C" sel_status sel_ctx_synchronize(sel_ctx* ctx) {
+    if (!ctx) {
+        set_error("sel_ctx_synchronize: ctx is NULL");
+        return SEL_ERR_INVALID_ARG;
+    }
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_err, ctx->err.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    sel_status s = sync_and_check(ctx, "sel_ctx_synchronize");
+    if (s != SEL_OK) return s;
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(ctx->err.p, 0, 4, ctx->stream));
+    if (*ctx->h_err) {
+        set_error("sel_ctx_synchronize: a device wait timed out since the last check");
+        return SEL_ERR_TIMEOUT;
+    }
+    return SEL_OK;
+}

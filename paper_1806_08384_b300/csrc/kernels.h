@@ -1,0 +1,84 @@
+// kernels.h -- launch interface between the host runtime and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "program.h"
+
+namespace sel {
+
+constexpr int kMaxTables = 8;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device wait
+constexpr int kScanThreads = 256;
+
+// One table of a scan launch: its referenced columns ("slots"), its tiles in
+// the launch's global tile sequence and the programs evaluated on it.
+struct TableArg {
+    const uint8_t* col[kMaxSlots];   // device base pointer of each slot's column
+    int64_t n_rows;
+    int64_t tile_begin;              // first global tile index of this table
+    int64_t n_tiles;                 // ceil(n_rows / tile_rows)
+    uint32_t slot_off[kMaxSlots];    // byte offset of each slot inside a stage
+    uint32_t width[kMaxSlots];       // bytes per element of each slot
+    uint32_t prog_begin, prog_end;   // programs [prog_begin, prog_end) run on this table
+    uint32_t n_slots;
+    uint32_t row_bytes;              // sum of the slot widths
+    uint32_t tma;                    // 1: every slot base is 16-byte aligned
+    uint32_t pad;
+};
+
+// Program blob (device): ProgDesc[n_progs] | Instr[] at instr_off | pool at pool_off.
+struct ScanArgs {
+    const uint8_t* blob;
+    uint32_t n_progs, instr_off, pool_off, blob_bytes;
+    uint32_t tile_rows, stages, stage_bytes, prog_in_smem;
+    uint32_t cnt_off, prog_off, stage_off, n_tables;
+    int64_t total_tiles;
+    unsigned long long* counts;      // n_progs, zeroed before the launch
+    unsigned int* err;               // bit 0: a bounded wait timed out
+    TableArg t[kMaxTables];
+};
+
+// Shared-memory bytes needed by a scan launch (and fills the *_off fields).
+size_t scan_layout(ScanArgs& a);
+cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st);
+cudaError_t scan_kernel_max_smem(int bytes);
+
+// ---------------------------------------------------------------------------
+// push-down (stable compaction with decoupled look-back)
+// ---------------------------------------------------------------------------
+constexpr int kPdThreads = 256;
+constexpr int kPdMaxProj = 16;
+
+struct PushdownArgs {
+    const uint8_t* blob;             // single-program blob (ProgDesc | Instr | pool)
+    uint32_t instr_off, pool_off, n_instr, blob_bytes;
+    const uint8_t* col[kMaxSlots];   // predicate slots
+    uint32_t width[kMaxSlots];
+    uint32_t slot_off[kMaxSlots];
+    uint32_t n_slots, row_bytes, tma, tile_rows;
+    int64_t n_rows, n_tiles;
+    // projection
+    uint32_t n_proj;
+    int32_t proj_slot[kPdMaxProj];   // slot index when the column is a predicate slot, else -1
+    const uint8_t* proj_src[kPdMaxProj];
+    uint8_t* proj_dst[kPdMaxProj];
+    uint32_t proj_width[kPdMaxProj];
+    uint32_t proj_stage_off[kPdMaxProj + 1];   // the last used entry is the row ids
+    long long* rowids;               // may be null
+    unsigned long long max_rows;
+    // scratch
+    unsigned long long* status;      // n_tiles, zeroed
+    unsigned int* tile_counter;      // zeroed
+    unsigned long long* total;       // count written by the last tile
+    unsigned int* err;
+    // fault injection for the timeout test: this tile never publishes
+    long long skip_publish_tile;
+    unsigned long long wait_ns;
+    uint32_t smem_prog_off, smem_stage_off, smem_out_off, smem_bytes;
+};
+
+size_t pushdown_layout(PushdownArgs& a);
+cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
+
+}  // namespace sel

@@ -1,0 +1,252 @@
+// scan.cuh -- device building blocks of the column scans (sm_103a).
+//
+//  * bulk (TMA) copies of column tiles global -> shared, completed on an
+//    mbarrier (cp.async.bulk ... mbarrier::complete_tx::bytes);
+//  * bounded mbarrier waits (a wait gives up after kWaitNs nanoseconds of
+//    %globaltimer and the caller reports SEL_ERR_TIMEOUT);
+//  * the bit-sliced predicate interpreter: a warp evaluates one compiled
+//    program over a 256-row chunk of a staged tile, each lane producing an
+//    8-bit mask for its 8 rows.
+//
+// Row ownership inside a 256-row chunk starting at tile row c0: lane l owns
+// rows c0 + 4l + i (mask bit i) and c0 + 128 + 4l + i (mask bit 4 + i),
+// i = 0..3.  A 4-byte column is then read with two conflict-free 16-byte
+// shared loads per lane; an 8-byte column with four.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+#include "program.h"
+
+namespace sel {
+
+
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// L2 policy for streamed column data: read once, evict first.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// One bulk copy global -> shared (both 16-byte aligned, bytes % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                         uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// leaf evaluation over the 8 rows of a lane
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void load8x32(uint32_t col_base, uint32_t c0, uint32_t lane, uint32_t (&v)[8]) {
+    const uint32_t p = col_base + c0 * 4u + lane * 16u;
+    const uint4 a = lds128(p);
+    const uint4 b = lds128(p + 512u);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+__device__ __forceinline__ void load8x64(uint32_t col_base, uint32_t c0, uint32_t lane, uint64_t (&v)[8]) {
+    const uint32_t p = col_base + c0 * 8u + lane * 32u;
+    const uint4 a0 = lds128(p), a1 = lds128(p + 16u);
+    const uint4 b0 = lds128(p + 1024u), b1 = lds128(p + 1040u);
+    v[0] = (uint64_t)a0.y << 32 | a0.x; v[1] = (uint64_t)a0.w << 32 | a0.z;
+    v[2] = (uint64_t)a1.y << 32 | a1.x; v[3] = (uint64_t)a1.w << 32 | a1.z;
+    v[4] = (uint64_t)b0.y << 32 | b0.x; v[5] = (uint64_t)b0.w << 32 | b0.z;
+    v[6] = (uint64_t)b1.y << 32 | b1.x; v[7] = (uint64_t)b1.w << 32 | b1.z;
+}
+
+template <typename Pred>
+__device__ __forceinline__ uint32_t mask8(Pred pred) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m |= (pred(i) ? 1u : 0u) << i;
+    return m;
+}
+
+// Evaluates one leaf; the pool pointer may address shared or global memory.
+__device__ __forceinline__ uint32_t eval_leaf(const Instr& in, uint32_t col_base, uint32_t c0, uint32_t lane,
+                                              const uint8_t* pool) {
+    uint32_t m;
+    switch (in.opc) {
+    case OP_RANGE32: {
+        uint32_t v[8];
+        load8x32(col_base, c0, lane, v);
+        const uint32_t lo = in.a, sp = in.b;
+        m = mask8([&](int i) { return v[i] - lo <= sp; });
+        break;
+    }
+    case OP_RANGEF: {
+        uint32_t v[8];
+        load8x32(col_base, c0, lane, v);
+        const float lo = __uint_as_float(in.a), hi = __uint_as_float(in.b);
+        m = mask8([&](int i) {
+            const float x = __uint_as_float(v[i]);
+            return lo <= x && x <= hi;
+        });
+        break;
+    }
+    case OP_RANGE64: {
+        uint64_t v[8];
+        load8x64(col_base, c0, lane, v);
+        const uint64_t lo = *reinterpret_cast<const uint64_t*>(pool + in.off);
+        const uint64_t sp = *reinterpret_cast<const uint64_t*>(pool + in.off + 8);
+        m = mask8([&](int i) { return v[i] - lo <= sp; });
+        break;
+    }
+    case OP_IN32: {
+        uint32_t v[8];
+        load8x32(col_base, c0, lane, v);
+        const uint32_t* vals = reinterpret_cast<const uint32_t*>(pool + in.off);
+        m = 0;
+        for (uint32_t k = 0; k < in.a; ++k) {
+            const uint32_t w = vals[k];
+            m |= mask8([&](int i) { return v[i] == w; });
+        }
+        break;
+    }
+    case OP_INF: {
+        uint32_t v[8];
+        load8x32(col_base, c0, lane, v);
+        const float* vals = reinterpret_cast<const float*>(pool + in.off);
+        m = 0;
+        for (uint32_t k = 0; k < in.a; ++k) {
+            const float w = vals[k];
+            m |= mask8([&](int i) { return __uint_as_float(v[i]) == w; });
+        }
+        break;
+    }
+    case OP_IN64: {
+        uint64_t v[8];
+        load8x64(col_base, c0, lane, v);
+        const uint64_t* vals = reinterpret_cast<const uint64_t*>(pool + in.off);
+        m = 0;
+        for (uint32_t k = 0; k < in.a; ++k) {
+            const uint64_t w = vals[k];
+            m |= mask8([&](int i) { return v[i] == w; });
+        }
+        break;
+    }
+    case OP_BITMAP: {
+        uint32_t v[8];
+        load8x32(col_base, c0, lane, v);
+        const uint32_t* words = reinterpret_cast<const uint32_t*>(pool + in.off);
+        const uint32_t lo = in.a, nbits = in.b;
+        m = mask8([&](int i) {
+            const uint32_t d = v[i] - lo;
+            return d < nbits && ((words[d >> 5] >> (d & 31u)) & 1u);
+        });
+        break;
+    }
+    default:  // OP_CONST
+        m = 0xFFu;
+        break;
+    }
+    return in.neg ? (m ^ 0xFFu) : m;
+}
+
+// Runs a compiled program over one 256-row chunk; returns the lane's 8-bit
+// row mask.  stage_base: shared address of the staged tile; slot_off: byte
+// offset of each slot's column inside the stage.
+__device__ __forceinline__ uint32_t eval_program(const Instr* __restrict__ prog, uint32_t n_instr,
+                                                 const uint8_t* __restrict__ pool, uint32_t stage_base,
+                                                 const uint32_t* slot_off, uint32_t c0, uint32_t lane) {
+    uint32_t top = 0;
+    uint64_t stk = 0;   // up to 8 pending 8-bit masks
+    for (uint32_t pc = 0; pc < n_instr; ++pc) {
+        const Instr in = prog[pc];
+        if (in.opc == OP_AND) {
+            top &= static_cast<uint32_t>(stk) & 0xFFu;
+            stk >>= 8;
+        } else if (in.opc == OP_OR) {
+            top |= static_cast<uint32_t>(stk) & 0xFFu;
+            stk >>= 8;
+        } else {
+            const uint32_t m = eval_leaf(in, stage_base + slot_off[in.slot], c0, lane, pool);
+            stk = (stk << 8) | top;
+            top = m;
+        }
+    }
+    return top;
+}
+
+// Mask of the lane's rows that lie below `valid` rows of the tile.
+__device__ __forceinline__ uint32_t valid_mask(uint32_t c0, uint32_t lane, uint32_t valid) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        m |= (c0 + 4u * lane + i < valid ? 1u : 0u) << i;
+        m |= (c0 + 128u + 4u * lane + i < valid ? 1u : 0u) << (4 + i);
+    }
+    return m;
+}
+
+// Row (within the tile) of mask bit b for lane l of the chunk at c0.
+__device__ __forceinline__ uint32_t bit_row(uint32_t c0, uint32_t lane, uint32_t b) {
+    return c0 + (b >> 2) * 128u + 4u * lane + (b & 3u);
+}
+
+}  // namespace sel

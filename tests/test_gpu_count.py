@@ -1,0 +1,128 @@
+"""Exact COUNT on the GPU (§3.1) against the oracle: bit-exact u64 counts."""
+import numpy as np
+import pytest
+import torch
+
+import datagen as dg
+import oracle
+import paper_1806_08384_b300 as sel
+
+pytestmark = pytest.mark.gpu
+
+TINY_SIZES = [0, 1, 2, 3, 31, 32, 33, 127, 128, 129, 255, 256, 257, 4097, 10_000]
+
+
+@pytest.mark.parametrize("n", TINY_SIZES)
+def test_random_trees_tiny(ctx, dev, n):
+    t = dg.tiny_table(n, seed=n)
+    ot = oracle.OTable.from_table(t)
+    T = sel.Table(t.to(dev).columns)
+    rng = np.random.default_rng(1000 + n)
+    for _ in range(40):
+        tree = dg.random_tree(t, rng, depth=4)
+        p = sel.Predicate(T, tree)
+        assert ctx.count(p, T) == oracle.count(ot, tree), tree
+
+
+def _medium(n=300_001):
+    return dg.gen_table("cfg2", dg.config2_specs(), n, "cuda")
+
+
+@pytest.fixture(scope="module")
+def medium():
+    t = _medium()
+    return t, oracle.OTable.from_table(t), sel.Table(t.columns)
+
+
+@pytest.mark.parametrize("shape", [(256, 2, 1), (512, 3, 2), (2048, 4, 1), (8192, 2, 1), (1024, 6, 3), (0, 0, 0)])
+def test_scan_shapes_config2(ctx, medium, shape):
+    """Several tiles, every pipeline depth, a ragged last tile (n = 300,001)."""
+    t, ot, T = medium
+    ctx.set_scan_shape(*shape)
+    for s in dg.CONFIG2_TARGETS:
+        tree = dg.config2_predicate(s, seed=1)
+        p = sel.Predicate(T, tree)
+        assert ctx.count(p, T) == oracle.count(ot, tree, threads=8)
+
+
+def test_unaligned_columns_take_the_plain_path(ctx, medium):
+    t, ot, _ = medium
+    cols = [dg.Column(c.spec, c.data[1:], c.dictionary) for c in t.columns]   # base + 4/8 bytes
+    T = sel.Table(cols)
+    sub = oracle.OTable([a[1:] for a in ot.arrays], ot.types, ot.dicts)
+    for s in (1e-3, 0.5):
+        tree = dg.config2_predicate(s, seed=2)
+        assert ctx.count(sel.Predicate(T, tree), T) == oracle.count(sub, tree, threads=8)
+
+
+def test_config1_full(ctx, dev):
+    t = dg.config1_table(device=dev)
+    ot = oracle.OTable.from_table(t)
+    T = sel.Table(t.columns)
+    for seed in range(5):
+        tree = dg.config1_predicate(seed)
+        got = ctx.count(sel.Predicate(T, tree), T)
+        assert got == oracle.count(ot, tree)
+        assert got > 0
+
+
+def test_constants_and_async(ctx, medium):
+    t, ot, T = medium
+    n = T.n_rows
+    assert ctx.count(sel.Predicate(T, dg.P_TRUE), T) == n
+    assert ctx.count(sel.Predicate(T, dg.P_FALSE), T) == 0
+    assert ctx.count(sel.Predicate(T, dg.p_or(dg.p_cmp(0, ">=", 0), dg.p_cmp(0, "<", 0))), T) == n
+    out = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    tree = dg.config2_predicate(0.1, seed=3)
+    ctx.count_async(sel.Predicate(T, tree), T, out)
+    torch.cuda.synchronize()
+    assert int(out.item()) == oracle.count(ot, tree, threads=8)
+
+
+def test_large_sets_and_prefixes(ctx, medium):
+    t, ot, T = medium
+    s1 = t.index("s1")
+    k2 = t.index("k2")
+    d = t.columns[s1].dictionary
+    trees = [dg.p_like(s1, d[i][:1].decode()) for i in (0, 3000, 9999)]
+    trees += [dg.p_in(s1, list(range(0, 3000, 7))), dg.p_in(s1, list(range(0, 600, 2)) + [9999])]
+    vals = [int(v) for v in dg.zipf_rank_values(t.columns[k2].spec)[:50]]
+    trees += [dg.p_in(k2, vals), dg.p_not(dg.p_in(k2, vals[:3]))]
+    trees += [dg.p_cmp(t.index("f1"), "<", 1.0), dg.p_in(t.index("f0"), [float(x) for x in ot.arrays[3][:20]])]
+    for tree in trees:
+        assert ctx.count(sel.Predicate(T, tree), T) == oracle.count(ot, tree, threads=8), tree
+
+
+def test_boolean_identities_on_gpu(ctx, medium):
+    """Identities that hold at any size: partition, inclusion-exclusion, complement."""
+    t, ot, T = medium
+    n = T.n_rows
+    A = dg.config2_predicate(0.1, seed=5)
+    B = dg.config2_predicate(0.5, seed=6)
+    c = lambda tr: ctx.count(sel.Predicate(T, tr), T)
+    cA, cB, cAB = c(A), c(B), c(dg.p_and(A, B))
+    assert cA == cAB + c(dg.p_and(A, dg.p_not(B)))
+    assert c(dg.p_or(A, B)) == cA + cB - cAB
+    assert c(dg.p_not(A)) == n - cA
+    assert c(dg.p_not(dg.p_and(A, B))) == c(dg.p_or(dg.p_not(A), dg.p_not(B)))
+
+
+def test_type_mismatch_is_rejected(ctx, medium):
+    t, ot, T = medium
+    p = sel.Predicate(T, dg.p_cmp(0, "<", 5))
+    cols = list(t.columns)
+    cols[0] = dg.Column(dg.ColumnSpec("x", "f32", "normal"), cols[3].data, None)
+    with pytest.raises(sel.SelError) as e:
+        ctx.count(p, sel.Table(cols))
+    assert e.value.status == sel.SEL_ERR_TYPE
+
+
+@pytest.mark.slow
+def test_config2_full_size(ctx, dev):
+    """300M rows, the five target selectivities, exact vs the (threaded) oracle."""
+    t = dg.config2_table(device=dev)
+    T = sel.Table(t.columns)
+    ot = oracle.OTable.from_table(t)
+    for s in dg.CONFIG2_TARGETS:
+        tree = dg.config2_predicate(s)
+        assert ctx.count(sel.Predicate(T, tree), T) == oracle.count(ot, tree, threads=32)

@@ -1,0 +1,134 @@
+"""Selection push-down on the GPU (§3.3, Algorithm 1 Execute) against the
+oracle: identical projected rows, in ascending row order, identical row ids,
+and the maxSize contract (count > max_rows -> SEL_ERR_TOO_LARGE, exact count)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import datagen as dg
+import oracle
+import paper_1806_08384_b300 as sel
+
+pytestmark = pytest.mark.gpu
+THREADS = max(1, min(32, os.cpu_count() or 1))
+
+
+def check_pushdown(ctx, T, ot, tree, proj, max_rows=None, rowids=True):
+    p = sel.Predicate(T, tree)
+    want_ids = oracle.select(ot, tree, threads=THREADS)
+    max_rows = len(want_ids) if max_rows is None else max_rows
+    st, n, cols, ids = ctx.pushdown(p, T, proj, max_rows, rowids=rowids)
+    assert n == len(want_ids), tree
+    if n > max_rows:
+        assert st == sel.SEL_ERR_TOO_LARGE and cols is None
+        return n
+    assert st == sel.SEL_OK
+    if rowids:
+        assert np.array_equal(ids.cpu().numpy(), want_ids)
+    for c, out in zip(proj, cols):
+        assert np.array_equal(out.cpu().numpy(), ot.arrays[c][want_ids]), (tree, c)
+    return n
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 33, 255, 256, 257, 1023, 1025, 4097, 20_000])
+def test_random_trees_tiny(ctx, dev, n):
+    t = dg.tiny_table(n, seed=n + 7)
+    ot = oracle.OTable.from_table(t)
+    T = sel.Table(t.to(dev).columns)
+    rng = np.random.default_rng(77 + n)
+    proj = [0, 1, 2, 3, 4]
+    for _ in range(25):
+        tree = dg.random_tree(t, rng, depth=4)
+        check_pushdown(ctx, T, ot, tree, proj)
+
+
+@pytest.fixture(scope="module")
+def medium():
+    t = dg.gen_table("cfg2", dg.config2_specs(), 1_000_003, "cuda")
+    return t, oracle.OTable.from_table(t), sel.Table(t.columns)
+
+
+def proj_cfg2(t):
+    return [t.index(c) for c in dg.CONFIG2_PROJECTION]
+
+
+@pytest.mark.parametrize("tile_rows", [256, 1024, 4096, 8192])
+def test_config2_selectivities(ctx, medium, tile_rows):
+    t, ot, T = medium
+    ctx.set_scan_shape(tile_rows, 0, 0)
+    for s in dg.CONFIG2_TARGETS:
+        check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=11), proj_cfg2(t))
+
+
+def test_projection_of_non_predicate_columns_and_no_rowids(ctx, medium):
+    t, ot, T = medium
+    tree = dg.p_between(t.index("f0"), 100.0, 2000.0)
+    check_pushdown(ctx, T, ot, tree, [t.index("k2"), t.index("s1"), t.index("f0")], rowids=False)
+    check_pushdown(ctx, T, ot, tree, [], rowids=True)
+
+
+def test_max_rows_contract(ctx, medium):
+    t, ot, T = medium
+    tree = dg.config2_predicate(1e-2, seed=12)
+    n = oracle.count(ot, tree, threads=THREADS)
+    assert n > 10
+    p = sel.Predicate(T, tree)
+    proj = proj_cfg2(t)
+    # exactly at the limit: materialised (Algorithm 1 throws only when count > maxSize)
+    check_pushdown(ctx, T, ot, tree, proj, max_rows=n)
+    # one below: rejected, exact count reported, nothing written past max_rows
+    m = n - 1
+    guard = 64
+    outs = [torch.full((m + guard,), 7, dtype=c.data.dtype, device="cuda") for c in (t.columns[j] for j in proj)]
+    ids = torch.full((m + guard,), -5, dtype=torch.int64, device="cuda")
+    st, cnt, _, _ = ctx.pushdown(p, T, proj, m, out_cols=outs, out_rowids=ids)
+    assert st == sel.SEL_ERR_TOO_LARGE and cnt == n
+    for o in outs:
+        assert bool((o[m:] == 7).all())
+    assert bool((ids[m:] == -5).all())
+    # ratio 0 (the overhead runs of Ch5): only an empty selection is pushed down
+    st, cnt, _, _ = ctx.pushdown(p, T, proj, 0)
+    assert st == sel.SEL_ERR_TOO_LARGE and cnt == n
+    st, cnt, cols, _ = ctx.pushdown(sel.Predicate(T, dg.P_FALSE), T, proj, 0)
+    assert st == sel.SEL_OK and cnt == 0
+    # the written prefix of a rejected push-down is still the start of the true result
+    want = oracle.select(ot, tree, threads=THREADS)
+    assert np.array_equal(ids[:m].cpu().numpy(), want[:m])
+
+
+def test_unaligned_columns(ctx, medium):
+    t, ot, _ = medium
+    cols = [dg.Column(c.spec, c.data[3:], c.dictionary) for c in t.columns]
+    T = sel.Table(cols)
+    sub = oracle.OTable([a[3:] for a in ot.arrays], ot.types, ot.dicts)
+    for s in (1e-3, 0.5):
+        check_pushdown(ctx, T, sub, dg.config2_predicate(s, seed=13), proj_cfg2(t))
+
+
+def test_lookback_wait_times_out_and_context_recovers(ctx, dev):
+    """A tile that never publishes makes its successors' bounded waits run out:
+    the call returns SEL_ERR_TIMEOUT, and the context works afterwards."""
+    t = dg.tiny_table(8 * 1024, seed=3)
+    ot = oracle.OTable.from_table(t)
+    T = sel.Table(t.to(dev).columns)
+    tree = dg.p_cmp(0, "<", 2)
+    p = sel.Predicate(T, tree)
+    ctx.set_scan_shape(1024, 0, 0)
+    ctx.debug_pushdown_fault(2, 50_000_000)          # tile 2 never publishes; waits give up after 50 ms
+    with pytest.raises(sel.SelError) as e:
+        ctx.pushdown(p, T, [0], T.n_rows)
+    assert e.value.status == sel.SEL_ERR_TIMEOUT
+    ctx.debug_pushdown_fault(-1, 0)
+    check_pushdown(ctx, T, ot, tree, [0, 1, 2])
+    assert ctx.count(p, T) == oracle.count(ot, tree)
+
+
+@pytest.mark.slow
+def test_config2_full_size(ctx, dev):
+    t = dg.config2_table(device=dev)
+    T = sel.Table(t.columns)
+    ot = oracle.OTable.from_table(t)
+    for s in (1e-4, 1e-2, 0.5):
+        check_pushdown(ctx, T, ot, dg.config2_predicate(s), proj_cfg2(t))
