@@ -76,6 +76,7 @@ def _load():
         "sel_count_batch_async": (C.c_int, [V, P(V), P(P(sel_table)), C.c_int32, V]),
         "sel_pushdown_async": (C.c_int, [V, V, P(sel_table), P(C.c_int32), C.c_int32, P(V), V, C.c_uint64, V]),
         "sel_ctx_synchronize": (C.c_int, [V]),
+        "sel_pushdown_noalloc": (C.c_int, [V, V, P(sel_table), P(C.c_int32), C.c_int32, P(V), V, C.c_uint64, V, V]),
         "sel_batch_plan_create": (C.c_int, [V, P(V), P(P(sel_table)), C.c_int32, C.c_int32, P(V)]),
         "sel_batch_plan_run": (C.c_int, [V, V, P(C.c_uint64)]),
         "sel_batch_plan_info": (C.c_int, [V, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_float)]),
@@ -350,6 +351,22 @@ class Context:
         if h and h.value and lib is not None:
             lib.sel_ctx_destroy(h)
             self.h = None
+
+
+def pushdown_noalloc(pred: Predicate, table, proj: Sequence[int], max_rows: int, out_cols: List[torch.Tensor],
+                     out_rowids: Optional[torch.Tensor], out_count: torch.Tensor,
+                     out_error: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None):
+    """sel_pushdown_noalloc: the push-down with the library's fixed scratch and
+    caller-owned outputs only (no context, no device allocation); enqueue only."""
+    table = Table.of(table)
+    stream = stream or torch.cuda.current_stream()
+    pc = (C.c_int32 * max(1, len(proj)))(*proj)
+    po = (C.c_void_p * max(1, len(proj)))(*[t.data_ptr() for t in out_cols])
+    _check(lib.sel_pushdown_noalloc(C.c_void_p(stream.cuda_stream), pred.h, table.ref(), pc, len(proj), po,
+                                    C.c_void_p(out_rowids.data_ptr()) if out_rowids is not None else None,
+                                    int(max_rows), C.c_void_p(out_count.data_ptr()),
+                                    C.c_void_p(out_error.data_ptr()) if out_error is not None else None),
+           "sel_pushdown_noalloc")
 
 
 class BatchPlan:
