@@ -54,50 +54,86 @@ def load_peaks():
 # ----------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
-              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
-              "clocks_event_reasons.sw_power_cap"]
+    """SM clock and clock-event reasons sampled every 10 ms through NVML (read
+    only) while the timed region runs."""
+    REASONS = [("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
+               ("hw_power_brake_slowdown", "nvmlClocksEventReasonHwPowerBrakeSlowdown")]
 
     def __init__(self, index: int):
         self.index = index
-        self.rows = []
-        self.proc = None
+        self.samples = []
+        self.reasons = set()
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self._thread = None
 
     def start(self):
+        self.error = None
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + ",".join(self.FIELDS),
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            threading.Thread(target=self._read, daemon=True).start()
-        except OSError:
-            self.proc = None
+            import pynvml as nv
+            nv.nvmlInit()
+            h = nv.nvmlDeviceGetHandleByIndex(self.index)
+            self.max_mhz = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+        except Exception as e:   # fall back to nvidia-smi
+            self.error = f"nvml: {type(e).__name__}: {e}"
+            self._start_smi()
+            return
 
-    def _read(self):
-        for line in self.proc.stdout:
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) == len(self.FIELDS):
-                self.rows.append(parts)
+        def run():
+            while not self._stop.is_set():
+                try:
+                    self.samples.append(float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)))
+                    r = nv.nvmlDeviceGetCurrentClocksEventReasons(h)
+                    for name, const in self.REASONS:
+                        if r & getattr(nv, const, 0):
+                            self.reasons.add(name)
+                except Exception:
+                    pass
+                time.sleep(0.01)
+        self._thread = threading.Thread(target=run, daemon=True)
+        self._thread.start()
+
+    def _start_smi(self):
+        def run():
+            try:
+                p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=clocks.sm,clocks.max.sm,"
+                                      "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                                      "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                                      "--format=csv,noheader,nounits", "-lms", "100"],
+                                     stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except OSError as e:
+                self.error = (self.error or "") + f"; nvidia-smi: {e}"
+                return
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in p.stdout:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) == 6:
+                    try:
+                        self.samples.append(float(parts[0]))
+                        self.max_mhz = float(parts[1])
+                    except ValueError:
+                        pass
+                    for k, v in zip(names, parts[2:]):
+                        if v.lower() == "active":
+                            self.reasons.add(k)
+                if self._stop.is_set():
+                    break
+            p.terminate()
+        self._thread = threading.Thread(target=run, daemon=True)
+        self._thread.start()
+        time.sleep(0.3)   # let nvidia-smi start before the timed region
 
     def stop(self):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            for k, v in zip(names, r[3:]):
-                if v.lower() == "active":
-                    reasons.add(k)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+        self._stop.set()
+        if self._thread:
+            self._thread.join(timeout=2)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unsampled"], "error": self.error}
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": sorted(self.reasons), "samples": len(self.samples)}
 
 
 # ----------------------------------------------------------------------------
@@ -258,7 +294,10 @@ def kernel_source_hash(name):
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, source: str, rows: int):
+def traffic_for(kernel: str, source: str, algorithmic_bytes: float):
+    """DRAM bytes of one launch: the DRAM-to-algorithmic byte ratio measured by
+    ncu on a smaller case of the same kernel (profiles/traffic.json) times this
+    launch's algorithmic bytes; None when the kernel source changed since."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -267,7 +306,7 @@ def traffic_for(kernel: str, source: str, rows: int):
     e = d.get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash(source):
         return None
-    return e["dram_bytes_per_row"] * rows
+    return int(e["traffic_per_algorithmic_byte"] * algorithmic_bytes)
 
 
 # ----------------------------------------------------------------------------
@@ -275,7 +314,7 @@ def traffic_for(kernel: str, source: str, rows: int):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--rows", type=int, default=300_000_000)
@@ -354,7 +393,7 @@ def main():
         ach = kk["bytes"] / (kk["ms"] / 1e3) / 1e9 if kk["ms"] > 0 else 0.0
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic_for(kk["name"], kk["source"], w.n), "kernel": kk["name"],
+                "traffic": traffic_for(kk["name"], kk["source"], kk["bytes"]), "kernel": kk["name"],
                 "algorithmic_bytes_per_launch": int(kk["bytes"]), "avg_launch_ms": round(kk["ms"], 4),
                 "launches_timed": kk["launches"]}
     dominant = max(kernels, key=lambda k: kernels[k]["total_ms"])

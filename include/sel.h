@@ -256,6 +256,15 @@ uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
  * The context stays usable; set skip_tile back to -1 to disarm. */
 sel_status sel_ctx_debug_pushdown_fault(sel_ctx* ctx, int64_t skip_tile, uint64_t wait_ns);
 
+/* Test hook for the tensor-core matrix product behind the learned estimator
+ * (the paper has none): C[M x N] = A[M x K] * B[N x K]^T with A, B row-major
+ * BF16 device matrices (16-byte aligned, K a multiple of 8) and C row-major
+ * FP32 (device, caller-owned), FP32 accumulation, k_splits-way split over K
+ * (1..64).  Enqueued on cuda_stream; *dev_err (device, 4 bytes) becomes
+ * nonzero if a bounded wait inside the kernel gave up. */
+sel_status sel_debug_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int32_t N, int32_t K,
+                               float* C, int32_t k_splits, uint32_t* dev_err);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,7 @@ def _load():
         "sel_ctx_set_scan_shape": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32]),
         "sel_ctx_launch_count": (C.c_uint64, [V]),
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
+        "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -367,6 +368,21 @@ def pushdown_noalloc(pred: Predicate, table, proj: Sequence[int], max_rows: int,
                                     int(max_rows), C.c_void_p(out_count.data_ptr()),
                                     C.c_void_p(out_error.data_ptr()) if out_error is not None else None),
            "sel_pushdown_noalloc")
+
+
+def debug_gemm_bf16(A: torch.Tensor, B: torch.Tensor, k_splits: int = 1) -> torch.Tensor:
+    """C = A @ B.T on the tensor cores (bf16 inputs, fp32 result); for tests."""
+    M, K = A.shape
+    N = B.shape[0]
+    C_ = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    err = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.sel_debug_gemm_bf16(C.c_void_p(torch.cuda.current_stream().cuda_stream), C.c_void_p(A.data_ptr()),
+                                   C.c_void_p(B.data_ptr()), M, N, K, C.c_void_p(C_.data_ptr()), k_splits,
+                                   C.c_void_p(err.data_ptr())), "sel_debug_gemm_bf16")
+    torch.cuda.synchronize()
+    if int(err.item()):
+        raise SelError(SEL_ERR_TIMEOUT, "sel_debug_gemm_bf16", "a bounded wait gave up")
+    return C_
 
 
 class BatchPlan:

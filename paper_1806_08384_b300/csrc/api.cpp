@@ -70,7 +70,8 @@ struct sel_ctx {
     cudaStream_t stream = nullptr;
     int device = 0;
     int n_sm = 0;
-    int max_smem = 0;
+    int max_smem = 0;         // opt-in shared memory per block
+    int max_smem_scan = 0;    // dynamic shared memory available to the scan kernel
     DevBuf counts;            // sel_count / batch staging
     DevBuf err;               // 4 bytes: error flag of the last launches
     DevBuf pd_scratch;        // push-down: tile status | tile counter | total
@@ -190,12 +191,12 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
         probe.blob_bytes = blob_bytes;
         probe.prog_in_smem = blob_bytes <= 48u * 1024u ? 1u : 0u;
         const size_t fixed = scan_layout(probe);
-        if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem || sh.stages < 1) {
+        if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem_scan || sh.stages < 1) {
             set_error("scan: %u programs and %d stages do not fit in shared memory", n_progs, sh.stages);
             return SEL_ERR_UNSUPPORTED;
         }
         if (max_rb > 0) {
-            const size_t per_stage = ((size_t)ctx->max_smem - fixed) / (size_t)sh.stages;
+            const size_t per_stage = ((size_t)ctx->max_smem_scan - fixed) / (size_t)sh.stages;
             const int fit = (int)(per_stage / max_rb) / kChunkRows * kChunkRows;
             if (fit < kChunkRows) {
                 set_error("scan: %d stages of 256 rows x %u bytes do not fit in shared memory", sh.stages, max_rb);
@@ -237,7 +238,7 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
         a.stage_bytes = ((uint32_t)sh.tile_rows * max_rb + 127u) / 128u * 128u;
         a.prog_in_smem = blob_bytes <= 48u * 1024u ? 1u : 0u;
         size_t smem = scan_layout(a);
-        if (smem > (size_t)ctx->max_smem) {
+        if (smem > (size_t)ctx->max_smem_scan) {
             set_error("scan: %zu bytes of shared memory needed (tile_rows %d, stages %d)", smem, sh.tile_rows,
                       sh.stages);
             return SEL_ERR_UNSUPPORTED;
@@ -303,7 +304,7 @@ extern "C" sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out) {
     SEL_CUDA("cudaDeviceGetAttribute", cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev));
     SEL_CUDA("cudaDeviceGetAttribute",
              cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    SEL_CUDA("scan smem attribute", scan_kernel_max_smem(c->max_smem));
+    SEL_CUDA("scan smem attribute", scan_kernel_max_smem(c->max_smem, &c->max_smem_scan));
     sel_status s = c->err.ensure(256, "error flag");
     if (s != SEL_OK) return s;
     SEL_CUDA("cudaMemset", cudaMemset(c->err.p, 0, 256));
@@ -449,13 +450,10 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     a.n_slots = ta.n_slots;
     a.row_bytes = ta.row_bytes;
     a.tma = ta.tma;
-    a.tile_rows = ctx->shape.tile_rows > 0 ? (uint32_t)ctx->shape.tile_rows : 1024u;
-    {   // shrink the tile until its stage and its output staging fit in shared memory
-        uint32_t proj_bytes = dev_out_rowids ? 8u : 0u;
-        for (int32_t j = 0; j < n_proj; ++j) proj_bytes += a.proj_width[j];
-        const size_t fixed = ((size_t)pred->blob_bytes + 127) / 128 * 128 + 1024 + 16 * (size_t)(n_proj + 1);
-        while (a.tile_rows > (uint32_t)kChunkRows &&
-               fixed + (size_t)a.tile_rows * (ta.row_bytes + proj_bytes) > (size_t)ctx->max_smem)
+    a.tile_rows = ctx->shape.tile_rows > 0 ? (uint32_t)std::min(ctx->shape.tile_rows, kPdMaxTileRows) : 1024u;
+    {   // shrink the tile until its stage fits in shared memory
+        const size_t fixed = ((size_t)pred->blob_bytes + 127) / 128 * 128 + 1024;
+        while (a.tile_rows > (uint32_t)kChunkRows && fixed + (size_t)a.tile_rows * ta.row_bytes > (size_t)ctx->max_smem)
             a.tile_rows -= kChunkRows;
     }
     uint32_t off = 0;

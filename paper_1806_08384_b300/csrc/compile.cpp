@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <limits>
+#include <map>
 #include <sstream>
 
 #include "internal.h"
@@ -156,6 +157,11 @@ Leaf lower_leaf(const sel_node& nd, const sel_table& schema, bool neg, Clause& c
     cl.kind = nd.kind;
     cl.op = nd.op;
     cl.negated = neg ? 1 : 0;
+    cl.nnf_neg = neg ? 1 : 0;
+    cl.raw_i0 = nd.i_lo;
+    cl.raw_i1 = nd.i_hi;
+    cl.raw_f0 = nd.f_lo;
+    cl.raw_f1 = nd.f_hi;
     if (type == SEL_F32) {
         if (nd.kind == SEL_N_LIKE) fail(SEL_ERR_TYPE, "LIKE on a float32 column");
         if (nd.kind == SEL_N_CMP) {
@@ -253,6 +259,7 @@ Leaf lower_leaf(const sel_node& nd, const sel_table& schema, bool neg, Clause& c
         if (std::strncmp(c.dict[i], nd.prefix, m) == 0) codes.push_back(i);
     }
     cl.like_count = (int32_t)codes.size();
+    for (i128 x : codes) cl.like_codes.push_back((int32_t)x);
     cl.code_lo = codes.empty() ? 0 : (int32_t)codes.front();
     cl.code_hi = codes.empty() ? -1 : (int32_t)codes.back();
     if (codes.empty()) return make_const(neg);
@@ -403,6 +410,15 @@ struct Compiler {
             return;
         }
         if (e.kind == K_LEAF) {
+            const std::string key = leaf_key(e.leaf);
+            auto done = memo_slot.find(key);
+            if (done != memo_slot.end()) {   // evaluated before: reuse its saved mask
+                Instr ld{};
+                ld.opc = OP_LOAD;
+                ld.a = (uint32_t)done->second;
+                p.instrs.push_back(ld);
+                return;
+            }
             Instr in = e.leaf.ins;
             in.slot = (uint8_t)col_slot[e.leaf.col];
             if (!e.leaf.pool.empty()) {
@@ -413,6 +429,14 @@ struct Compiler {
             }
             p.instrs.push_back(in);
             p.leaves++;
+            if (occurrences[key] > 1 && (int)memo_slot.size() < kMemoSlots) {
+                const int k = (int)memo_slot.size();
+                memo_slot[key] = k;
+                Instr sv{};
+                sv.opc = OP_SAVE;
+                sv.a = (uint32_t)k;
+                p.instrs.push_back(sv);
+            }
             return;
         }
         emit(e.kids[0], p, col_slot);
@@ -422,6 +446,22 @@ struct Compiler {
             in.opc = e.kind == K_AND ? OP_AND : OP_OR;
             p.instrs.push_back(in);
         }
+    }
+
+    // Identity of a lowered leaf: column, operation, negation and constants.
+    static std::string leaf_key(const Leaf& l) {
+        std::string k(reinterpret_cast<const char*>(&l.ins), sizeof(Instr));
+        k += std::to_string(l.col) + ":";
+        k.append(reinterpret_cast<const char*>(l.pool.data()), l.pool.size());
+        return k;
+    }
+
+    std::map<std::string, int> occurrences;   // leaf key -> number of occurrences in the tree
+    std::map<std::string, int> memo_slot;     // leaf key -> memo slot holding its mask
+
+    void count_leaves(const ENode& e) {
+        if (e.kind == K_LEAF) occurrences[leaf_key(e.leaf)]++;
+        for (auto& k : e.kids) count_leaves(k);
     }
 
     static void columns(const ENode& e, std::vector<int>& cols) {
@@ -466,13 +506,14 @@ struct Compiler {
 std::string describe(const Program& p) {
     std::ostringstream o;
     static const char* names[] = {"?", "AND", "OR", "CONST", "RANGE32", "RANGE64", "RANGEF",
-                                  "IN32", "IN64", "INF", "BITMAP"};
+                                  "IN32", "IN64", "INF", "BITMAP", "SAVE", "LOAD"};
     o << "slots:";
     for (size_t s = 0; s < p.slot_col.size(); ++s) o << " " << p.slot_col[s] << "/" << p.slot_width[s];
     o << "\nneed: " << p.need << "\nleaves: " << p.leaves << "\n";
     for (const Instr& in : p.instrs) {
-        o << names[in.opc <= OP_BITMAP ? in.opc : 0];
-        if (in.opc != OP_AND && in.opc != OP_OR) {
+        o << names[in.opc <= OP_LOAD ? in.opc : 0];
+        if (in.opc == OP_SAVE || in.opc == OP_LOAD) o << " m=" << in.a;
+        if (in.opc != OP_AND && in.opc != OP_OR && in.opc != OP_SAVE && in.opc != OP_LOAD) {
             if (in.opc != OP_CONST) o << " slot=" << (int)in.slot;
             o << " neg=" << (int)in.neg;
         }
@@ -576,6 +617,7 @@ extern "C" sel_status sel_compile_predicate(const sel_table* schema, const sel_n
             prog.slot_width.push_back(schema->cols[cols[s]].type == SEL_I64 ? 8u : 4u);
         }
         prog.need = e.need;
+        cp.count_leaves(e);
         cp.emit(e, prog, col_slot);
         if (prog.leaves > SEL_MAX_LEAVES) fail(SEL_ERR_UNSUPPORTED, "more than SEL_MAX_LEAVES leaves");
         if (prog.need > kMaxDepth) fail(SEL_ERR_UNSUPPORTED, "tree needs a deeper evaluation stack than 8");
@@ -644,7 +686,7 @@ void build_blob(const std::vector<const Program*>& progs, const std::vector<std:
         pool.insert(pool.end(), p.pool.begin(), p.pool.end());
         pd.push_back(ProgDesc{(uint32_t)ins.size(), (uint32_t)p.instrs.size(), (uint32_t)(outs.empty() ? i : outs[i]), 0u});
         for (Instr in : p.instrs) {
-            if (in.opc != OP_AND && in.opc != OP_OR && in.opc != OP_CONST) {
+            if (in.opc != OP_AND && in.opc != OP_OR && in.opc != OP_CONST && in.opc != OP_SAVE && in.opc != OP_LOAD) {
                 in.slot = (uint8_t)slot_maps[i][in.slot];
                 in.off += pbase;
             }

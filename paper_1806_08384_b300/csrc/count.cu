@@ -3,17 +3,19 @@
 // SELECT COUNT(*) FROM R WHERE <predicates>), generalised to a batch of
 // programs over up to kMaxTables tables in one persistent launch.
 //
-// Each CTA walks the launch's global tile sequence with stride gridDim.x.
-// Thread 0 keeps `stages` tiles in flight: for a full, 16-byte aligned tile
-// it issues one bulk copy per referenced column into a shared-memory stage
-// and arms the stage's mbarrier with the byte count; any other tile (the
-// ragged last tile of a table, or unaligned columns) is copied by the whole
-// CTA with plain loads once the stage is free.  Every warp then evaluates
-// every program of the tile's table on its 256-row chunks, bit-sliced (one
-// bit per row), and adds popc of the masks to a per-program shared counter;
-// the counters are added to the 64-bit global counts once per CTA.  Column
-// tiles are therefore read from HBM exactly once per launch, whatever the
-// number of programs on the table.
+// Warp roles.  The last warp is the producer: it keeps `stages` tiles in
+// flight -- for a full, 16-byte aligned tile its lane 0 issues one bulk copy
+// per referenced column into a shared-memory stage, completing on the
+// stage's `full` mbarrier; any other tile (the ragged last tile of a table,
+// unaligned columns) is copied by the producer warp with plain loads, which
+// then arrives on `full` itself.  The consumer warps evaluate every program
+// of the tile's table on 256-row chunks, bit-sliced (one bit per row), add
+// popc of the masks to per-program shared counters, and arrive on the
+// stage's `empty` mbarrier; the producer refills a stage once every consumer
+// warp has arrived.  Consumers never wait for each other, and chunk
+// ownership rotates from tile to tile, so tiles with fewer chunks than warps
+// leave no warp idle.  Each column tile is read from HBM exactly once per
+// launch, whatever the number of programs on the table.
 #include "kernels.h"
 #include "scan.cuh"
 
@@ -25,34 +27,59 @@ __device__ __forceinline__ int find_table(const ScanArgs& a, int64_t g) {
     return t;
 }
 
-__device__ __forceinline__ void issue_tile(const ScanArgs& a, int64_t g, uint32_t s, uint8_t* stages,
-                                           uint64_t* full, uint64_t pol) {
-    if (g >= a.total_tiles) return;
+__device__ __forceinline__ uint32_t tile_valid(const ScanArgs& a, const TableArg& T, int64_t g) {
+    const int64_t r0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows);
+    const int64_t left = T.n_rows - r0;
+    return static_cast<uint32_t>(left < static_cast<int64_t>(a.tile_rows) ? left : a.tile_rows);
+}
+
+// Producer warp: fills stage s with tile g (all 32 lanes call this).
+__device__ __forceinline__ void produce_tile(const ScanArgs& a, int64_t g, uint32_t s, uint8_t* stages,
+                                             uint64_t* full, uint64_t pol, uint32_t lane) {
     const TableArg& T = a.t[find_table(a, g)];
     const int64_t r0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows);
-    const bool whole = r0 + a.tile_rows <= T.n_rows;
-    if (T.tma && whole && T.row_bytes > 0) {
-        uint8_t* st = stages + static_cast<size_t>(s) * a.stage_bytes;
-        mbar_arrive_expect_tx(&full[s], a.tile_rows * T.row_bytes);
-        for (uint32_t j = 0; j < T.n_slots; ++j)
-            bulk_g2s(st + T.slot_off[j], T.col[j] + r0 * T.width[j], a.tile_rows * T.width[j], &full[s], pol);
+    const uint32_t valid = tile_valid(a, T, g);
+    uint8_t* st = stages + static_cast<size_t>(s) * a.stage_bytes;
+    if (T.tma && valid == a.tile_rows && T.row_bytes > 0) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(&full[s], a.tile_rows * T.row_bytes);
+            for (uint32_t j = 0; j < T.n_slots; ++j)
+                bulk_g2s(st + T.slot_off[j], T.col[j] + r0 * T.width[j], a.tile_rows * T.width[j], &full[s], pol);
+        }
     } else {
-        mbar_arrive(&full[s]);   // completes the phase; the CTA copies this tile itself
+        for (uint32_t j = 0; j < T.n_slots; ++j) {
+            const uint32_t words = valid * T.width[j] / 4u;
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(T.col[j] + r0 * T.width[j]);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(st + T.slot_off[j]);
+            for (uint32_t i = lane; i < words; i += 32) dst[i] = src[i];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[s]);   // release: the copies above are visible to the waiters
     }
 }
 
 __global__ void __launch_bounds__(kScanThreads) scan_count_kernel(const __grid_constant__ ScanArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, n_warps = blockDim.x >> 5;
+    __shared__ uint32_t s_off[kMaxTables][kMaxSlots];
+    __shared__ uint32_t s_fail;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    constexpr uint32_t W = kScanConsumers / 32;   // consumer warps
     const uint32_t S = a.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + S;
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem + a.cnt_off);
     uint8_t* stages = smem + a.stage_off;
 
     if (tid == 0) {
-        for (uint32_t s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        for (uint32_t s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W);
+        }
         fence_mbar_init();
+        s_fail = 0;
     }
+    for (uint32_t i = tid; i < kMaxTables * kMaxSlots; i += blockDim.x)
+        s_off[i / kMaxSlots][i % kMaxSlots] = a.t[i / kMaxSlots].slot_off[i % kMaxSlots];
     for (uint32_t p = tid; p < a.n_progs; p += blockDim.x) cnt[p] = 0ull;
     const uint8_t* blob = a.blob;
     if (a.prog_in_smem) {
@@ -62,61 +89,84 @@ __global__ void __launch_bounds__(kScanThreads) scan_count_kernel(const __grid_c
         blob = smem + a.prog_off;
     }
     __syncthreads();
-    const ProgDesc* pd = reinterpret_cast<const ProgDesc*>(blob);
-    const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
-    const uint8_t* pool = blob + a.pool_off;
-
     const int64_t G = gridDim.x;
-    const uint64_t pol = policy_evict_first();
-    if (tid == 0)
-        for (uint32_t s = 0; s < S; ++s) issue_tile(a, blockIdx.x + s * G, s, stages, full, pol);
 
-    for (int64_t k = 0;; ++k) {
-        const int64_t g = blockIdx.x + k * G;
-        if (g >= a.total_tiles) break;
-        const uint32_t s = static_cast<uint32_t>(k % S);
-        const uint32_t parity = static_cast<uint32_t>((k / S) & 1);
-        const TableArg& T = a.t[find_table(a, g)];
-        const int64_t r0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows);
-        const uint32_t valid = static_cast<uint32_t>((T.n_rows - r0 < (int64_t)a.tile_rows ? T.n_rows - r0 : (int64_t)a.tile_rows));
-        const bool bulk = T.tma && valid == a.tile_rows && T.row_bytes > 0;
-        const bool ok = mbar_wait_bounded(&full[s], parity);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(a.err, 1u);
-            // let the copies already issued for the next stages land (bounded) before leaving
-            for (uint32_t j = 1; j < S; ++j) {
-                const int64_t kj = k + j;
-                if (blockIdx.x + kj * G >= a.total_tiles) break;
-                mbar_wait_bounded(&full[kj % S], static_cast<uint32_t>((kj / S) & 1));
+    if (warp == W) {
+        // ------------------------------- producer -------------------------------
+        const uint64_t pol = policy_evict_first();
+        uint32_t s = 0, phase = 0;   // stage of tile k and the number of times it was reused, mod 2
+        for (int64_t k = 0;; ++k) {
+            const int64_t g = blockIdx.x + k * G;
+            if (g >= a.total_tiles) break;
+            if (k >= S) {   // wait until every consumer warp released the stage's previous tile
+                const bool ok = mbar_wait_bounded(&empty[s], phase ^ 1u);
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
+                    // consumers waiting for tiles that are never produced give up on their own bound
+                    if (lane == 0) {
+                        atomicOr(a.err, 1u);
+                        atomicOr(&s_fail, 1u);
+                    }
+                    break;
+                }
             }
-            break;   // every thread leaves together
-        }
-        uint8_t* st = stages + static_cast<size_t>(s) * a.stage_bytes;
-        if (!bulk) {
-            for (uint32_t j = 0; j < T.n_slots; ++j) {
-                const uint32_t words = valid * T.width[j] / 4u;
-                const uint32_t* src = reinterpret_cast<const uint32_t*>(T.col[j] + r0 * T.width[j]);
-                uint32_t* dst = reinterpret_cast<uint32_t*>(st + T.slot_off[j]);
-                for (uint32_t i = tid; i < words; i += blockDim.x) dst[i] = src[i];
-            }
-            __syncthreads();
-        }
-        const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
-        const uint32_t st_addr = smem_u32(st);
-        for (uint32_t ch = warp; ch < n_chunks; ch += n_warps) {
-            const uint32_t c0 = ch * kChunkRows;
-            const uint32_t vm = (c0 + kChunkRows <= valid) ? 0xFFu : valid_mask(c0, lane, valid);
-            for (uint32_t p = T.prog_begin; p < T.prog_end; ++p) {
-                const uint32_t m =
-                    eval_program(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, T.slot_off, c0, lane) & vm;
-                const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(m)));
-                if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
+            produce_tile(a, g, s, stages, full, pol, lane);
+            if (++s == S) {
+                s = 0;
+                phase ^= 1u;
             }
         }
-        __syncthreads();   // stage s is free again
-        if (tid == 0) issue_tile(a, g + static_cast<int64_t>(S) * G, s, stages, full, pol);
+    } else {
+        // ------------------------------- consumers ------------------------------
+        const ProgDesc* pd = reinterpret_cast<const ProgDesc*>(blob);
+        const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
+        const uint8_t* pool = blob + a.pool_off;
+        uint32_t rot = 0;   // running chunk count: chunk c of a tile belongs to warp (rot + c) % W
+        uint32_t s = 0, parity = 0;
+        for (int64_t k = 0;; ++k) {
+            const int64_t g = blockIdx.x + k * G;
+            if (g >= a.total_tiles) break;
+            const int ti = find_table(a, g);
+            const TableArg& T = a.t[ti];
+            const uint32_t valid = tile_valid(a, T, g);
+            const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
+            // lane 0 waits for the stage; the warp follows its verdict (one decision per warp)
+            uint32_t okw = 0;
+            if (lane == 0) okw = mbar_wait_bounded(&full[s], parity) ? 1u : 0u;
+            okw = __shfl_sync(0xFFFFFFFFu, okw, 0);
+            __syncwarp();
+            if (!okw) {
+                if (lane == 0) {
+                    atomicOr(a.err, 1u);
+                    atomicOr(&s_fail, 1u);
+                    mbar_wait_bounded(&full[s], parity);   // a copy still in flight lands before we leave
+                }
+                break;
+            }
+            if (*reinterpret_cast<volatile uint32_t*>(&s_fail)) break;
+            const uint32_t st_addr = smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes);
+            const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
+            for (uint32_t ch = first; ch < n_chunks; ch += W) {
+                const uint32_t c0 = ch * kChunkRows;
+                const uint32_t vm = (c0 + kChunkRows <= valid) ? 0xFFu : valid_mask(c0, lane, valid);
+                for (uint32_t p = T.prog_begin; p < T.prog_end; ++p) {
+                    const uint32_t m =
+                        eval_program(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane) & vm;
+                    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(m)));
+                    if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
+                }
+            }
+            rot += n_chunks;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            if (++s == S) {
+                s = 0;
+                parity ^= 1u;
+            }
+        }
     }
     __syncthreads();
+    if (s_fail) return;   // counts are invalid; the error flag is set
+    const ProgDesc* pd = reinterpret_cast<const ProgDesc*>(blob);
     for (uint32_t p = tid; p < a.n_progs; p += blockDim.x)
         if (cnt[p]) atomicAdd(&a.counts[pd[p].out], cnt[p]);
 }
@@ -124,15 +174,19 @@ __global__ void __launch_bounds__(kScanThreads) scan_count_kernel(const __grid_c
 static inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 size_t scan_layout(ScanArgs& a) {
-    a.cnt_off = align_up(8u * a.stages, 16u);
+    a.cnt_off = align_up(16u * a.stages, 16u);   // full[S] | empty[S]
     a.prog_off = align_up(a.cnt_off + 8u * a.n_progs, 16u);
     const uint32_t prog_bytes = a.prog_in_smem ? align_up(a.blob_bytes, 16u) : 0u;
     a.stage_off = align_up(a.prog_off + prog_bytes, 128u);
     return static_cast<size_t>(a.stage_off) + static_cast<size_t>(a.stages) * a.stage_bytes;
 }
 
-cudaError_t scan_kernel_max_smem(int bytes) {
-    return cudaFuncSetAttribute(scan_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+cudaError_t scan_kernel_max_smem(int optin, int* dyn_max) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, scan_count_kernel);
+    if (e != cudaSuccess) return e;
+    *dyn_max = optin - static_cast<int>(fa.sharedSizeBytes);
+    return cudaFuncSetAttribute(scan_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_max);
 }
 
 cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st) {

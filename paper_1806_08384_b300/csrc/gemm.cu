@@ -1,0 +1,193 @@
+// gemm.cu -- BF16 x BF16 -> FP32 matrix product on the 5th-generation tensor
+// cores (tcgen05.mma, accumulator in TMEM), with the fused epilogues the
+// learned estimator's forward and backward passes need:
+//   C[M x N] = A[M x K] * B[N x K]^T      (A and B row-major, K contiguous)
+// One CTA (4 warps) computes a 128 x 256 tile.  K is walked in 64-column
+// blocks: all 128 threads copy the next A and B blocks into the other of two
+// shared-memory stages (16-byte cp.async into the 128-byte-swizzled K-major
+// layout, zero-filled past M, N or K) while thread 0 has the tensor core
+// multiply the current stage (4 MMAs of K = 16) and commits their completion
+// to that stage's mbarrier.  The epilogue reads the tile back from TMEM, one
+// row per thread, 32 columns at a time.  Split-K (gridDim.z > 1) adds partial
+// tiles with FP32 atomics.
+#include <cuda_bf16.h>
+
+#include "gemm.h"
+#include "tc.cuh"
+
+namespace sel {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr uint32_t kStageA = BM * BK * 2;   // 16 KiB
+constexpr uint32_t kStageB = BN * BK * 2;   // 32 KiB
+constexpr uint32_t kStage = kStageA + kStageB;
+
+__device__ __forceinline__ void load_stage(const GemmArgs& g, uint32_t sA, uint32_t sB, int m0, int n0, int k0,
+                                           uint32_t tid) {
+    // A: 128 rows x 8 chunks; B: 256 rows x 8 chunks of 16 bytes
+    for (uint32_t i = tid; i < BM * 8; i += 128) {
+        const uint32_t r = i >> 3, c = i & 7u;
+        const int row = m0 + (int)r, col = k0 + (int)c * 8;
+        const bool ok = row < g.M && col < g.K;
+        const __nv_bfloat16* src = ok ? g.A + (size_t)row * g.lda + col : g.A;
+        cp_async16(sA + sw128_offset(r, c), src, ok ? 16u : 0u);
+    }
+    for (uint32_t i = tid; i < BN * 8; i += 128) {
+        const uint32_t r = i >> 3, c = i & 7u;
+        const int row = n0 + (int)r, col = k0 + (int)c * 8;
+        const bool ok = row < g.N && col < g.K;
+        const __nv_bfloat16* src = ok ? g.B + (size_t)row * g.ldb + col : g.B;
+        cp_async16(sB + sw128_offset(r, c), src, ok ? 16u : 0u);
+    }
+    cp_async_commit();
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ GemmArgs g) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ uint64_t mma_done[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t s_fail;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    // stage s: A tile at base + s * kStage, B tile kStageA bytes after it
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nkb_total = (g.K + BK - 1) / BK;
+    const int per = (nkb_total + (int)gridDim.z - 1) / (int)gridDim.z;
+    const int kb0 = (int)blockIdx.z * per;
+    const int kb1 = min(nkb_total, kb0 + per);
+    const int nkb = kb1 - kb0;
+
+    if (warp == 0) tc_alloc(&tmem_base, 256);
+    if (tid == 0) {
+        mbar_init(&mma_done[0], 1);
+        mbar_init(&mma_done[1], 1);
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = idesc_bf16(BM, BN);
+
+    if (nkb > 0) {
+        load_stage(g, base, base + kStageA, m0, n0, kb0 * BK, tid);
+        for (int i = 0; i < nkb; ++i) {
+            const int s = i & 1;
+            if (i + 1 < nkb) {
+                if (i >= 1) {   // the MMAs of iteration i-1 read the other stage
+                    const bool ok = mbar_wait_bounded(&mma_done[s ^ 1], static_cast<uint32_t>(((i - 1) >> 1) & 1));
+                    if (!ok) atomicOr(&s_fail, 1u);
+                }
+                load_stage(g, base + (s ^ 1) * kStage, base + (s ^ 1) * kStage + kStageA, m0, n0, (kb0 + i + 1) * BK, tid);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            fence_proxy_async();   // make the copied tiles visible to the tensor core
+            __syncthreads();
+            if (s_fail) break;
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc_mma(tmem, sw128_desc(base + s * kStage + 32u * kk),
+                           sw128_desc(base + s * kStage + kStageA + 32u * kk), idesc,
+                           (i > 0 || kk > 0) ? 1u : 0u);
+                tc_commit(&mma_done[s]);
+            }
+        }
+        // all MMAs of this thread are complete when the last commit arrives
+        const int last = nkb - 1;
+        if (!mbar_wait_bounded(&mma_done[last & 1], static_cast<uint32_t>((last >> 1) & 1))) atomicOr(&s_fail, 1u);
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (s_fail) {
+        if (tid == 0) atomicOr(g.err, 1u);
+    } else {
+        const int row = m0 + (int)(warp * 32 + lane);
+        const bool row_ok = row < g.M;
+#pragma unroll 1
+        for (int cc = 0; cc < BN / 32; ++cc) {
+            float f[32];
+            if (nkb > 0) {
+                tc_ld32(tmem + ((warp * 32u) << 16) + (uint32_t)cc * 32u, f);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) f[j] = 0.f;
+            }
+            const int c0 = n0 + cc * 32;
+            if (g.epi == EPI_F32) {
+                if (row_ok)
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = c0 + j;
+                        if (col < g.N) {
+                            float* dst = g.C + (size_t)row * g.ldc + col;
+                            if (gridDim.z > 1) atomicAdd(dst, f[j]);
+                            else *dst = f[j];
+                        }
+                    }
+            } else {
+                // EPI_BIAS_RELU: relu(acc + bias); EPI_DRELU: acc where mask > 0 (plus column sums)
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int col = c0 + j;
+                    float v = f[j];
+                    if (g.epi == EPI_BIAS_RELU) {
+                        v = fmaxf(v + (col < g.N ? g.bias[col] : 0.f), 0.f);
+                    } else if (row_ok && col < g.N) {
+                        const float mk = __bfloat162float(g.mask[(size_t)row * g.ldm + col]);
+                        v = mk > 0.f ? v : 0.f;
+                    }
+                    if (!row_ok) v = 0.f;
+                    f[j] = v;
+                }
+                if (g.epi == EPI_DRELU && g.colsum) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        float s = f[j];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+                        if (lane == 0 && c0 + j < g.N) atomicAdd(&g.colsum[c0 + j], s);
+                    }
+                }
+                if (row_ok) {
+                    if (g.out)
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < g.N) g.out[(size_t)row * g.ldo + c0 + j] = __float2bfloat16_rn(f[j]);
+                    if (g.outT)   // lanes write consecutive rows of the transposed matrix: coalesced
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < g.N) g.outT[(size_t)(c0 + j) * g.ldoT + row] = __float2bfloat16_rn(f[j]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, 256);
+}
+
+size_t gemm_smem_bytes() { return 2 * (size_t)kStage + 1024; }
+
+cudaError_t launch_gemm(const GemmArgs& g, int k_splits, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gemm_smem_bytes());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((g.M + BM - 1) / BM, (g.N + BN - 1) / BN, k_splits < 1 ? 1 : k_splits);
+    tc_gemm_kernel<<<grid, 128, gemm_smem_bytes(), st>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace sel

@@ -29,6 +29,11 @@ struct Clause {
     std::vector<float> fvals;
     int32_t code_lo, code_hi;   // LIKE: matching dictionary codes (range when contiguous)
     int32_t like_count;         // LIKE: number of matching codes
+    // source-level description used by the learned estimator's features
+    int32_t nnf_neg;            // the leaf sits under an odd number of NOTs
+    int64_t raw_i0, raw_i1;     // constants as written (CMP: i0; BETWEEN: i0..i1)
+    float raw_f0, raw_f1;
+    std::vector<int32_t> like_codes;   // LIKE: every matching code
 };
 
 // Host program compiled by sel_compile_predicate.

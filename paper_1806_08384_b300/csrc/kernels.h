@@ -9,7 +9,8 @@ namespace sel {
 
 constexpr int kMaxTables = 8;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device wait
-constexpr int kScanThreads = 256;
+constexpr int kScanConsumers = 256;                 // 8 consumer warps
+constexpr int kScanThreads = kScanConsumers + 32;   // + 1 producer warp
 
 // One table of a scan launch: its referenced columns ("slots"), its tiles in
 // the launch's global tile sequence and the programs evaluated on it.
@@ -42,12 +43,15 @@ struct ScanArgs {
 // Shared-memory bytes needed by a scan launch (and fills the *_off fields).
 size_t scan_layout(ScanArgs& a);
 cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st);
-cudaError_t scan_kernel_max_smem(int bytes);
+// Sets the scan kernel's dynamic shared-memory limit to the opt-in maximum
+// minus its static shared memory, returned in *dyn_max.
+cudaError_t scan_kernel_max_smem(int optin, int* dyn_max);
 
 // ---------------------------------------------------------------------------
 // push-down (stable compaction with decoupled look-back)
 // ---------------------------------------------------------------------------
-constexpr int kPdThreads = 256;
+constexpr int kPdThreads = 128;       // 4 warps: a 1024-row tile is one 256-row chunk per warp
+constexpr int kPdMaxTileRows = 4096;  // at most 4 chunks per warp
 constexpr int kPdMaxProj = 16;
 
 struct PushdownArgs {

@@ -23,7 +23,11 @@ enum Opcode : uint8_t {
     OP_IN64 = 8,      // x == pool64[k], k < a
     OP_INF = 9,       // x == poolf[k], k < a
     OP_BITMAP = 10,   // d = (uint32)(x - a); d < b && bit d of the pool words at off
+    OP_SAVE = 11,     // memo slot a := top of stack (a leaf that occurs again later)
+    OP_LOAD = 12,     // push memo slot a (a repeated leaf, evaluated once)
 };
+
+constexpr int kMemoSlots = 4;      // 8-bit masks kept in one 32-bit register
 
 // 16 bytes; read uniformly by a whole warp.
 struct Instr {

@@ -13,8 +13,8 @@
 // in windows of 32 until it meets an inclusive prefix, then publishes its own
 // inclusive prefix.  Selected rows are gathered into shared memory in row
 // order (projected columns that are predicate columns come from the staged
-// tile, the others are read from HBM for selected rows only) and written out
-// with consecutive threads storing consecutive output rows.  Rows at output
+// tile, the others are read from HBM for selected rows only) and stored
+// straight to their output positions.  Rows at output
 // positions >= max_rows are not written; the count stays exact.
 #include "kernels.h"
 #include "scan.cuh"
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kPdThreads) pushdown_kernel(const __grid_const
     const uint8_t* blob = smem + a.smem_prog_off;
     const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
     const uint8_t* pool = blob + a.pool_off;
-    const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;   // <= 4 per warp (tile_rows <= 8192)
+    const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;   // <= 4 per warp (tile_rows <= 4096)
     const uint32_t st_addr = smem_u32(st);
     uint32_t masks[4];
     uint32_t lane_pre[4];   // rank of the lane's first selected row inside its chunk (A and B halves packed)
@@ -192,61 +192,40 @@ __global__ void __launch_bounds__(kPdThreads) pushdown_kernel(const __grid_const
     if (t == a.n_tiles - 1 && tid == 0 && t > 0) *a.total = excl + tile_cnt;
     if (tile_cnt == 0 || excl >= a.max_rows) return;
 
-    // --- gather the selected rows of the projection into shared memory ---
-    uint8_t* out_stage = smem + a.smem_out_off;
+    if (s_fail) return;
+    // --- write the selected rows straight to their output positions ---
+    // Ranks follow row order, so a warp's stores for one mask bit land in a
+    // short increasing run of output positions.
+    const unsigned long long lim = a.max_rows;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint32_t ch = warp + q * n_warps;
         if (ch >= n_chunks || masks[q] == 0) continue;
         const uint32_t c0 = ch * kChunkRows;
         const uint32_t m = masks[q];
-        uint32_t rankA = s_chunk_pre[ch] + (lane_pre[q] & 0xFFFFu);
-        uint32_t rankB = s_chunk_pre[ch] + (lane_pre[q] >> 16);
+        unsigned long long posA = excl + s_chunk_pre[ch] + (lane_pre[q] & 0xFFFFu);
+        unsigned long long posB = excl + s_chunk_pre[ch] + (lane_pre[q] >> 16);
         for (uint32_t b = 0; b < 8; ++b) {
             if (!((m >> b) & 1u)) continue;
-            const uint32_t r = (b < 4) ? rankA++ : rankB++;
+            const unsigned long long pos = (b < 4) ? posA++ : posB++;
+            if (pos >= lim) continue;
             const uint32_t row = bit_row(c0, lane, b);
             for (uint32_t j = 0; j < a.n_proj; ++j) {
-                const uint32_t w = a.proj_width[j];
-                uint8_t* dst = out_stage + a.proj_stage_off[j] + static_cast<size_t>(r) * w;
                 const int32_t sl = a.proj_slot[j];
-                if (w == 8) {
+                if (a.proj_width[j] == 8) {
                     const uint64_t v = (sl >= 0)
                         ? *reinterpret_cast<const uint64_t*>(st + a.slot_off[sl] + static_cast<size_t>(row) * 8)
                         : __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[j]) + (r0 + row));
-                    *reinterpret_cast<uint64_t*>(dst) = v;
+                    reinterpret_cast<uint64_t*>(a.proj_dst[j])[pos] = v;
                 } else {
                     const uint32_t v = (sl >= 0)
                         ? *reinterpret_cast<const uint32_t*>(st + a.slot_off[sl] + static_cast<size_t>(row) * 4)
                         : __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[j]) + (r0 + row));
-                    *reinterpret_cast<uint32_t*>(dst) = v;
+                    reinterpret_cast<uint32_t*>(a.proj_dst[j])[pos] = v;
                 }
             }
-            if (a.rowids) {
-                reinterpret_cast<long long*>(out_stage + a.proj_stage_off[a.n_proj])[r] =
-                    static_cast<long long>(r0 + row);
-            }
+            if (a.rowids) a.rowids[pos] = static_cast<long long>(r0 + row);
         }
-    }
-    __syncthreads();
-    if (s_fail) return;
-    // --- coalesced write-out of rows [excl, min(excl + tile_cnt, max_rows)) ---
-    const unsigned long long lim = ((unsigned long long)tile_cnt < a.max_rows - excl ? (unsigned long long)tile_cnt : a.max_rows - excl);
-    for (uint32_t j = 0; j < a.n_proj; ++j) {
-        if (a.proj_width[j] == 8) {
-            const uint64_t* src = reinterpret_cast<const uint64_t*>(out_stage + a.proj_stage_off[j]);
-            uint64_t* dst = reinterpret_cast<uint64_t*>(a.proj_dst[j]) + excl;
-            for (uint32_t i = tid; i < lim; i += blockDim.x) dst[i] = src[i];
-        } else {
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(out_stage + a.proj_stage_off[j]);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(a.proj_dst[j]) + excl;
-            for (uint32_t i = tid; i < lim; i += blockDim.x) dst[i] = src[i];
-        }
-    }
-    if (a.rowids) {
-        const long long* src = reinterpret_cast<const long long*>(out_stage + a.proj_stage_off[a.n_proj]);
-        long long* dst = a.rowids + excl;
-        for (uint32_t i = tid; i < lim; i += blockDim.x) dst[i] = src[i];
     }
 }
 
@@ -255,17 +234,9 @@ static inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a
 size_t pushdown_layout(PushdownArgs& a) {
     a.smem_prog_off = 0;
     a.smem_stage_off = align_up(a.blob_bytes, 128u);
-    uint32_t off = a.smem_stage_off + a.tile_rows * a.row_bytes;
-    off = align_up(off, 128u);
-    a.smem_out_off = off;
-    uint32_t o = 0;
-    for (uint32_t j = 0; j < a.n_proj; ++j) {
-        a.proj_stage_off[j] = o;
-        o = align_up(o + a.tile_rows * a.proj_width[j], 16u);
-    }
-    a.proj_stage_off[a.n_proj] = o;   // row ids
-    if (a.rowids) o += a.tile_rows * 8u;
-    a.smem_bytes = off + o;
+    a.smem_out_off = align_up(a.smem_stage_off + a.tile_rows * a.row_bytes, 128u);
+    for (uint32_t j = 0; j <= a.n_proj; ++j) a.proj_stage_off[j] = 0;   // outputs are not staged
+    a.smem_bytes = a.smem_out_off;
     return a.smem_bytes;
 }
 

@@ -215,7 +215,8 @@ __device__ __forceinline__ uint32_t eval_program(const Instr* __restrict__ prog,
                                                  const uint8_t* __restrict__ pool, uint32_t stage_base,
                                                  const uint32_t* slot_off, uint32_t c0, uint32_t lane) {
     uint32_t top = 0;
-    uint64_t stk = 0;   // up to 8 pending 8-bit masks
+    uint64_t stk = 0;    // up to 8 pending 8-bit masks
+    uint32_t memo = 0;   // kMemoSlots saved 8-bit masks of repeated leaves
     for (uint32_t pc = 0; pc < n_instr; ++pc) {
         const Instr in = prog[pc];
         if (in.opc == OP_AND) {
@@ -224,6 +225,12 @@ __device__ __forceinline__ uint32_t eval_program(const Instr* __restrict__ prog,
         } else if (in.opc == OP_OR) {
             top |= static_cast<uint32_t>(stk) & 0xFFu;
             stk >>= 8;
+        } else if (in.opc == OP_SAVE) {
+            const uint32_t sh = 8u * in.a;
+            memo = (memo & ~(0xFFu << sh)) | (top << sh);
+        } else if (in.opc == OP_LOAD) {
+            stk = (stk << 8) | top;
+            top = (memo >> (8u * in.a)) & 0xFFu;
         } else {
             const uint32_t m = eval_leaf(in, stage_base + slot_off[in.slot], c0, lane, pool);
             stk = (stk << 8) | top;

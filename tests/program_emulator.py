@@ -72,7 +72,14 @@ def _leaf_mask(op: str, kv: dict, col: np.ndarray) -> np.ndarray:
 def evaluate(text: str, arrays: List[np.ndarray], n_rows: int) -> np.ndarray:
     slots, prog = parse(text)
     stack = []
+    memo = {}
     for op, kv in prog:
+        if op == "SAVE":
+            memo[kv["m"]] = stack[-1]
+            continue
+        if op == "LOAD":
+            stack.append(memo[kv["m"]])
+            continue
         if op in ("AND", "OR"):
             b, a = stack.pop(), stack.pop()
             stack.append(a & b if op == "AND" else a | b)

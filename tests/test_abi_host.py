@@ -163,3 +163,23 @@ def test_every_single_clause_matches_oracle():
             for tr in (tree, dg.p_not(tree)):
                 got = emu.evaluate(_compile(t, tr).describe(), arrays, n)
                 assert int(got.sum()) == oracle.count(ot, tr), tr
+
+
+def test_repeated_leaves_are_evaluated_once():
+    """A leaf that occurs in several AND groups is saved once and reloaded."""
+    t = dg.gen_table("cfg2", dg.config2_specs(), 3000, "cpu")
+    ot = oracle.OTable.from_table(t)
+    arrays = [c.data.numpy() for c in t.columns]
+    saw_load = False
+    for s in dg.CONFIG2_TARGETS:
+        for seed in range(4):
+            tree = dg.config2_predicate(s, seed=seed)
+            txt = _compile(t, tree).describe()
+            saw_load |= "LOAD m=" in txt
+            got = emu.evaluate(txt, arrays, t.n_rows)
+            assert int(got.sum()) == oracle.count(ot, tree), tree
+    assert saw_load
+    a = dg.p_in(2, [1, 5, 9])
+    txt = _compile(t, dg.p_or(dg.p_and(a, dg.p_cmp(0, "<", 9)), dg.p_and(a, dg.p_cmp(1, ">", 9)),
+                              dg.p_and(dg.p_not(a), dg.p_cmp(5, "=", 9)))).describe()
+    assert txt.count("IN64") == 2 and txt.count("LOAD") == 1     # NOT a is a different leaf
