@@ -577,3 +577,34 @@ def random_tree(table: Table, rng: np.random.Generator, depth=3):
         return p_not(random_tree(table, rng, depth - 1))
     m = int(rng.integers(1, 4))
     return (k, [random_tree(table, rng, depth - 1) for _ in range(m)])
+
+
+# ----------------------------------------------------------------------------
+# predicates of the learned estimator's workload (OR of <= 3 ANDs, <= 6 leaves)
+# ----------------------------------------------------------------------------
+
+def random_dnf_predicate(specs: Sequence[ColumnSpec], rng: np.random.Generator, max_leaves=6, max_groups=3,
+                         prob_not=0.1):
+    """Random shape, random clause kinds and operators, per-clause selectivity
+    log-uniform in [1e-4, 1]."""
+    g = int(rng.integers(1, max_groups + 1))
+    sizes = [1] * g
+    for _ in range(int(rng.integers(0, max_leaves - g + 1))):
+        sizes[int(rng.integers(0, g))] += 1
+    groups = []
+    for k in sizes:
+        cols = [int(c) for c in rng.choice(len(specs), size=min(k, len(specs)), replace=False)]
+        leaves = []
+        for c in cols:
+            p = float(10 ** rng.uniform(-4, 0))
+            leaf = clause_for(specs[c], c, p, rng)
+            if leaf[0] == "between" and rng.random() < 0.5:     # one-sided comparisons too
+                op = ("<", "<=", ">", ">=")[int(rng.integers(0, 4))]
+                leaf = p_cmp(c, op, leaf[2] if op in (">", ">=") else leaf[3])
+            elif leaf[0] == "in" and rng.random() < 0.3:
+                leaf = p_cmp(c, "=" if rng.random() < 0.7 else "<>", leaf[2][0])
+            if rng.random() < prob_not:
+                leaf = p_not(leaf)
+            leaves.append(leaf)
+        groups.append(p_and(*leaves) if len(leaves) > 1 else leaves[0])
+    return p_or(*groups) if len(groups) > 1 else groups[0]

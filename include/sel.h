@@ -256,6 +256,79 @@ uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
  * The context stays usable; set skip_tile back to -1 to disarm. */
 sel_status sel_ctx_debug_pushdown_fault(sel_ctx* ctx, int64_t skip_tile, uint64_t wait_ns);
 
+/* ---------------------------------------------------------------------------
+ * Learned estimator (not in the paper, whose selectivity is always the exact
+ * COUNT of §3.1): a small MLP answers from predicate features and the exact
+ * batched count answers whenever the MLP's predicted uncertainty is above a
+ * threshold, so exactness stays available for every probe.
+ *
+ * Features (a6): per column (the first 8 columns of the table) an empirical
+ * CDF from sample_rows rows drawn with SplitMix64, idx_i = splitmix64(seed +
+ * (col + 1) * 2^40 + i) mod n_rows.  A predicate whose negation normal form
+ * is an OR of at most 3 ANDs of at most 6 leaves in total gets 144 features:
+ * per leaf slot a column one-hot (8), an operator one-hot (= <> < <= > >=
+ * BETWEEN IN LIKE) plus a NOT flag (10), [F_lo, F_hi] = sample fractions
+ * bounding the leaf's value set (2), the AND group one-hot (3) and a present
+ * flag.  Other predicates are "not featurizable" and always answered exactly.
+ * Network (a7, a8): 144 -> 256 -> 256 -> 256 (ReLU) -> 2 = (mu, log sigma^2)
+ * of y = ln(1 + count); BF16 operands with FP32 accumulation on the tensor
+ * cores; Gaussian negative log-likelihood; Adam on FP32 master weights.
+ * ------------------------------------------------------------------------- */
+typedef struct sel_mlp sel_mlp;
+
+typedef struct sel_train_cfg {
+    int32_t epochs;        /* sel_mlp_train: passes over the training predicates          */
+    int32_t batch;         /* rows per minibatch, a positive multiple of 8                */
+    float lr, beta1, beta2, eps;   /* Adam                                                */
+    uint64_t seed;         /* minibatch shuffling                                         */
+    int32_t apply_update;  /* sel_mlp_train_step: 1 = Adam step (gradients are then cleared),
+                              0 = only accumulate gradients (inspect with sel_mlp_get_grads) */
+    int32_t reserved;
+} sel_train_cfg;
+
+/* Builds the CDF tables from `table` (device columns; sample_rows a power of
+ * two in [2, 8192]) and seeded initial weights.  The model keeps no pointer
+ * to the table. */
+sel_status sel_mlp_create(sel_ctx* ctx, const sel_table* table, int32_t sample_rows, uint64_t seed, sel_mlp** out);
+void sel_mlp_free(sel_mlp* m);
+/* a6: features of n predicates into dev_features (device BF16, n x 144,
+ * caller-owned) and, when dev_ok is not NULL, 1/0 featurizable flags (device,
+ * n bytes).  Predicates must be compiled against the model's table schema.
+ * Synchronous. */
+sel_status sel_mlp_featurize(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds, int32_t n, void* dev_features,
+                             uint8_t* dev_ok);
+/* a7: dev_out (device FP32, n x 2) = (mu, raw log-variance) per feature row.
+ * dev_features 16-byte aligned.  Enqueued on the context's stream. */
+sel_status sel_mlp_forward(sel_ctx* ctx, sel_mlp* m, const void* dev_features, int32_t n, float* dev_out);
+/* a8: one minibatch (n rows, a multiple of 8) of features and targets
+ * y = ln(1 + count) (device FP32): gradients of the mean Gaussian NLL, then
+ * an Adam step when cfg->apply_update.  *loss_out = the batch's mean loss.
+ * Synchronous. */
+sel_status sel_mlp_train_step(sel_ctx* ctx, sel_mlp* m, const void* dev_features, const float* dev_y, int32_t n,
+                              const sel_train_cfg* cfg, float* loss_out);
+/* a8 driver: featurizes the n predicates, targets ln(1 + exact_counts[i])
+ * (host), shuffled minibatches for cfg->epochs epochs (non-featurizable
+ * predicates skipped).  *final_loss = mean loss of the last epoch. */
+sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds, const uint64_t* exact_counts,
+                         int64_t n, const sel_train_cfg* cfg, float* final_loss);
+/* a9: est[i] (host) = the exact count of preds[i] over `table` when the
+ * predicate is not featurizable or sigma_i = exp(lv_i / 2) > tau (lv clamped
+ * to [-8, 8]); otherwise max(0, exp(mu_i) - 1).  sigma (host, may be NULL)
+ * gets sigma_i (+inf when not featurizable), used_exact (host, may be NULL)
+ * 1 where the exact batched scan answered.  Synchronous. */
+sel_status sel_mlp_estimate(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds, const sel_table* table,
+                            int32_t n, float tau, double* est, float* sigma, uint8_t* used_exact);
+/* Parameters as one FP32 array (W1 256x144, b1 256, W2 256x256, b2, W3
+ * 256x256, b3, W4 2x256, b4 2; row-major, [out][in]) of sel_mlp_param_count()
+ * floats.  set also clears gradients and Adam state. */
+int64_t sel_mlp_param_count(void);
+sel_status sel_mlp_get_params(const sel_mlp* m, float* host_params, int64_t n_floats);
+sel_status sel_mlp_set_params(sel_ctx* ctx, sel_mlp* m, const float* host_params, int64_t n_floats);
+sel_status sel_mlp_get_grads(const sel_mlp* m, float* host_grads, int64_t n_floats);
+/* Checkpoint: weights, Adam state, step and CDF tables in one binary file. */
+sel_status sel_mlp_save(const sel_mlp* m, const char* path);
+sel_status sel_mlp_load(sel_ctx* ctx, const char* path, sel_mlp** out);
+
 /* Test hook for the tensor-core matrix product behind the learned estimator
  * (the paper has none): C[M x N] = A[M x K] * B[N x K]^T with A, B row-major
  * BF16 device matrices (16-byte aligned, K a multiple of 8) and C row-major

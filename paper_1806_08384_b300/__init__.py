@@ -49,6 +49,16 @@ class sel_node(C.Structure):
                 ("prefix", C.c_char_p)]
 
 
+class TrainCfg(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64), ("apply_update", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+def train_cfg(epochs=5, batch=4096, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, seed=0, apply_update=1) -> TrainCfg:
+    return TrainCfg(epochs, batch, lr, beta1, beta2, eps, seed, apply_update, 0)
+
+
 class SelError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
@@ -85,6 +95,20 @@ def _load():
         "sel_ctx_launch_count": (C.c_uint64, [V]),
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
+        "sel_mlp_create": (C.c_int, [V, P(sel_table), C.c_int32, C.c_uint64, P(V)]),
+        "sel_mlp_free": (None, [V]),
+        "sel_mlp_featurize": (C.c_int, [V, V, P(V), C.c_int32, V, V]),
+        "sel_mlp_forward": (C.c_int, [V, V, V, C.c_int32, V]),
+        "sel_mlp_train_step": (C.c_int, [V, V, V, V, C.c_int32, P(TrainCfg), P(C.c_float)]),
+        "sel_mlp_train": (C.c_int, [V, V, P(V), P(C.c_uint64), C.c_int64, P(TrainCfg), P(C.c_float)]),
+        "sel_mlp_estimate": (C.c_int, [V, V, P(V), P(sel_table), C.c_int32, C.c_float, P(C.c_double),
+                                       P(C.c_float), P(C.c_uint8)]),
+        "sel_mlp_param_count": (C.c_int64, []),
+        "sel_mlp_get_params": (C.c_int, [V, P(C.c_float), C.c_int64]),
+        "sel_mlp_set_params": (C.c_int, [V, V, P(C.c_float), C.c_int64]),
+        "sel_mlp_get_grads": (C.c_int, [V, P(C.c_float), C.c_int64]),
+        "sel_mlp_save": (C.c_int, [V, C.c_char_p]),
+        "sel_mlp_load": (C.c_int, [V, C.c_char_p, P(V)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -421,3 +445,127 @@ class BatchPlan:
         if h and h.value and lib is not None:
             lib.sel_batch_plan_free(h)
             self.h = None
+
+
+# ----------------------------------------------------------------------------
+# learned estimator
+# ----------------------------------------------------------------------------
+
+N_FEATURES = 144
+
+
+class Estimator:
+    """sel_mlp: CDF-sampled features, a BF16 tensor-core MLP and the gated
+    exact fallback (see include/sel.h)."""
+
+    def __init__(self, ctx: "Context", table=None, sample_rows: int = 4096, seed: int = 0, _handle=None):
+        self.ctx = ctx
+        if _handle is not None:
+            self.h = _handle
+            return
+        table = Table.of(table)
+        h = C.c_void_p()
+        _check(lib.sel_mlp_create(ctx.h, table.ref(), sample_rows, seed, C.byref(h)), "sel_mlp_create")
+        self.h = h
+
+    @classmethod
+    def load(cls, ctx: "Context", path: str) -> "Estimator":
+        h = C.c_void_p()
+        _check(lib.sel_mlp_load(ctx.h, path.encode(), C.byref(h)), "sel_mlp_load")
+        return cls(ctx, _handle=h)
+
+    def save(self, path: str):
+        _check(lib.sel_mlp_save(self.h, path.encode()), "sel_mlp_save")
+
+    def featurize(self, preds: Sequence[Predicate], device="cuda"):
+        n = len(preds)
+        feat = torch.empty(n, N_FEATURES, dtype=torch.bfloat16, device=device)
+        ok = torch.empty(n, dtype=torch.uint8, device=device)
+        pa = (C.c_void_p * n)(*[p.h.value for p in preds])
+        _check(lib.sel_mlp_featurize(self.ctx.h, self.h, pa, n, C.c_void_p(feat.data_ptr()),
+                                     C.c_void_p(ok.data_ptr())), "sel_mlp_featurize")
+        return feat, ok
+
+    def forward(self, feat: torch.Tensor) -> torch.Tensor:
+        out = torch.empty(feat.shape[0], 2, dtype=torch.float32, device=feat.device)
+        _check(lib.sel_mlp_forward(self.ctx.h, self.h, C.c_void_p(feat.data_ptr()), feat.shape[0],
+                                   C.c_void_p(out.data_ptr())), "sel_mlp_forward")
+        return out
+
+    def train_step(self, feat: torch.Tensor, y: torch.Tensor, cfg: TrainCfg) -> float:
+        loss = C.c_float()
+        _check(lib.sel_mlp_train_step(self.ctx.h, self.h, C.c_void_p(feat.data_ptr()), C.c_void_p(y.data_ptr()),
+                                      feat.shape[0], C.byref(cfg), C.byref(loss)), "sel_mlp_train_step")
+        return float(loss.value)
+
+    def train(self, preds: Sequence[Predicate], counts, cfg: TrainCfg) -> float:
+        n = len(preds)
+        pa = (C.c_void_p * n)(*[p.h.value for p in preds])
+        ca = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64))
+        loss = C.c_float()
+        _check(lib.sel_mlp_train(self.ctx.h, self.h, pa, ca.ctypes.data_as(C.POINTER(C.c_uint64)), n, C.byref(cfg),
+                                 C.byref(loss)), "sel_mlp_train")
+        return float(loss.value)
+
+    def estimate(self, preds: Sequence[Predicate], table, tau: float):
+        table = Table.of(table)
+        n = len(preds)
+        pa = (C.c_void_p * n)(*[p.h.value for p in preds])
+        est = np.zeros(n, np.float64)
+        sig = np.zeros(n, np.float32)
+        used = np.zeros(n, np.uint8)
+        _check(lib.sel_mlp_estimate(self.ctx.h, self.h, pa, table.ref(), n, float(tau),
+                                    est.ctypes.data_as(C.POINTER(C.c_double)),
+                                    sig.ctypes.data_as(C.POINTER(C.c_float)),
+                                    used.ctypes.data_as(C.POINTER(C.c_uint8))), "sel_mlp_estimate")
+        return est, sig, used.astype(bool)
+
+    def get_params(self) -> np.ndarray:
+        n = int(lib.sel_mlp_param_count())
+        a = np.zeros(n, np.float32)
+        _check(lib.sel_mlp_get_params(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), n), "sel_mlp_get_params")
+        return a
+
+    def get_grads(self) -> np.ndarray:
+        n = int(lib.sel_mlp_param_count())
+        a = np.zeros(n, np.float32)
+        _check(lib.sel_mlp_get_grads(self.h, a.ctypes.data_as(C.POINTER(C.c_float)), n), "sel_mlp_get_grads")
+        return a
+
+    def set_params(self, flat: np.ndarray):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(lib.sel_mlp_set_params(self.ctx.h, self.h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size),
+               "sel_mlp_set_params")
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h and h.value and lib is not None:
+            lib.sel_mlp_free(h)
+            self.h = None
+
+
+PARAM_LAYOUT = [("W1", (256, 144)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
+                ("b3", (256,)), ("W4", (2, 256)), ("b4", (2,))]
+
+
+def unflatten(flat: np.ndarray) -> dict:
+    out, o = {}, 0
+    for name, shape in PARAM_LAYOUT:
+        k = int(np.prod(shape))
+        out[name] = flat[o:o + k].reshape(shape)
+        o += k
+    return out
+
+
+def flatten(params: dict) -> np.ndarray:
+    return np.concatenate([np.asarray(params[name], np.float32).ravel() for name, _ in PARAM_LAYOUT])
+
+
+def count_many(ctx: "Context", preds: Sequence[Predicate], table, chunk: int = 2048) -> List[int]:
+    """Exact counts of many predicates over one table, in batched launches of `chunk` probes."""
+    T = Table.of(table)
+    out = []
+    for i in range(0, len(preds), chunk):
+        part = list(preds[i:i + chunk])
+        out += BatchPlan(ctx, part, [T] * len(part), autotune=False).run()
+    return out

@@ -338,6 +338,10 @@ extern "C" sel_status sel_ctx_set_scan_shape(sel_ctx* c, int32_t tile_rows, int3
 
 extern "C" uint64_t sel_ctx_launch_count(const sel_ctx* c) { return c ? c->launches : 0; }
 
+namespace sel {
+cudaStream_t ctx_stream(sel_ctx* c) { return c->stream; }
+}
+
 extern "C" sel_status sel_ctx_debug_pushdown_fault(sel_ctx* c, int64_t skip_tile, uint64_t wait_ns) {
     if (!c) {
         set_error("sel_ctx_debug_pushdown_fault: ctx is NULL");

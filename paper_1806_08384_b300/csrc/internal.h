@@ -72,3 +72,8 @@ void build_blob(const std::vector<const sel::Program*>& progs, const std::vector
 
 // Uploads the single-program blob of a predicate (first use).
 sel_status pred_upload(const sel_pred* p);
+
+namespace sel {
+// The CUDA stream a context is bound to.
+cudaStream_t ctx_stream(sel_ctx* ctx);
+}

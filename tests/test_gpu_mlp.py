@@ -1,0 +1,146 @@
+"""The learned estimator on the GPU against its CPU oracle (oracle/mlp.py).
+
+Features are compared bit for bit (after the oracle's values are rounded to
+BF16 like the GPU's); the forward pass, the gradients of the Gaussian NLL and
+the Adam step within the tolerance the arithmetic allows: FP32 accumulation
+in a different order plus BF16 rounding points that may flip by one BF16 ulp,
+so |gpu - oracle| <= 2e-2 * (1 + |oracle|) element-wise for outputs and
+<= 2e-2 * max|oracle| per tensor for gradients.  Every exact fallback of the
+gate equals the exact count."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import datagen as dg
+from oracle import mlp as om
+import paper_1806_08384_b300 as sel
+from paper_1806_08384_b300 import baselines
+
+pytestmark = pytest.mark.gpu
+M = 4096
+SEED = 20180612
+
+
+@pytest.fixture(scope="module")
+def setup():
+    t = dg.gen_table("cfg2", dg.config2_specs(), 400_000, "cuda")
+    T = sel.Table(t.columns)
+    ctx = sel.Context()
+    est = sel.Estimator(ctx, T, sample_rows=M, seed=SEED)
+    cdfs = [om.CDF(c.data.cpu().numpy(), SEED, i, M) for i, c in enumerate(t.columns)]
+    dicts = [c.dictionary for c in t.columns]
+    rng = np.random.default_rng(7)
+    trees = [dg.random_dnf_predicate(dg.config2_specs(), rng) for _ in range(600)]
+    trees += [dg.config2_predicate(s, seed=k) for s in dg.CONFIG2_TARGETS for k in range(3)]
+    trees += [dg.p_and(dg.p_or(dg.p_cmp(0, "<", 5), dg.p_cmp(1, ">", 7)), dg.p_cmp(3, "<", 1.0)),   # not DNF
+              dg.p_or(*[dg.p_cmp(i % 8, ">=", 0) for i in range(4)])]                              # 4 groups
+    return t, T, ctx, est, cdfs, dicts, trees
+
+
+def test_features_bit_exact(setup):
+    t, T, ctx, est, cdfs, dicts, trees = setup
+    preds = [sel.Predicate(T, tr) for tr in trees]
+    feat, ok = est.featurize(preds)
+    got = feat.float().cpu().numpy()
+    okh = ok.cpu().numpy().astype(bool)
+    for i, tr in enumerate(trees):
+        f, fok = om.featurize(tr, cdfs, dicts)
+        assert okh[i] == fok, tr
+        assert np.array_equal(got[i], om.bf16_round(f)), (tr, np.nonzero(got[i] != om.bf16_round(f)))
+    assert okh[:600].all()                   # every random OR-of-ANDs has a feature form
+    assert not okh[-1] and not okh[-2]       # nested shapes and 4 groups have none
+
+
+def _features(setup, n):
+    t, T, ctx, est, cdfs, dicts, trees = setup
+    preds = [sel.Predicate(T, tr) for tr in trees[:n]]
+    feat, ok = est.featurize(preds)
+    return feat, feat.float().cpu().numpy()
+
+
+def test_forward_matches_oracle(setup):
+    est = setup[3]
+    P = om.init_params(5)
+    rng = np.random.default_rng(1)
+    for k in ("b1", "b2", "b3", "b4"):
+        P[k] = (rng.standard_normal(P[k].shape) * 0.05).astype(np.float32)
+    est.set_params(sel.flatten(P))
+    feat, X = _features(setup, 600)
+    out = est.forward(feat).cpu().numpy()
+    ref = om.forward(P, X)["out"]
+    assert np.all(np.abs(out - ref) <= 2e-2 * (1 + np.abs(ref))), float(np.abs(out - ref).max())
+
+
+def test_gradients_and_adam_match_oracle(setup):
+    est = setup[3]
+    P = om.init_params(11)
+    est.set_params(sel.flatten(P))
+    feat, X = _features(setup, 512)
+    y = np.log1p(np.random.default_rng(2).integers(0, 10 ** 6, 512)).astype(np.float32)
+    yd = torch.from_numpy(y).cuda()
+    loss = est.train_step(feat, yd, sel.train_cfg(apply_update=0))
+    ref_loss, G = om.loss_and_grads(P, X, y)
+    assert abs(loss - ref_loss) <= 2e-2 * (1 + abs(ref_loss))
+    g = sel.unflatten(est.get_grads())
+    for k in G:
+        scale = max(float(np.abs(G[k]).max()), 1e-12)
+        assert float(np.abs(g[k] - G[k]).max()) <= 2e-2 * scale, k
+    # Adam on the GPU's own gradients (a fresh gradient of the same batch)
+    est.set_params(sel.flatten(P))
+    est.train_step(feat, yd, sel.train_cfg(apply_update=0))
+    g_gpu = sel.unflatten(est.get_grads())
+    est.set_params(sel.flatten(P))
+    est.train_step(feat, yd, sel.train_cfg(lr=1e-3, apply_update=1))
+    after = sel.unflatten(est.get_params())
+    Pm = {k: v.copy() for k, v in P.items()}
+    Mo = {k: np.zeros(v.shape) for k, v in P.items()}
+    Vo = {k: np.zeros(v.shape) for k, v in P.items()}
+    om.adam_step(Pm, g_gpu, Mo, Vo, t=1, lr=1e-3)
+    for k in P:
+        diff = np.abs(after[k] - Pm[k])
+        # the sign of a tiny gradient may differ between two runs (atomic sums): allow <= 0.5 % of entries
+        assert np.mean(diff > 1e-6) <= 5e-3, k
+
+
+def test_training_versus_the_independence_estimate(setup):
+    t, T, ctx, est, cdfs, dicts, _ = setup
+    rng = np.random.default_rng(3)
+    trees = [dg.random_dnf_predicate(dg.config2_specs(), rng) for _ in range(24_000)]
+    preds = [sel.Predicate(T, tr) for tr in trees]
+    counts = np.array(sel.count_many(ctx, preds, T), dtype=np.uint64)
+    n_train = 20_000
+    model = sel.Estimator(ctx, T, sample_rows=M, seed=SEED)
+    loss = model.train(preds[:n_train], counts[:n_train], sel.train_cfg(epochs=12, batch=512, lr=2e-3, seed=1))
+    assert math.isfinite(loss)
+    test_p, test_c = preds[n_train:], counts[n_train:]
+    feat, ok = model.featurize(test_p)
+    out = model.forward(feat).cpu().numpy()
+    okm = ok.cpu().numpy().astype(bool)
+    q_mlp = om.q_error(np.expm1(out[:, 0]), test_c)[okm]
+    ind = baselines.independence_selectivity(feat.float().cpu().numpy()) * T.n_rows
+    q_ind = om.q_error(ind, test_c)[okm]
+    print(f"q-error p50/p95: mlp {np.median(q_mlp):.3f}/{np.percentile(q_mlp, 95):.3f}  "
+          f"independence {np.median(q_ind):.3f}/{np.percentile(q_ind, 95):.3f}  final loss {loss:.4f}")
+    assert np.median(q_mlp) <= 1.5 * np.median(q_ind)
+    assert np.percentile(q_mlp, 95) <= np.percentile(q_ind, 95)
+
+
+def test_gate_exact_fallback_and_checkpoint(setup, tmp_path):
+    t, T, ctx, est, cdfs, dicts, trees = setup
+    preds = [sel.Predicate(T, tr) for tr in trees[:200]] + [sel.Predicate(T, trees[-1])]
+    exact = np.array(sel.count_many(ctx, preds, T), dtype=np.float64)
+    e0, s0, u0 = est.estimate(preds, T, tau=0.0)
+    assert u0.all() and np.array_equal(e0, exact)
+    e1, s1, u1 = est.estimate(preds, T, tau=float("inf"))
+    assert u1[-1] and not u1[:-1].any()             # the last one has no feature form
+    assert e1[-1] == exact[-1]
+    tau = float(np.median(s1[:-1]))
+    e2, s2, u2 = est.estimate(preds, T, tau=tau)
+    assert np.array_equal(e2[u2], exact[u2]) and np.all(s2[:-1][u2[:-1]] > tau)
+    path = str(tmp_path / "m.bin")
+    est.save(path)
+    again = sel.Estimator.load(ctx, path)
+    feat, _ = est.featurize(preds)
+    assert torch.equal(est.forward(feat), again.forward(feat))
