@@ -137,10 +137,16 @@ class Table:
 _ZIPF_CACHE = {}
 
 
+_PMF_CACHE = {}
+
+
 def zipf_pmf(n_values: int, s: float) -> np.ndarray:
-    """P(k) proportional to k^-s for k = 1..n_values (float64)."""
-    w = np.arange(1, n_values + 1, dtype=np.float64) ** (-s)
-    return w / w.sum()
+    """P(k) proportional to k^-s for k = 1..n_values (float64), cached."""
+    key = (n_values, s)
+    if key not in _PMF_CACHE:
+        w = np.arange(1, n_values + 1, dtype=np.float64) ** (-s)
+        _PMF_CACHE[key] = w / w.sum()
+    return _PMF_CACHE[key]
 
 
 def zipf_cdf(n_values: int, s: float) -> np.ndarray:
@@ -153,8 +159,18 @@ def zipf_cdf(n_values: int, s: float) -> np.ndarray:
     return _ZIPF_CACHE[key]
 
 
+_RANK_CACHE = {}
+
+
 def zipf_rank_values(spec: ColumnSpec) -> np.ndarray:
-    """Map 0-based Zipf rank -> stored value for a zipf / dict column."""
+    """Map 0-based Zipf rank -> stored value for a zipf / dict column (cached)."""
+    key = (spec.type, spec.name, spec.n_values, spec.dict_seed, spec.permute)
+    if key not in _RANK_CACHE:
+        _RANK_CACHE[key] = _zipf_rank_values(spec)
+    return _RANK_CACHE[key]
+
+
+def _zipf_rank_values(spec: ColumnSpec) -> np.ndarray:
     if spec.type == "i64":
         # int64 key domain: rank k (1-based) -> splitmix64(k) as signed int64
         ks = np.arange(1, spec.n_values + 1, dtype=np.uint64)
@@ -429,9 +445,10 @@ def clause_for(spec: ColumnSpec, col: int, p: float, rng: np.random.Generator, k
             return p_like(col, pick.decode())
         vals = zipf_rank_values(spec)
         pmf = zipf_pmf(spec.n_values, spec.s)
-        # ranks r..r+4 with 5 * pmf(r) ~ p
+        # ranks r..r+4 with 5 * pmf(r) ~ p (pmf is decreasing)
         target = p / 5.0
-        r = int(np.searchsorted(-pmf, -target))
+        r = int(np.searchsorted(pmf[::-1], target, side="left"))
+        r = spec.n_values - r
         r = min(max(r - 2, 0), max(spec.n_values - 5, 0))
         ranks = [min(r + j, spec.n_values - 1) for j in range(5)]
         return p_in(col, [int(vals[k]) for k in ranks])
@@ -595,6 +612,15 @@ def random_dnf_predicate(specs: Sequence[ColumnSpec], rng: np.random.Generator, 
     for k in sizes:
         cols = [int(c) for c in rng.choice(len(specs), size=min(k, len(specs)), replace=False)]
         leaves = []
+        if k >= 2 and rng.random() < 0.4:
+            # two one-sided comparisons on one ordered column, as in the paper's
+            # "B < y1 AND B > y2" (§1.1): correlated clauses independence gets wrong
+            c = int(rng.choice([i for i, sp in enumerate(specs) if sp.type in ("i32", "i64", "f32", "date")
+                                and sp.dist != "zipf"]))
+            lo_leaf = clause_for(specs[c], c, float(10 ** rng.uniform(-3, math.log10(0.5))), rng)
+            a, b = lo_leaf[2], lo_leaf[3]
+            leaves += [p_cmp(c, ">=" if rng.random() < 0.5 else ">", a), p_cmp(c, "<=" if rng.random() < 0.5 else "<", b)]
+            cols = [x for x in cols if x != c][: k - 2]
         for c in cols:
             p = float(10 ** rng.uniform(-4, 0))
             leaf = clause_for(specs[c], c, p, rng)

@@ -268,8 +268,11 @@ sel_status sel_ctx_debug_pushdown_fault(sel_ctx* ctx, int64_t skip_tile, uint64_
  * is an OR of at most 3 ANDs of at most 6 leaves in total gets 144 features:
  * per leaf slot a column one-hot (8), an operator one-hot (= <> < <= > >=
  * BETWEEN IN LIKE) plus a NOT flag (10), [F_lo, F_hi] = sample fractions
- * bounding the leaf's value set (2), the AND group one-hot (3) and a present
- * flag.  Other predicates are "not featurizable" and always answered exactly.
+ * bounding the leaf's value set (2), the AND group one-hot (3) and the leaf's
+ * log selectivity ln(max(p, 1/(2m))) / ln(2m) with p = F_hi - F_lo (its
+ * complement for <> and for a negated leaf).  Other predicates are "not
+ * featurizable" and always answered exactly.  sel_mlp_train starts an
+ * untrained model's output biases at the targets' mean and log-variance.
  * Network (a7, a8): 144 -> 256 -> 256 -> 256 (ReLU) -> 2 = (mu, log sigma^2)
  * of y = ln(1 + count); BF16 operands with FP32 accumulation on the tensor
  * cores; Gaussian negative log-likelihood; Adam on FP32 master weights.

@@ -12,7 +12,10 @@ surrogate computes so that the GPU kernels can be checked against it:
   an OR of <= 3 ANDs of leaves, <= 6 leaves, on columns 0..7.  Each leaf
   fills a 24-float slot: column one-hot (8), operator one-hot (10: = <> < <=
   > >= BETWEEN IN LIKE, NOT), [F_lo, F_hi] from the CDF, group one-hot (3),
-  present flag.  F values are sample counts / m in float32;
+  and the leaf's log selectivity from the sample, ln(max(p, 1/(2m))) /
+  ln(2m) in [-1, 0], where p = F_hi - F_lo, complemented for <> and for a
+  negated leaf.  F values are sample counts / m in float32; the log term is
+  evaluated in float64 and rounded to float32;
 * an MLP 144 -> 256 -> 256 -> 256 -> 2 (ReLU) giving (mu, log sigma^2) of
   y = ln(1 + count), trained with the Gaussian negative log-likelihood and
   Adam.  BF16 rounding (round to nearest even) is applied where the GPU
@@ -144,6 +147,15 @@ def leaf_bounds(leaf, cdf: CDF, dictionary=None) -> Tuple[float, float]:
     return 0.0, cdf.frac(min(c, cdf.m))
 
 
+def log_selectivity(lo: float, hi: float, ne: bool, neg: bool, m: int) -> float:
+    p = max(float(hi) - float(lo), 0.0)
+    if ne:
+        p = 1.0 - p
+    if neg:
+        p = 1.0 - p
+    return float(np.float32(math.log(max(p, 0.5 / m)) / math.log(2.0 * m)))
+
+
 def op_index(leaf) -> int:
     k = leaf[0]
     if k == "cmp":
@@ -171,7 +183,7 @@ def featurize(tree, cdfs: Sequence[CDF], dicts) -> Tuple[np.ndarray, bool]:
             f[o + 18] = lo
             f[o + 19] = hi
             f[o + 20 + gi] = 1.0
-            f[o + 23] = 1.0
+            f[o + 23] = log_selectivity(lo, hi, leaf[0] == "cmp" and leaf[2] == "<>", neg, cdfs[col].m)
             s += 1
     return f, True
 

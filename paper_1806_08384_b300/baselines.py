@@ -37,7 +37,7 @@ def independence_selectivity(features: np.ndarray) -> np.ndarray:
         groups = {}
         for s in range(N_SLOTS):
             slot = f[i, s]
-            if slot[23] < 0.5:
+            if slot[:8].max() < 0.5:     # unused slot (no column)
                 continue
             p = max(0.0, slot[19] - slot[18])
             if slot[8 + 1] > 0.5:        # <>: complement of the equality mass

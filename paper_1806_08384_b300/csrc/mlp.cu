@@ -8,7 +8,7 @@
 //  * a6 features: per-column empirical CDFs from a SplitMix64 sample of rows
 //    (sorted order keys), and for each predicate in OR-of-ANDs form up to six
 //    24-float clause slots (column / operator / group one-hots, NOT flag,
-//    [F_lo, F_hi] from the CDF).
+//    [F_lo, F_hi] from the CDF, the leaf's log selectivity).
 //  * a7 forward: 144 -> 256 -> 256 -> 256 on the tensor cores (gemm.cu, BF16
 //    operands, FP32 accumulation in TMEM, bias + ReLU fused), and the 256 -> 2
 //    head (mu and log sigma^2 of y = ln(1 + count)) on the CUDA cores.
@@ -160,13 +160,19 @@ __global__ void featurize_kernel(const FeatClause* cl, const uint64_t* set_keys,
             hi = frac(min(cnt, m));
         }
         }
+        // log selectivity of the leaf from the sample, in [-1, 0]: ln(max(p, 1/(2m))) / ln(2m),
+        // p = hi - lo, complemented for <> and for a negated leaf (evaluated in double)
+        double p = fmax((double)hi - (double)lo, 0.0);
+        if (c.opi == 1) p = 1.0 - p;
+        if (c.neg) p = 1.0 - p;
+        const float ls = (float)(log(fmax(p, 0.5 / (double)m)) / log(2.0 * (double)m));
         f[c.col] = 1.f;
         f[8 + c.opi] = 1.f;
         f[17] = c.neg ? 1.f : 0.f;
         f[18] = lo;
         f[19] = hi;
         f[20 + c.group] = 1.f;
-        f[23] = 1.f;
+        f[23] = ls;
     }
     __nv_bfloat16* dst = feat + t * kSlot;   // slot s of predicate p starts at (p * 6 + s) * 24
 #pragma unroll
@@ -796,6 +802,19 @@ extern "C" sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* co
     MLP_TRY(cuda_ok(cudaMalloc(&idx.p, usable.size() * 4), "sel_mlp_train"));
     MLP_TRY(cuda_ok(cudaMalloc(&xb.p, (size_t)cfg->batch * kFeat * 2), "sel_mlp_train"));
     MLP_TRY(cuda_ok(cudaMalloc(&yb.p, (size_t)cfg->batch * 4), "sel_mlp_train"));
+    if (m->step == 0) {
+        // start the head at the targets' mean and log-variance (an untrained model)
+        double s1 = 0.0, s2 = 0.0;
+        for (int32_t i : usable) {
+            s1 += yh[(size_t)i];
+            s2 += (double)yh[(size_t)i] * yh[(size_t)i];
+        }
+        const double mean = s1 / (double)usable.size();
+        const double var = std::max(s2 / (double)usable.size() - mean * mean, 1e-4);
+        const float b4[2] = {(float)mean, (float)std::log(var)};
+        MLP_TRY(cuda_ok(cudaMemcpyAsync(m->p + oB4, b4, 8, cudaMemcpyHostToDevice, st), "sel_mlp_train"));
+        MLP_TRY(cuda_ok(cudaStreamSynchronize(st), "sel_mlp_train"));
+    }
     std::mt19937_64 rng(cfg->seed);
     const int64_t steps = (int64_t)usable.size() / cfg->batch;
     double last = 0.0;

@@ -21,7 +21,7 @@ def test_from_features():
     # group 0: two leaves with masses 0.5 and 0.2; group 1: one negated leaf of mass 0.9
     for s, (lo, hi, g, neg) in enumerate([(0.25, 0.75, 0, 0), (0.0, 0.2, 0, 0), (0.0, 0.9, 1, 1)]):
         o = s * 24
-        f[0, o + 23] = 1
+        f[0, o + s] = 1                      # column one-hot
         f[0, o + 18], f[0, o + 19] = lo, hi
         f[0, o + 20 + g] = 1
         f[0, o + 17] = neg
