@@ -10,7 +10,12 @@ Execute for one relation, with every probe of the pass):
       autotuned shape) -- a2 is the same kernel with one program;
   a3  maxSize = floor(n * 0.05): probes above it are not pushed down;
   a4  push-down (fused count + stable compaction) of 4 projected columns for
-      every probe at or under maxSize.
+      every probe at or under maxSize;
+  a6-a9  the learned estimator on the same table: features and the tensor-core
+      forward pass of 4096 held-out probes, the uncertainty gate, and one
+      training minibatch (the model is trained before the timed region on
+      exact counts from the count kernel; the gate's exact fallback is the a5
+      scan, timed separately as exact_ms_per_estimate).
 value = algorithmic bytes of all scans of a step / device time of the step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -217,6 +222,104 @@ class OurStep:
         return counts, accepted, d2h
 
 
+def q_error(est, true):
+    e = np.maximum(np.asarray(est, np.float64), 1.0)
+    t = np.maximum(np.asarray(true, np.float64), 1.0)
+    return np.maximum(e / t, t / e)
+
+
+class Surrogate:
+    """a6-a9 on the same table: the learned estimator, trained before the timed
+    region on exact counts from the count kernel (a5), then inside every timed
+    step: featurize + forward of a batch of probes, the gate decision, and one
+    training minibatch.  The gate's exact fallback is the batched scan of a5;
+    its cost per estimate is timed separately."""
+
+    def __init__(self, step: "OurStep", n_train=20_000, n_eval=4096, sample_rows=4096):
+        sel, T, ctx = step.sel, step.T, step.ctx
+        self.sel, self.T, self.ctx = sel, T, ctx
+        rng = np.random.default_rng(dg.mix_seed("bench_estimator"))
+        specs = dg.config2_specs()
+        trees = [dg.random_dnf_predicate(specs, rng) for _ in range(n_train + n_eval)]
+        preds = [sel.Predicate(T, t) for t in trees]
+        t0 = time.perf_counter()
+        counts = np.array(sel.count_many(ctx, preds, T), dtype=np.uint64)
+        self.label_s = time.perf_counter() - t0
+        self.model = sel.Estimator(ctx, T, sample_rows=sample_rows, seed=dg.MASTER_SEED)
+        self.cfg = sel.train_cfg(epochs=40, batch=256, lr=1e-3, seed=1)
+        t0 = time.perf_counter()
+        self.final_loss = self.model.train(preds[:n_train], counts[:n_train], self.cfg)
+        self.train_s = time.perf_counter() - t0
+        self.n_train = n_train
+        self.eval_preds, self.eval_counts = preds[n_train:], counts[n_train:]
+        feat, ok = self.model.featurize(self.eval_preds)
+        out = self.model.forward(feat).cpu().numpy()
+        okm = ok.cpu().numpy().astype(bool)
+        sig = np.exp(0.5 * np.clip(out[:, 1], -8, 8))
+        self.tau = float(np.median(sig[okm]))
+        acc = okm & (sig <= self.tau)
+        q = q_error(np.expm1(out[:, 0]), self.eval_counts)
+        from paper_1806_08384_b300 import baselines
+        ind = baselines.independence_selectivity(feat.float().cpu().numpy()) * T.n_rows
+        qi = q_error(ind, self.eval_counts)
+        self.quality = {
+            "q_error_p50": round(float(np.median(q[okm])), 3), "q_error_p95": round(float(np.percentile(q[okm], 95)), 3),
+            "gated_tau": round(self.tau, 4), "gated_answered_fraction": round(float(acc.mean()), 3),
+            "gated_q_error_p50": round(float(np.median(q[acc])), 3),
+            "gated_q_error_p95": round(float(np.percentile(q[acc], 95)), 3),
+            "independence_q_error_p50": round(float(np.median(qi[okm])), 3),
+            "independence_q_error_p95": round(float(np.percentile(qi[okm], 95)), 3)}
+        # the step's training minibatch: the first 256 labelled probes
+        self.train_feat, _ = self.model.featurize(preds[:256])
+        self.train_y = torch.from_numpy(np.log1p(counts[:256].astype(np.float64)).astype(np.float32)).cuda()
+        self.step_cfg = sel.train_cfg(batch=256, lr=1e-4, apply_update=1)
+        # exact fallback cost: one batched scan of 256 of the held-out probes
+        self.exact_plan = sel.BatchPlan(ctx, self.eval_preds[:256], [T] * 256, autotune=False)
+        self.events = []
+        self.accepted = 0
+
+    def run(self, record=False):
+        ev = lambda: torch.cuda.Event(enable_timing=True)
+        a, b, c = ev(), ev(), ev()
+        if record:
+            a.record()
+        feat, ok = self.model.featurize(self.eval_preds)              # a6
+        out = self.model.forward(feat)                                # a7
+        if record:
+            b.record()
+        o = out.cpu().numpy()                                         # a9: gate decision on the host
+        self.accepted = int(((np.exp(0.5 * np.clip(o[:, 1], -8, 8)) <= self.tau) & ok.cpu().numpy().astype(bool)).sum())
+        self.model.train_step(self.train_feat, self.train_y, self.step_cfg)   # a8
+        if record:
+            c.record()
+            self.events.append((a, b, c))
+
+    def summary(self):
+        inf = [x.elapsed_time(y) for x, y, _ in self.events]
+        trn = [y.elapsed_time(z) for _, y, z in self.events]
+        reps = 5
+        self.exact_plan.run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            self.exact_plan.run()
+        e1.record()
+        torch.cuda.synchronize()
+        exact_ms = e0.elapsed_time(e1) / reps
+        n = len(self.eval_preds)
+        return dict(self.quality, **{
+            "workload": f"{n} held-out OR-of-AND probes (<= 6 leaves) on the same table; trained on "
+                        f"{self.n_train} probes labelled by the count kernel",
+            "label_seconds": round(self.label_s, 2), "train_seconds": round(self.train_s, 2),
+            "final_train_loss": round(self.final_loss, 4),
+            "ms_per_batch_featurize_forward": round(statistics.mean(inf), 3),
+            "ms_per_estimate": round(statistics.mean(inf) / n, 6),
+            "exact_ms_per_estimate": round(exact_ms / 256, 4),
+            "train_step_ms": round(statistics.mean(trn), 3),
+            "answered_without_scan_per_step": self.accepted})
+
+
 def time_separate_vs_batched(step: OurStep, reps=5):
     """The same probes as one batched launch vs one launch per probe."""
     sel, w = step.sel, step.w
@@ -320,6 +423,7 @@ def main():
     ap.add_argument("--rows", type=int, default=300_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.steps <= 2, "at least 3 warm-up steps"
@@ -343,8 +447,11 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     w = Workload(args.rows, dev, seed_offset=rank)
     step = OurStep(w, sel)
+    sur = Surrogate(step) if not args.no_surrogate else None
     for _ in range(args.warmup):
         step.run()
+        if sur:
+            sur.run()
     # per-step bytes are fixed (same probes, same data)
     counts, accepted, _ = step.run()
     b_batch, b_pds = algorithmic_bytes(w.types, w.n, w.trees, counts, accepted, w.proj)
@@ -361,6 +468,8 @@ def main():
     t0.record()
     for _ in range(args.steps):
         step.run(record=True)
+        if sur:
+            sur.run(record=True)
     t1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -418,6 +527,8 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
     }
+    if sur:
+        out["surrogate"] = sur.summary()
     if rank == 0:
         out["batched_vs_separate"] = time_separate_vs_batched(step)
     if rank == 0 and not args.no_e2e:
