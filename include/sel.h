@@ -240,11 +240,21 @@ sel_status sel_batch_plan_run(sel_batch_plan* plan, uint64_t* dev_out_counts, ui
  * not autotuned). */
 sel_status sel_batch_plan_info(const sel_batch_plan* plan, int32_t* tile_rows, int32_t* stages,
                                int32_t* ctas_per_sm, float* ms);
+/* Count-scan kernel variant chosen by the plan (see sel_ctx_set_scan_variant). */
+sel_status sel_batch_plan_variant(const sel_batch_plan* plan, int32_t* consumer_warps, int32_t* chunks_per_pass);
 void sel_batch_plan_free(sel_batch_plan* plan);
 
 /* Launch configuration override for sel_count / sel_count_async / sel_pushdown
- * (0 = keep the library default).  tile_rows must be a multiple of 256. */
+ * (0 = keep the library default).  tile_rows must be a multiple of 256 and at
+ * most 16384 (the push-down uses at most 4096). */
 sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm);
+
+/* Count-scan kernel variant for sel_count / sel_count_async (both 0 = the
+ * library default): consumer_warps 8 or 16 (plus one producer warp per CTA)
+ * and chunks_per_pass 1 or 2 (256-row chunks a warp evaluates with one pass
+ * over the program's instructions).  Any other pair: SEL_ERR_INVALID_ARG.
+ * Results do not depend on the variant. */
+sel_status sel_ctx_set_scan_variant(sel_ctx* ctx, int32_t consumer_warps, int32_t chunks_per_pass);
 
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
@@ -297,7 +307,9 @@ void sel_mlp_free(sel_mlp* m);
 /* a6: features of n predicates into dev_features (device BF16, n x 144,
  * caller-owned) and, when dev_ok is not NULL, 1/0 featurizable flags (device,
  * n bytes).  Predicates must be compiled against the model's table schema.
- * Synchronous. */
+ * Asynchronous on the context's stream: the host builds the clause records,
+ * copies them through a pinned staging block owned by the model (a later call
+ * waits for the previous copy out of it) and launches the feature kernel. */
 sel_status sel_mlp_featurize(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds, int32_t n, void* dev_features,
                              uint8_t* dev_ok);
 /* a7: dev_out (device FP32, n x 2) = (mu, raw log-variance) per feature row.

@@ -90,8 +90,10 @@ def _load():
         "sel_batch_plan_create": (C.c_int, [V, P(V), P(P(sel_table)), C.c_int32, C.c_int32, P(V)]),
         "sel_batch_plan_run": (C.c_int, [V, V, P(C.c_uint64)]),
         "sel_batch_plan_info": (C.c_int, [V, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_float)]),
+        "sel_batch_plan_variant": (C.c_int, [V, P(C.c_int32), P(C.c_int32)]),
         "sel_batch_plan_free": (None, [V]),
         "sel_ctx_set_scan_shape": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32]),
+        "sel_ctx_set_scan_variant": (C.c_int, [V, C.c_int32, C.c_int32]),
         "sel_ctx_launch_count": (C.c_uint64, [V]),
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
@@ -299,6 +301,9 @@ class Context:
     def set_scan_shape(self, tile_rows=0, stages=0, ctas_per_sm=0):
         _check(lib.sel_ctx_set_scan_shape(self.h, tile_rows, stages, ctas_per_sm), "sel_ctx_set_scan_shape")
 
+    def set_scan_variant(self, consumer_warps=0, chunks_per_pass=0):
+        _check(lib.sel_ctx_set_scan_variant(self.h, consumer_warps, chunks_per_pass), "sel_ctx_set_scan_variant")
+
     def debug_pushdown_fault(self, skip_tile: int, wait_ns: int = 0):
         _check(lib.sel_ctx_debug_pushdown_fault(self.h, skip_tile, wait_ns), "sel_ctx_debug_pushdown_fault")
 
@@ -438,7 +443,10 @@ class BatchPlan:
         tr, st, cp, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_float()
         _check(lib.sel_batch_plan_info(self.h, C.byref(tr), C.byref(st), C.byref(cp), C.byref(ms)),
                "sel_batch_plan_info")
-        return {"tile_rows": tr.value, "stages": st.value, "ctas_per_sm": cp.value, "ms": ms.value}
+        w, g = C.c_int32(), C.c_int32()
+        _check(lib.sel_batch_plan_variant(self.h, C.byref(w), C.byref(g)), "sel_batch_plan_variant")
+        return {"tile_rows": tr.value, "stages": st.value, "ctas_per_sm": cp.value, "ms": ms.value,
+                "consumer_warps": w.value, "chunks_per_pass": g.value}
 
     def __del__(self):
         h = getattr(self, "h", None)

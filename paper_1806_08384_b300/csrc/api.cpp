@@ -60,6 +60,7 @@ struct DevBuf {
 
 struct Shape {
     int tile_rows = 0, stages = 0, ctas_per_sm = 0;
+    int warps = 0, group = 0;   // count-scan variant: consumer warps, chunks per instruction pass
 };
 
 }  // namespace sel
@@ -169,7 +170,7 @@ static void fill_table_arg(TableArg& ta, const std::vector<int32_t>& slot_col, c
 static int default_tile_rows(uint32_t row_bytes, int stage_target) {
     if (row_bytes == 0) return 2048;
     int r = (int)(stage_target / row_bytes) / kChunkRows * kChunkRows;
-    return std::max(kChunkRows, std::min(8192, r));
+    return std::max(kChunkRows, std::min(kMaxTileRows, r));
 }
 
 // Fills shape-dependent fields and launches (several launches when the
@@ -245,7 +246,7 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
         }
         if (tiles == 0) continue;
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->n_sm * sh.ctas_per_sm));
-        cudaError_t e = launch_scan_count(a, (int)grid, smem, ctx->stream);
+        cudaError_t e = launch_scan_count(a, (int)grid, smem, ctx->stream, sh.warps, sh.group);
         if (e != cudaSuccess) return cuda_fail("scan launch", e);
         ++launches;
         ctx->launches++;
@@ -256,9 +257,13 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
 
 static Shape single_shape(sel_ctx* ctx, uint32_t row_bytes) {
     Shape s;
-    s.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 4;
+    // measured on the 300M-row fact table: 3 stages of about 64 KB, one CTA of
+    // 16 consumer warps per SM, 2 chunks per instruction pass
+    s.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 3;
     s.ctas_per_sm = ctx->shape.ctas_per_sm > 0 ? ctx->shape.ctas_per_sm : 1;
-    s.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : default_tile_rows(row_bytes, 40 * 1024);
+    s.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : default_tile_rows(row_bytes, 64 * 1024);
+    s.warps = ctx->shape.warps > 0 ? ctx->shape.warps : kScanDefaultWarps;
+    s.group = ctx->shape.group > 0 ? ctx->shape.group : kScanDefaultGroup;
     return s;
 }
 
@@ -325,7 +330,7 @@ extern "C" void sel_ctx_destroy(sel_ctx* c) {
 }
 
 extern "C" sel_status sel_ctx_set_scan_shape(sel_ctx* c, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm) {
-    if (!c || tile_rows < 0 || tile_rows % kChunkRows || tile_rows > 8192 || stages < 0 || stages > 16 ||
+    if (!c || tile_rows < 0 || tile_rows % kChunkRows || tile_rows > kMaxTileRows || stages < 0 || stages > 16 ||
         ctas_per_sm < 0 || ctas_per_sm > 8) {
         set_error("sel_ctx_set_scan_shape: bad arguments");
         return SEL_ERR_INVALID_ARG;
@@ -333,6 +338,16 @@ extern "C" sel_status sel_ctx_set_scan_shape(sel_ctx* c, int32_t tile_rows, int3
     c->shape.tile_rows = tile_rows;
     c->shape.stages = stages;
     c->shape.ctas_per_sm = ctas_per_sm;
+    return SEL_OK;
+}
+
+extern "C" sel_status sel_ctx_set_scan_variant(sel_ctx* c, int32_t consumer_warps, int32_t chunks_per_pass) {
+    if (!c || !((consumer_warps == 0 && chunks_per_pass == 0) || scan_variant_ok(consumer_warps, chunks_per_pass))) {
+        set_error("sel_ctx_set_scan_variant: bad arguments (0,0 or warps 8|16 and chunks 1|2)");
+        return SEL_ERR_INVALID_ARG;
+    }
+    c->shape.warps = consumer_warps;
+    c->shape.group = chunks_per_pass;
     return SEL_OK;
 }
 
@@ -680,22 +695,28 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_counts, (size_t)n * 8));
     uint32_t max_rb = 0;
     for (auto& t : p->tables) max_rb = std::max(max_rb, t.row_bytes);
-    // default shape, then the autotuner's candidates
+    // default shape, then the autotuner's candidates (stage size, stages, CTAs
+    // per SM, consumer warps, chunks per instruction pass)
     Shape best;
-    best.stages = 4;
-    best.ctas_per_sm = 2;
-    best.tile_rows = default_tile_rows(max_rb, 24 * 1024);
+    best.stages = 3;
+    best.ctas_per_sm = 1;
+    best.tile_rows = default_tile_rows(max_rb, 64 * 1024);
+    best.warps = 16;
+    best.group = 2;
     float best_ms = 0.f;
     if (autotune) {
-        struct Cand { int stage_kb, stages, ctas; };
-        const Cand cands[] = {{24, 4, 2}, {16, 4, 2}, {32, 3, 2}, {40, 4, 1}, {16, 6, 2},
-                              {12, 4, 3}, {8, 4, 4}, {48, 3, 1}, {32, 5, 1}};
+        struct Cand { int stage_kb, stages, ctas, warps, group; };
+        const Cand cands[] = {{64, 3, 1, 16, 2}, {48, 4, 1, 16, 2}, {96, 2, 1, 16, 2}, {64, 3, 1, 16, 1},
+                              {48, 4, 1, 16, 1}, {32, 3, 2, 8, 2},  {24, 4, 2, 8, 2},  {32, 3, 2, 8, 1},
+                              {24, 4, 2, 8, 1},  {16, 4, 3, 8, 1}};
         best_ms = 1e30f;
         for (const Cand& c : cands) {
             Shape sh;
             sh.stages = c.stages;
             sh.ctas_per_sm = c.ctas;
             sh.tile_rows = default_tile_rows(max_rb, c.stage_kb * 1024);
+            sh.warps = c.warps;
+            sh.group = c.group;
             float ms = 0;
             sel_status s = plan_time(p.get(), sh, 2, &ms);
             if (s == SEL_ERR_UNSUPPORTED) continue;
@@ -753,6 +774,17 @@ extern "C" sel_status sel_batch_plan_info(const sel_batch_plan* p, int32_t* tile
     if (stages) *stages = p->shape.stages;
     if (ctas_per_sm) *ctas_per_sm = p->shape.ctas_per_sm;
     if (ms) *ms = p->ms;
+    return SEL_OK;
+}
+
+extern "C" sel_status sel_batch_plan_variant(const sel_batch_plan* p, int32_t* consumer_warps,
+                                             int32_t* chunks_per_pass) {
+    if (!p) {
+        set_error("sel_batch_plan_variant: plan is NULL");
+        return SEL_ERR_INVALID_ARG;
+    }
+    if (consumer_warps) *consumer_warps = p->shape.warps;
+    if (chunks_per_pass) *chunks_per_pass = p->shape.group;
     return SEL_OK;
 }
 

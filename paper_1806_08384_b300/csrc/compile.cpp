@@ -99,6 +99,67 @@ Leaf int_range(int col, int type, i128 lo, i128 hi, bool neg) {
     return l;
 }
 
+// Perfect multiply-shift hash of a value set: slot(x) = (uint32)(key(x) * mult)
+// >> shift over a table of 2^(32 - shift) entries, key(x) = x for 32-bit
+// columns and lo32(x) ^ hi32(x) for int64.  Multipliers are drawn from a fixed
+// SplitMix64 stream (the same set always compiles to the same table) until one
+// puts every value in its own slot; the table doubles (up to 8 KB) when a size
+// finds none.  Empty slots hold the first value, which cannot match there
+// because that value hashes to its own slot.
+constexpr size_t kMaxHashKeys = 128;
+
+bool perfect_hash(Leaf& l, const std::vector<i128>& v, bool wide) {
+    const size_t max_entries = wide ? 1024 : 2048;
+    uint64_t state = 0x5E1EC7ull;
+    auto next = [&]() {
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    std::vector<uint32_t> keys;
+    for (i128 x : v) {
+        const uint64_t u = (uint64_t)(int64_t)x;
+        keys.push_back(wide ? (uint32_t)u ^ (uint32_t)(u >> 32) : (uint32_t)u);
+    }
+    int bits = 1;
+    while (((size_t)1 << bits) < 2 * v.size()) ++bits;
+    std::vector<int> slot_of;
+    for (; ((size_t)1 << bits) <= max_entries; ++bits) {
+        const size_t m = (size_t)1 << bits;
+        const uint32_t shift = 32u - (uint32_t)bits;
+        std::vector<uint8_t> used(m);
+        for (int attempt = 0; attempt < 4000; ++attempt) {
+            const uint32_t mult = (uint32_t)next() | 1u;
+            std::fill(used.begin(), used.end(), 0);
+            bool ok = true;
+            for (uint32_t k : keys) {
+                const uint32_t h = (k * mult) >> shift;
+                if (used[h]) {
+                    ok = false;
+                    break;
+                }
+                used[h] = 1;
+            }
+            if (!ok) continue;
+            l.ins.opc = wide ? OP_HASH64 : OP_HASH32;
+            l.ins.a = mult;
+            l.ins.b = shift;
+            l.pool.clear();
+            std::vector<uint64_t> table(m, (uint64_t)(int64_t)v.front());
+            for (size_t i = 0; i < v.size(); ++i) table[(keys[i] * mult) >> shift] = (uint64_t)(int64_t)v[i];
+            for (uint64_t t : table) {
+                if (wide)
+                    put<uint64_t>(l.pool, t);
+                else
+                    put<uint32_t>(l.pool, (uint32_t)t);
+            }
+            return true;
+        }
+    }
+    return false;
+}
+
 Leaf int_set(int col, int type, std::vector<i128> v, bool neg) {
     const i128 tmin = (type == SEL_I64) ? (i128)std::numeric_limits<int64_t>::min() : (i128)INT32_MIN;
     const i128 tmax = (type == SEL_I64) ? (i128)std::numeric_limits<int64_t>::max() : (i128)INT32_MAX;
@@ -111,6 +172,15 @@ Leaf int_set(int col, int type, std::vector<i128> v, bool neg) {
     Leaf l;
     l.col = col;
     l.ins.neg = neg ? 1 : 0;
+    if (type != SEL_I64 && span < 32) {   // the whole set in one 32-bit word of the instruction
+        uint32_t word = 0;
+        for (i128 x : v) word |= 1u << (uint32_t)(x - v.front());
+        l.ins.opc = OP_MASK32;
+        l.ins.a = (uint32_t)(int32_t)v.front();
+        l.ins.b = word;
+        return l;
+    }
+    if (v.size() >= 3 && v.size() <= kMaxHashKeys && perfect_hash(l, v, type == SEL_I64)) return l;
     if (type != SEL_I64 && v.size() > 8 && span < (i128)(1 << 20)) {
         const uint32_t nbits = (uint32_t)(span + 1);
         std::vector<uint32_t> words((nbits + 31) / 32, 0u);
@@ -422,7 +492,7 @@ struct Compiler {
             Instr in = e.leaf.ins;
             in.slot = (uint8_t)col_slot[e.leaf.col];
             if (!e.leaf.pool.empty()) {
-                const size_t al = (in.opc == OP_RANGE64 || in.opc == OP_IN64) ? 8 : 4;
+                const size_t al = (in.opc == OP_RANGE64 || in.opc == OP_IN64 || in.opc == OP_HASH64) ? 8 : 4;
                 while (p.pool.size() % al) p.pool.push_back(0);
                 in.off = (uint32_t)p.pool.size();
                 p.pool.insert(p.pool.end(), e.leaf.pool.begin(), e.leaf.pool.end());
@@ -506,12 +576,12 @@ struct Compiler {
 std::string describe(const Program& p) {
     std::ostringstream o;
     static const char* names[] = {"?", "AND", "OR", "CONST", "RANGE32", "RANGE64", "RANGEF",
-                                  "IN32", "IN64", "INF", "BITMAP", "SAVE", "LOAD"};
+                                  "IN32", "IN64", "INF", "BITMAP", "SAVE", "LOAD", "MASK32", "HASH32", "HASH64"};
     o << "slots:";
     for (size_t s = 0; s < p.slot_col.size(); ++s) o << " " << p.slot_col[s] << "/" << p.slot_width[s];
     o << "\nneed: " << p.need << "\nleaves: " << p.leaves << "\n";
     for (const Instr& in : p.instrs) {
-        o << names[in.opc <= OP_LOAD ? in.opc : 0];
+        o << names[in.opc <= OP_HASH64 ? in.opc : 0];
         if (in.opc == OP_SAVE || in.opc == OP_LOAD) o << " m=" << in.a;
         if (in.opc != OP_AND && in.opc != OP_OR && in.opc != OP_SAVE && in.opc != OP_LOAD) {
             if (in.opc != OP_CONST) o << " slot=" << (int)in.slot;
@@ -549,6 +619,24 @@ std::string describe(const Program& p) {
                     uint32_t v;
                     std::memcpy(&v, &p.pool[in.off + 4 * k], 4);
                     o << "0x" << std::hex << v << std::dec;
+                }
+            }
+            break;
+        }
+        case OP_MASK32: o << " lo=" << (int32_t)in.a << " word=0x" << std::hex << in.b << std::dec; break;
+        case OP_HASH32: case OP_HASH64: {
+            const uint32_t entries = 1u << (32u - in.b);
+            o << " mult=0x" << std::hex << in.a << std::dec << " shift=" << in.b << " table=";
+            for (uint32_t k = 0; k < entries; ++k) {
+                if (k) o << ",";
+                if (in.opc == OP_HASH32) {
+                    int32_t v;
+                    std::memcpy(&v, &p.pool[in.off + 4 * k], 4);
+                    o << v;
+                } else {
+                    int64_t v;
+                    std::memcpy(&v, &p.pool[in.off + 8 * k], 8);
+                    o << v;
                 }
             }
             break;

@@ -16,6 +16,8 @@
 // ownership rotates from tile to tile, so tiles with fewer chunks than warps
 // leave no warp idle.  Each column tile is read from HBM exactly once per
 // launch, whatever the number of programs on the table.
+#include <algorithm>
+
 #include "kernels.h"
 #include "scan.cuh"
 
@@ -58,12 +60,15 @@ __device__ __forceinline__ void produce_tile(const ScanArgs& a, int64_t g, uint3
     }
 }
 
-__global__ void __launch_bounds__(kScanThreads) scan_count_kernel(const __grid_constant__ ScanArgs a) {
+// W consumer warps (+1 producer warp); each consumer pass evaluates the
+// programs on G chunks at once (G independent mask stacks share one
+// instruction stream, which hides the interpreter's latency).
+template <int W, int G>
+__global__ void __launch_bounds__((W + 1) * 32, W == 8 ? 2 : 1) scan_count_kernel(const __grid_constant__ ScanArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint32_t s_off[kMaxTables][kMaxSlots];
     __shared__ uint32_t s_fail;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    constexpr uint32_t W = kScanConsumers / 32;   // consumer warps
     const uint32_t S = a.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + S;
@@ -89,14 +94,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_count_kernel(const __grid_c
         blob = smem + a.prog_off;
     }
     __syncthreads();
-    const int64_t G = gridDim.x;
+    const int64_t NB = gridDim.x;
 
     if (warp == W) {
         // ------------------------------- producer -------------------------------
         const uint64_t pol = policy_evict_first();
         uint32_t s = 0, phase = 0;   // stage of tile k and the number of times it was reused, mod 2
         for (int64_t k = 0;; ++k) {
-            const int64_t g = blockIdx.x + k * G;
+            const int64_t g = blockIdx.x + k * NB;
             if (g >= a.total_tiles) break;
             if (k >= S) {   // wait until every consumer warp released the stage's previous tile
                 const bool ok = mbar_wait_bounded(&empty[s], phase ^ 1u);
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_count_kernel(const __grid_c
         uint32_t rot = 0;   // running chunk count: chunk c of a tile belongs to warp (rot + c) % W
         uint32_t s = 0, parity = 0;
         for (int64_t k = 0;; ++k) {
-            const int64_t g = blockIdx.x + k * G;
+            const int64_t g = blockIdx.x + k * NB;
             if (g >= a.total_tiles) break;
             const int ti = find_table(a, g);
             const TableArg& T = a.t[ti];
@@ -144,18 +149,30 @@ __global__ void __launch_bounds__(kScanThreads) scan_count_kernel(const __grid_c
             }
             if (*reinterpret_cast<volatile uint32_t*>(&s_fail)) break;
             const uint32_t st_addr = smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes);
+            const uint32_t n_groups = (n_chunks + G - 1) / G;
             const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
-            for (uint32_t ch = first; ch < n_chunks; ch += W) {
-                const uint32_t c0 = ch * kChunkRows;
-                const uint32_t vm = (c0 + kChunkRows <= valid) ? 0xFFu : valid_mask(c0, lane, valid);
+            for (uint32_t grp = first; grp < n_groups; grp += W) {
+                uint32_t c0[G], vm[G];
+#pragma unroll
+                for (int q = 0; q < G; ++q) {
+                    const uint32_t ch = grp * G + q;
+                    // a missing chunk of the last group re-reads the group's first chunk, masked out
+                    c0[q] = (ch < n_chunks ? ch : grp * G) * kChunkRows;
+                    vm[q] = ch >= n_chunks ? 0u
+                            : (c0[q] + kChunkRows <= valid) ? 0xFFu
+                                                              : valid_mask(c0[q], lane, valid);
+                }
                 for (uint32_t p = T.prog_begin; p < T.prog_end; ++p) {
-                    const uint32_t m =
-                        eval_program(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane) & vm;
-                    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(m)));
+                    uint32_t m[G];
+                    eval_program_g<G>(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane, m);
+                    uint32_t pc = 0;
+#pragma unroll
+                    for (int q = 0; q < G; ++q) pc += __popc(m[q] & vm[q]);
+                    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
                     if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
                 }
             }
-            rot += n_chunks;
+            rot += (n_chunks + G - 1) / G;
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);
             if (++s == S) {
@@ -181,16 +198,40 @@ size_t scan_layout(ScanArgs& a) {
     return static_cast<size_t>(a.stage_off) + static_cast<size_t>(a.stages) * a.stage_bytes;
 }
 
-cudaError_t scan_kernel_max_smem(int optin, int* dyn_max) {
+template <int W, int G>
+static cudaError_t set_smem_limit(int optin, int* dyn_max) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, scan_count_kernel);
+    cudaError_t e = cudaFuncGetAttributes(&fa, scan_count_kernel<W, G>);
     if (e != cudaSuccess) return e;
-    *dyn_max = optin - static_cast<int>(fa.sharedSizeBytes);
-    return cudaFuncSetAttribute(scan_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, *dyn_max);
+    const int lim = optin - static_cast<int>(fa.sharedSizeBytes);
+    *dyn_max = *dyn_max < 0 ? lim : std::min(*dyn_max, lim);
+    return cudaFuncSetAttribute(scan_count_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
-cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st) {
-    scan_count_kernel<<<grid, kScanThreads, smem, st>>>(a);
+cudaError_t scan_kernel_max_smem(int optin, int* dyn_max) {
+    *dyn_max = -1;
+    cudaError_t e = set_smem_limit<8, 1>(optin, dyn_max);
+    if (e == cudaSuccess) e = set_smem_limit<8, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = set_smem_limit<16, 1>(optin, dyn_max);
+    if (e == cudaSuccess) e = set_smem_limit<16, 2>(optin, dyn_max);
+    return e;
+}
+
+bool scan_variant_ok(int warps, int group) {
+    return (warps == 8 || warps == 16) && (group == 1 || group == 2);
+}
+
+cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group) {
+    if (warps == 8 && group == 1)
+        scan_count_kernel<8, 1><<<grid, 9 * 32, smem, st>>>(a);
+    else if (warps == 8 && group == 2)
+        scan_count_kernel<8, 2><<<grid, 9 * 32, smem, st>>>(a);
+    else if (warps == 16 && group == 1)
+        scan_count_kernel<16, 1><<<grid, 17 * 32, smem, st>>>(a);
+    else if (warps == 16 && group == 2)
+        scan_count_kernel<16, 2><<<grid, 17 * 32, smem, st>>>(a);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

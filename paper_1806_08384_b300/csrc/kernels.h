@@ -9,8 +9,11 @@ namespace sel {
 
 constexpr int kMaxTables = 8;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device wait
-constexpr int kScanConsumers = 256;                 // 8 consumer warps
-constexpr int kScanThreads = kScanConsumers + 32;   // + 1 producer warp
+// Count-scan variants: consumer warps (8 or 16, plus one producer warp) and
+// chunks evaluated per instruction pass (1 or 2).
+constexpr int kScanDefaultWarps = 16;
+constexpr int kMaxTileRows = 16384;
+constexpr int kScanDefaultGroup = 2;
 
 // One table of a scan launch: its referenced columns ("slots"), its tiles in
 // the launch's global tile sequence and the programs evaluated on it.
@@ -42,9 +45,10 @@ struct ScanArgs {
 
 // Shared-memory bytes needed by a scan launch (and fills the *_off fields).
 size_t scan_layout(ScanArgs& a);
-cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st);
-// Sets the scan kernel's dynamic shared-memory limit to the opt-in maximum
-// minus its static shared memory, returned in *dyn_max.
+bool scan_variant_ok(int warps, int group);
+cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group);
+// Sets every scan variant's dynamic shared-memory limit to the opt-in maximum
+// minus its static shared memory; *dyn_max receives the smallest of them.
 cudaError_t scan_kernel_max_smem(int optin, int* dyn_max);
 
 // ---------------------------------------------------------------------------

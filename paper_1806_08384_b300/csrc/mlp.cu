@@ -353,7 +353,17 @@ struct sel_mlp {
     __nv_bfloat16 *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr, *dz1t = nullptr, *dz2t = nullptr, *dz3t = nullptr;
     float* out = nullptr;
     std::vector<void*> owned;
+    // featurize staging: pinned host block -> device block, reused across calls;
+    // stage_done marks the end of the last copy out of the host block
+    uint8_t* h_stage = nullptr;
+    uint8_t* d_stage = nullptr;
+    size_t stage_cap = 0;
+    cudaEvent_t stage_done = nullptr;
     ~sel_mlp() {
+        if (stage_done) cudaEventSynchronize(stage_done);
+        if (h_stage) cudaFreeHost(h_stage);
+        if (d_stage) cudaFree(d_stage);
+        if (stage_done) cudaEventDestroy(stage_done);
         for (void* q : owned) cudaFree(q);
     }
 };
@@ -602,25 +612,49 @@ struct DeviceVec {
     }
 };
 
+// Makes the staging blocks hold `bytes`; waits for the last copy out of the
+// host block, so the caller may overwrite it.
+sel_status stage_reserve(sel_mlp* m, size_t bytes) {
+    if (!m->stage_done) MLP_TRY(cuda_ok(cudaEventCreateWithFlags(&m->stage_done, cudaEventDisableTiming), "featurize"));
+    MLP_TRY(cuda_ok(cudaEventSynchronize(m->stage_done), "featurize"));
+    if (bytes <= m->stage_cap) return SEL_OK;
+    const size_t cap = std::max<size_t>(bytes, 2 * m->stage_cap);
+    if (m->h_stage) cudaFreeHost(m->h_stage);
+    if (m->d_stage) cudaFree(m->d_stage);
+    m->h_stage = m->d_stage = nullptr;
+    m->stage_cap = 0;
+    MLP_TRY(cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&m->h_stage), cap), "featurize staging"));
+    MLP_TRY(cuda_ok(cudaMalloc(reinterpret_cast<void**>(&m->d_stage), cap), "featurize staging"));
+    m->stage_cap = cap;
+    return SEL_OK;
+}
+
+// a6 on n predicates: host clause records -> one pinned copy -> featurize_kernel.
+// Asynchronous on st (the staging block is protected by stage_done).
 sel_status featurize(sel_mlp* m, cudaStream_t st, const sel_pred* const* preds, int32_t n, __nv_bfloat16* feat,
                      std::vector<uint8_t>* ok_out, uint8_t* dev_ok) {
     std::vector<FeatClause> cl;
     std::vector<uint64_t> keys;
     std::vector<uint8_t> ok;
     MLP_TRY(build_clauses(m, preds, n, cl, keys, ok));
-    DeviceVec dcl, dkeys;
-    MLP_TRY(cuda_ok(cudaMalloc(&dcl.p, cl.size() * sizeof(FeatClause) + 16), "featurize"));
-    MLP_TRY(cuda_ok(cudaMalloc(&dkeys.p, keys.size() * 8 + 16), "featurize"));
-    MLP_TRY(cuda_ok(cudaMemcpyAsync(dcl.p, cl.data(), cl.size() * sizeof(FeatClause), cudaMemcpyHostToDevice, st),
-                    "featurize"));
-    if (!keys.empty())
-        MLP_TRY(cuda_ok(cudaMemcpyAsync(dkeys.p, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice, st), "featurize"));
-    if (dev_ok) MLP_TRY(cuda_ok(cudaMemcpyAsync(dev_ok, ok.data(), (size_t)n, cudaMemcpyHostToDevice, st), "featurize"));
+    const size_t cl_bytes = cl.size() * sizeof(FeatClause);
+    const size_t keys_off = (cl_bytes + 15) / 16 * 16;
+    const size_t ok_off = keys_off + (keys.size() * 8 + 15) / 16 * 16;
+    const size_t total = ok_off + (size_t)n;
+    MLP_TRY(stage_reserve(m, total));
+    std::memcpy(m->h_stage, cl.data(), cl_bytes);
+    if (!keys.empty()) std::memcpy(m->h_stage + keys_off, keys.data(), keys.size() * 8);
+    std::memcpy(m->h_stage + ok_off, ok.data(), (size_t)n);
+    MLP_TRY(cuda_ok(cudaMemcpyAsync(m->d_stage, m->h_stage, total, cudaMemcpyHostToDevice, st), "featurize"));
+    MLP_TRY(cuda_ok(cudaEventRecord(m->stage_done, st), "featurize"));
+    if (dev_ok)
+        MLP_TRY(cuda_ok(cudaMemcpyAsync(dev_ok, m->d_stage + ok_off, (size_t)n, cudaMemcpyDeviceToDevice, st),
+                        "featurize"));
     const int64_t threads = (int64_t)n * kSlots;
     featurize_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        static_cast<FeatClause*>(dcl.p), static_cast<uint64_t*>(dkeys.p), m->cdf, m->m, n, feat);
+        reinterpret_cast<const FeatClause*>(m->d_stage), reinterpret_cast<const uint64_t*>(m->d_stage + keys_off),
+        m->cdf, m->m, n, feat);
     MLP_TRY(cuda_ok(cudaGetLastError(), "featurize launch"));
-    MLP_TRY(cuda_ok(cudaStreamSynchronize(st), "featurize"));   // host vectors go out of scope
     if (ok_out) *ok_out = std::move(ok);
     return SEL_OK;
 }

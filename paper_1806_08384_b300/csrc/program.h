@@ -25,6 +25,9 @@ enum Opcode : uint8_t {
     OP_BITMAP = 10,   // d = (uint32)(x - a); d < b && bit d of the pool words at off
     OP_SAVE = 11,     // memo slot a := top of stack (a leaf that occurs again later)
     OP_LOAD = 12,     // push memo slot a (a repeated leaf, evaluated once)
+    OP_MASK32 = 13,   // d = (uint32)(x - a); d < 32 && bit d of b    (a set spanning <= 32 values)
+    OP_HASH32 = 14,   // t = pool32 at off; t[(uint32)(x * a) >> b] == x   (perfect multiply-shift hash)
+    OP_HASH64 = 15,   // t = pool64 at off; k = lo32(x) ^ hi32(x); t[(uint32)(k * a) >> b] == x
 };
 
 constexpr int kMemoSlots = 4;      // 8-bit masks kept in one 32-bit register

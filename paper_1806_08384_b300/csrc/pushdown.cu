@@ -68,7 +68,7 @@ __device__ bool look_back(const PushdownArgs& a, long long t, uint32_t lane, uns
     }
 }
 
-__global__ void __launch_bounds__(kPdThreads) pushdown_kernel(const __grid_constant__ PushdownArgs a) {
+__global__ void __launch_bounds__(kPdThreads, 6) pushdown_kernel(const __grid_constant__ PushdownArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t bar;
     __shared__ unsigned long long s_tile, s_excl;

@@ -127,117 +127,230 @@ __device__ __forceinline__ uint32_t mask8(Pred pred) {
     return m;
 }
 
-// Evaluates one leaf; the pool pointer may address shared or global memory.
-__device__ __forceinline__ uint32_t eval_leaf(const Instr& in, uint32_t col_base, uint32_t c0, uint32_t lane,
-                                              const uint8_t* pool) {
-    uint32_t m;
+// The same from 0/1 values.
+template <typename Bit>
+__device__ __forceinline__ uint32_t mask8_bits(Bit bit) {
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) m |= bit(i) << i;
+    return m;
+}
+
+// Set membership of the lane's 8 rows in blocks of B list values: each block
+// is one branch-free OR of B equality tests per row (a short list repeats its
+// last value, which changes nothing).
+template <int G, int B, typename T, typename Eq>
+__device__ __forceinline__ void in_list(const T (&v)[G][8], const T* vals, uint32_t n, Eq eq, uint32_t (&m)[G]) {
+    bool hit[G][8];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) hit[g][i] = false;
+    for (uint32_t k0 = 0; k0 < n; k0 += B) {
+        T w[B];
+#pragma unroll
+        for (int j = 0; j < B; ++j) w[j] = vals[min(k0 + j, n - 1)];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                bool h = hit[g][i];
+#pragma unroll
+                for (int j = 0; j < B; ++j) h = h | eq(v[g][i], w[j]);
+                hit[g][i] = h;
+            }
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) m[g] = mask8([&](int i) { return hit[g][i]; });
+}
+
+// Evaluates one leaf on G chunks (chunk g starts at tile row c0[g]); the pool
+// pointer may address shared or global memory.
+template <int G>
+__device__ __forceinline__ void eval_leaf_g(const Instr& in, uint32_t col_base, const uint32_t (&c0)[G], uint32_t lane,
+                                            const uint8_t* pool, uint32_t (&m)[G]) {
     switch (in.opc) {
     case OP_RANGE32: {
-        uint32_t v[8];
-        load8x32(col_base, c0, lane, v);
+        uint32_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
         const uint32_t lo = in.a, sp = in.b;
-        m = mask8([&](int i) { return v[i] - lo <= sp; });
+#pragma unroll
+        for (int g = 0; g < G; ++g) m[g] = mask8([&](int i) { return v[g][i] - lo <= sp; });
         break;
     }
     case OP_RANGEF: {
-        uint32_t v[8];
-        load8x32(col_base, c0, lane, v);
+        uint32_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
         const float lo = __uint_as_float(in.a), hi = __uint_as_float(in.b);
-        m = mask8([&](int i) {
-            const float x = __uint_as_float(v[i]);
-            return lo <= x && x <= hi;
-        });
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            m[g] = mask8([&](int i) {
+                const float x = __uint_as_float(v[g][i]);
+                return lo <= x && x <= hi;
+            });
         break;
     }
     case OP_RANGE64: {
-        uint64_t v[8];
-        load8x64(col_base, c0, lane, v);
+        uint64_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x64(col_base, c0[g], lane, v[g]);
         const uint64_t lo = *reinterpret_cast<const uint64_t*>(pool + in.off);
         const uint64_t sp = *reinterpret_cast<const uint64_t*>(pool + in.off + 8);
-        m = mask8([&](int i) { return v[i] - lo <= sp; });
+#pragma unroll
+        for (int g = 0; g < G; ++g) m[g] = mask8([&](int i) { return v[g][i] - lo <= sp; });
         break;
     }
     case OP_IN32: {
-        uint32_t v[8];
-        load8x32(col_base, c0, lane, v);
-        const uint32_t* vals = reinterpret_cast<const uint32_t*>(pool + in.off);
-        m = 0;
-        for (uint32_t k = 0; k < in.a; ++k) {
-            const uint32_t w = vals[k];
-            m |= mask8([&](int i) { return v[i] == w; });
-        }
+        uint32_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
+        in_list<G, 8>(v, reinterpret_cast<const uint32_t*>(pool + in.off), in.a,
+                      [](uint32_t x, uint32_t w) { return x == w; }, m);
         break;
     }
     case OP_INF: {
-        uint32_t v[8];
-        load8x32(col_base, c0, lane, v);
-        const float* vals = reinterpret_cast<const float*>(pool + in.off);
-        m = 0;
-        for (uint32_t k = 0; k < in.a; ++k) {
-            const float w = vals[k];
-            m |= mask8([&](int i) { return __uint_as_float(v[i]) == w; });
-        }
+        uint32_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
+        in_list<G, 8>(v, reinterpret_cast<const uint32_t*>(pool + in.off), in.a,
+                      [](uint32_t x, uint32_t w) { return __uint_as_float(x) == __uint_as_float(w); }, m);
         break;
     }
     case OP_IN64: {
-        uint64_t v[8];
-        load8x64(col_base, c0, lane, v);
-        const uint64_t* vals = reinterpret_cast<const uint64_t*>(pool + in.off);
-        m = 0;
-        for (uint32_t k = 0; k < in.a; ++k) {
-            const uint64_t w = vals[k];
-            m |= mask8([&](int i) { return v[i] == w; });
-        }
+        uint64_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x64(col_base, c0[g], lane, v[g]);
+        in_list<G, (G == 1 ? 8 : 4)>(v, reinterpret_cast<const uint64_t*>(pool + in.off), in.a,
+                      [](uint64_t x, uint64_t w) { return x == w; }, m);
         break;
     }
     case OP_BITMAP: {
-        uint32_t v[8];
-        load8x32(col_base, c0, lane, v);
+        uint32_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
         const uint32_t* words = reinterpret_cast<const uint32_t*>(pool + in.off);
         const uint32_t lo = in.a, nbits = in.b;
-        m = mask8([&](int i) {
-            const uint32_t d = v[i] - lo;
-            return d < nbits && ((words[d >> 5] >> (d & 31u)) & 1u);
-        });
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            m[g] = mask8([&](int i) {
+                const uint32_t d = v[g][i] - lo;
+                return d < nbits && ((words[d >> 5] >> (d & 31u)) & 1u);
+            });
+        break;
+    }
+    case OP_MASK32: {
+        uint32_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
+        const uint32_t lo = in.a, word = in.b;
+        // a clamped funnel shift: offsets >= 32 (values outside the word) give 0
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            m[g] = mask8_bits([&](int i) { return __funnelshift_rc(word, 0u, v[g][i] - lo) & 1u; });
+        break;
+    }
+    case OP_HASH32: {
+        uint32_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
+        const uint32_t* tab = reinterpret_cast<const uint32_t*>(pool + in.off);
+        const uint32_t mul = in.a, sh = in.b;
+#pragma unroll
+        for (int g = 0; g < G; ++g) m[g] = mask8([&](int i) { return tab[(v[g][i] * mul) >> sh] == v[g][i]; });
+        break;
+    }
+    case OP_HASH64: {
+        uint64_t v[G][8];
+#pragma unroll
+        for (int g = 0; g < G; ++g) load8x64(col_base, c0[g], lane, v[g]);
+        const uint64_t* tab = reinterpret_cast<const uint64_t*>(pool + in.off);
+        const uint32_t mul = in.a, sh = in.b;
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            m[g] = mask8([&](int i) {
+                const uint32_t k = static_cast<uint32_t>(v[g][i]) ^ static_cast<uint32_t>(v[g][i] >> 32);
+                return tab[(k * mul) >> sh] == v[g][i];
+            });
         break;
     }
     default:  // OP_CONST
-        m = 0xFFu;
+#pragma unroll
+        for (int g = 0; g < G; ++g) m[g] = 0xFFu;
         break;
     }
-    return in.neg ? (m ^ 0xFFu) : m;
+    if (in.neg) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) m[g] ^= 0xFFu;
+    }
 }
 
-// Runs a compiled program over one 256-row chunk; returns the lane's 8-bit
-// row mask.  stage_base: shared address of the staged tile; slot_off: byte
-// offset of each slot's column inside the stage.
+// Runs a compiled program over G 256-row chunks of a staged tile with one
+// pass over the instructions; m[g] is the lane's 8-bit row mask of chunk g.
+// stage_base: shared address of the staged tile; slot_off: byte offset of
+// each slot's column inside the stage.  The next instruction is fetched
+// while the current one is evaluated.
+template <int G>
+__device__ __forceinline__ void eval_program_g(const Instr* __restrict__ prog, uint32_t n_instr,
+                                               const uint8_t* __restrict__ pool, uint32_t stage_base,
+                                               const uint32_t* slot_off, const uint32_t (&c0)[G], uint32_t lane,
+                                               uint32_t (&top)[G]) {
+    uint64_t stk[G];     // up to 8 pending 8-bit masks per chunk
+    uint32_t memo[G];    // kMemoSlots saved 8-bit masks of repeated leaves
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        top[g] = 0;
+        stk[g] = 0;
+        memo[g] = 0;
+    }
+    if (n_instr == 0) return;
+    Instr nxt = prog[0];
+    for (uint32_t pc = 0; pc < n_instr; ++pc) {
+        const Instr in = nxt;
+        if (pc + 1 < n_instr) nxt = prog[pc + 1];
+        if (in.opc == OP_AND) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                top[g] &= static_cast<uint32_t>(stk[g]) & 0xFFu;
+                stk[g] >>= 8;
+            }
+        } else if (in.opc == OP_OR) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                top[g] |= static_cast<uint32_t>(stk[g]) & 0xFFu;
+                stk[g] >>= 8;
+            }
+        } else if (in.opc == OP_SAVE) {
+            const uint32_t sh = 8u * in.a;
+#pragma unroll
+            for (int g = 0; g < G; ++g) memo[g] = (memo[g] & ~(0xFFu << sh)) | (top[g] << sh);
+        } else if (in.opc == OP_LOAD) {
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                stk[g] = (stk[g] << 8) | top[g];
+                top[g] = (memo[g] >> (8u * in.a)) & 0xFFu;
+            }
+        } else {
+            uint32_t m[G];
+            eval_leaf_g<G>(in, stage_base + slot_off[in.slot], c0, lane, pool, m);
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                stk[g] = (stk[g] << 8) | top[g];
+                top[g] = m[g];
+            }
+        }
+    }
+}
+
+// One chunk: the lane's 8-bit row mask of the 256-row chunk at tile row c0.
 __device__ __forceinline__ uint32_t eval_program(const Instr* __restrict__ prog, uint32_t n_instr,
                                                  const uint8_t* __restrict__ pool, uint32_t stage_base,
                                                  const uint32_t* slot_off, uint32_t c0, uint32_t lane) {
-    uint32_t top = 0;
-    uint64_t stk = 0;    // up to 8 pending 8-bit masks
-    uint32_t memo = 0;   // kMemoSlots saved 8-bit masks of repeated leaves
-    for (uint32_t pc = 0; pc < n_instr; ++pc) {
-        const Instr in = prog[pc];
-        if (in.opc == OP_AND) {
-            top &= static_cast<uint32_t>(stk) & 0xFFu;
-            stk >>= 8;
-        } else if (in.opc == OP_OR) {
-            top |= static_cast<uint32_t>(stk) & 0xFFu;
-            stk >>= 8;
-        } else if (in.opc == OP_SAVE) {
-            const uint32_t sh = 8u * in.a;
-            memo = (memo & ~(0xFFu << sh)) | (top << sh);
-        } else if (in.opc == OP_LOAD) {
-            stk = (stk << 8) | top;
-            top = (memo >> (8u * in.a)) & 0xFFu;
-        } else {
-            const uint32_t m = eval_leaf(in, stage_base + slot_off[in.slot], c0, lane, pool);
-            stk = (stk << 8) | top;
-            top = m;
-        }
-    }
-    return top;
+    const uint32_t c[1] = {c0};
+    uint32_t m[1];
+    eval_program_g<1>(prog, n_instr, pool, stage_base, slot_off, c, lane, m);
+    return m[0];
 }
 
 // Mask of the lane's rows that lie below `valid` rows of the tile.

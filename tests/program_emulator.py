@@ -2,7 +2,8 @@
 
 Parses the text of ``sel_pred_describe`` and evaluates the postfix program
 row by row with the same per-opcode arithmetic the scan kernels use (32/64-bit
-wrap-around range tests, binary32 compares, bitmaps).  It models the
+wrap-around range tests, binary32 compares, bitmaps, multiply-shift hash
+tables).  It models the
 library's program format, not the paper: the tests compare its results with
 the oracle, so a compiler bug (a wrong bound, a lost negation, a misplaced
 operand) shows up without a GPU.
@@ -62,6 +63,19 @@ def _leaf_mask(op: str, kv: dict, col: np.ndarray) -> np.ndarray:
         inside = d < nb
         dd = np.where(inside, d, 0)
         m = inside & (((words[dd >> 5] >> (dd & 31).astype(np.uint64)) & np.uint64(1)) == 1)
+    elif op == "MASK32":
+        lo, word = int(kv["lo"]), int(kv["word"], 16)
+        d = (col.astype(np.int64) - lo) & 0xFFFFFFFF
+        dd = np.where(d < 32, d, 0)
+        m = (d < 32) & (((word >> dd) & 1) == 1)
+    elif op in ("HASH32", "HASH64"):
+        mult, sh = int(kv["mult"], 16), int(kv["shift"])
+        table = np.array([int(v) for v in kv["table"].split(",")], np.int64)
+        x = col.astype(np.int64)
+        u = x.view(np.uint64) if op == "HASH64" else (x & 0xFFFFFFFF).astype(np.uint64)
+        key = (u & np.uint64(0xFFFFFFFF)) ^ ((u >> np.uint64(32)) if op == "HASH64" else np.uint64(0))
+        h = ((key * np.uint64(mult)) & np.uint64(0xFFFFFFFF)) >> np.uint64(sh)
+        m = table[h.astype(np.int64)] == x
     else:
         raise ValueError(op)
     if kv.get("neg") == "1":

@@ -63,8 +63,13 @@ def test_not_is_pushed_to_the_leaves():
     (dg.p_cmp(0, "<>", 1 << 35), "CONST neg=0"),
     (dg.p_in(0, []), "CONST neg=1"),
     (dg.p_in(0, [3, 1, 2, 2]), "RANGE32 slot=0 neg=0 lo=1 span=2"),
-    (dg.p_in(0, [1, 5, 9]), "IN32"),
-    (dg.p_in(0, list(range(0, 40, 3))), "BITMAP"),
+    (dg.p_in(0, [1, 5, 9]), "MASK32 slot=0 neg=0 lo=1 word=0x111"),
+    (dg.p_in(0, [1, 5000]), "IN32"),
+    (dg.p_in(0, [1, 100, 5000]), "HASH32"),
+    (dg.p_in(0, list(range(0, 40, 3))), "HASH32"),
+    (dg.p_in(0, list(range(0, 3000, 3))), "BITMAP"),
+    (dg.p_in(1, [1, 5, 9]), "HASH64"),
+    (dg.p_in(1, [-(2 ** 62), 5]), "IN64"),
     (dg.p_between(0, 5, 4), "CONST neg=1"),
     (dg.p_between(2, 3.0, 1.0), "CONST neg=1"),
     (dg.p_cmp(2, "<", float("-inf")), "CONST neg=1"),
@@ -182,4 +187,26 @@ def test_repeated_leaves_are_evaluated_once():
     a = dg.p_in(2, [1, 5, 9])
     txt = _compile(t, dg.p_or(dg.p_and(a, dg.p_cmp(0, "<", 9)), dg.p_and(a, dg.p_cmp(1, ">", 9)),
                               dg.p_and(dg.p_not(a), dg.p_cmp(5, "=", 9)))).describe()
-    assert txt.count("IN64") == 2 and txt.count("LOAD") == 1     # NOT a is a different leaf
+    assert txt.count("HASH64") == 2 and txt.count("LOAD") == 1   # NOT a is a different leaf
+
+
+@pytest.mark.parametrize("n_vals", [3, 5, 8, 17, 64, 256])
+def test_hashed_in_lists_match_oracle(n_vals):
+    """IN lists lowered to perfect multiply-shift hash tables (int32 and int64
+    columns, values far apart, negated too): the emulated tables give the
+    oracle's counts, and members outside the table's rows still miss."""
+    t = dg.gen_table("cfg2", dg.config2_specs(), 4000, "cpu")
+    ot = oracle.OTable.from_table(t)
+    arrays = [c.data.numpy() for c in t.columns]
+    rng = np.random.default_rng(n_vals)
+    for col in (0, 2, 7):
+        data = arrays[col]
+        present = [int(x) for x in rng.choice(data, size=min(n_vals, 2 * n_vals // 3 + 1), replace=False)]
+        absent = [int(x) for x in rng.integers(-(2 ** 31), 2 ** 31, size=n_vals - len(present))]
+        vals = present + absent
+        for tr in (dg.p_in(col, vals), dg.p_not(dg.p_in(col, vals))):
+            txt = _compile(t, tr).describe()
+            if n_vals <= 64:   # a single multiply-shift table holds up to about 64 values within 8 KB
+                assert ("HASH64" if col == 2 else "HASH32") in txt, txt[:200]
+            got = emu.evaluate(txt, arrays, t.n_rows)
+            assert int(got.sum()) == oracle.count(ot, tr)

@@ -45,6 +45,60 @@ def test_scan_shapes_config2(ctx, medium, shape):
         assert ctx.count(p, T) == oracle.count(ot, tree, threads=8)
 
 
+VARIANTS = [(8, 1), (8, 2), (16, 1), (16, 2)]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("shape", [(256, 3, 1), (768, 4, 1), (4096, 3, 1), (1024, 4, 2), (16384, 3, 1)])
+def test_scan_variants_config2(ctx, medium, variant, shape):
+    """Every kernel variant (consumer warps x chunks per pass) on tiles with an
+    odd number of chunks (a half-empty last group) and a ragged last tile."""
+    t, ot, T = medium
+    ctx.set_scan_variant(*variant)
+    ctx.set_scan_shape(*shape)
+    try:
+        for s in (1e-3, 0.1):
+            tree = dg.config2_predicate(s, seed=3)
+            assert ctx.count(sel.Predicate(T, tree), T) == oracle.count(ot, tree, threads=8)
+    finally:
+        ctx.set_scan_variant(0, 0)
+        ctx.set_scan_shape(0, 0, 0)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_narrow_rows_in_large_tiles(ctx, medium, variant):
+    """One 4- or 8-byte column per row: tiles of up to 16384 rows (64-128 KB stages)."""
+    t, ot, T = medium
+    ctx.set_scan_variant(*variant)
+    for shape in ((16384, 3, 1), (12288, 2, 1), (0, 0, 0)):
+        ctx.set_scan_shape(*shape)
+        for tree in (dg.p_between(0, 1 << 28, 1 << 30), dg.p_cmp(2, "<", 1000), dg.p_cmp(3, ">=", dg.f32(5e4)),
+                     dg.p_not(dg.p_in(7, [3, 99, 1234, 777, 5]))):
+            assert ctx.count(sel.Predicate(T, tree), T) == oracle.count(ot, tree, threads=8), (shape, tree)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variants_tiny(ctx, dev, variant):
+    ctx.set_scan_variant(*variant)
+    try:
+        for n in (1, 255, 257, 513, 4097):
+            t = dg.tiny_table(n, seed=77 + n)
+            ot = oracle.OTable.from_table(t)
+            T = sel.Table(t.to(dev).columns)
+            rng = np.random.default_rng(77 + n)
+            for _ in range(20):
+                tree = dg.random_tree(t, rng, depth=4)
+                assert ctx.count(sel.Predicate(T, tree), T) == oracle.count(ot, tree), tree
+    finally:
+        ctx.set_scan_variant(0, 0)
+
+
+def test_bad_variant_is_rejected(ctx):
+    for w, g in [(4, 1), (8, 3), (0, 1), (32, 2)]:
+        with pytest.raises(sel.SelError):
+            ctx.set_scan_variant(w, g)
+
+
 def test_unaligned_columns_take_the_plain_path(ctx, medium):
     t, ot, _ = medium
     cols = [dg.Column(c.spec, c.data[1:], c.dictionary) for c in t.columns]   # base + 4/8 bytes
@@ -77,6 +131,31 @@ def test_constants_and_async(ctx, medium):
     ctx.count_async(sel.Predicate(T, tree), T, out)
     torch.cuda.synchronize()
     assert int(out.item()) == oracle.count(ot, tree, threads=8)
+
+
+@pytest.mark.parametrize("variant", [(16, 1), (8, 2)])
+@pytest.mark.parametrize("n_vals", [2, 3, 5, 17, 64, 100, 300])
+def test_set_lowerings(ctx, medium, variant, n_vals):
+    """IN lists in every lowering (MASK32 word, value compares, perfect hash
+    tables, bitmaps, long lists) on int32, int64, float and dictionary
+    columns, plain and negated, about two thirds of the values present."""
+    t, ot, T = medium
+    ctx.set_scan_variant(*variant)
+    rng = np.random.default_rng(500 + n_vals)
+    for col in range(8):
+        data = t.columns[col].data[:50_000].cpu().numpy()
+        k = min(n_vals, len(np.unique(data)))
+        present = rng.choice(np.unique(data), size=max(1, 2 * k // 3), replace=False).tolist()
+        if t.columns[col].type == "f32":
+            absent = [dg.f32(float(x)) for x in rng.random(n_vals - len(present)) * 7]
+        elif t.columns[col].type == "dict":
+            absent = [int(x) for x in rng.integers(0, len(t.columns[col].dictionary), n_vals - len(present))]
+        else:
+            absent = [int(x) for x in rng.integers(-(2 ** 31), 2 ** 31, n_vals - len(present))]
+        vals = present + absent
+        for tr in (dg.p_in(col, vals), dg.p_not(dg.p_in(col, vals)),
+                   dg.p_and(dg.p_in(col, vals), dg.p_cmp(5, ">", dg.DATE_BASE + 100))):
+            assert ctx.count(sel.Predicate(T, tr), T) == oracle.count(ot, tr, threads=8), (col, n_vals)
 
 
 def test_large_sets_and_prefixes(ctx, medium):
