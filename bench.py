@@ -345,6 +345,88 @@ def time_separate_vs_batched(step: OurStep, reps=5):
     return res
 
 
+def star_batch(sel, peak: float, device, reps=5):
+    """a5 on the star schema: 64 probes over a 480M-row fact table and four
+    dimension tables (2k, 200k, 2.4M, 16M rows) as one autotuned, graph-captured
+    launch sequence vs one count launch per probe on the same stream."""
+    tabs = dg.config3_tables(device=device)
+    T = [sel.Table(t.columns) for t in tabs]
+    probes = dg.config3_predicates()
+    preds = [sel.Predicate(T[ti], tr) for ti, tr in probes]
+    ptabs = [T[ti] for ti, _ in probes]
+    ctx = sel.Context()
+    t0 = time.perf_counter()
+    plan = sel.BatchPlan(ctx, preds, ptabs)
+    plan_s = time.perf_counter() - t0
+    out = torch.zeros(len(preds), dtype=torch.int64, device=device)
+    # bytes: each referenced column of each table once (shared pass) vs per probe
+    shared = 0
+    for ti, t in enumerate(tabs):
+        cols = sorted({c for tj, tr in probes if tj == ti for c in dg.tree_columns(tr)})
+        shared += sum(t.columns[c].spec.width for c in cols) * t.n_rows
+    separate_bytes = sum(sum(tabs[ti].columns[c].spec.width for c in dg.tree_columns(tr)) * tabs[ti].n_rows
+                         for ti, tr in probes)
+    res = {}
+    for mode in ("batched", "separate"):
+        def run():
+            if mode == "batched":
+                plan.run(out)
+            else:
+                for i, (p, tb) in enumerate(zip(preds, ptabs)):
+                    ctx.count_async(p, tb, out[i:i + 1])
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            run()
+        b.record()
+        torch.cuda.synchronize()
+        res[mode + "_ms"] = round(a.elapsed_time(b) / reps, 4)
+        res[mode + "_counts"] = out.cpu().tolist()
+    assert res["batched_counts"] == res["separate_counts"]
+    del res["batched_counts"], res["separate_counts"]
+    info = plan.info()
+    res.update({
+        "workload": "config3 star: fact 480M x 6 cols (i32 U/Zipf/U, f32 U/N/U) + dims 2k/200k/2.4M/16M x 4 cols; "
+                    "32 fact probes + 8 per dimension, OR of 1-3 ANDs, s log-uniform in [1e-4, 0.5]",
+        "speedup": round(res["separate_ms"] / res["batched_ms"], 3),
+        "batched_gbs_shared_pass": round(shared / res["batched_ms"] / 1e6, 1),
+        "batched_frac_shared_pass": round(shared / res["batched_ms"] / 1e6 / peak, 4),
+        "shared_pass_bytes": shared, "separate_bytes": separate_bytes,
+        "ms_per_estimate_batched": round(res["batched_ms"] / len(preds), 4),
+        "autotune_pick": info, "plan_create_s": round(plan_s, 2)})
+    del plan, T, tabs
+    torch.cuda.empty_cache()
+    return res
+
+
+def count_single(step: OurStep, peak: float, reps=5):
+    """a2 alone: each probe's exact count as its own launch (sel_count_async,
+    the library's default shape), GB/s of its referenced columns."""
+    sel, w = step.sel, step.w
+    out = torch.zeros(1, dtype=torch.int64, device=step.counts_dev.device)
+    res = []
+    for tree in w.trees:
+        p = sel.Predicate(step.T, tree)
+        nb = sum(WIDTH[w.types[c]] for c in dg.tree_columns(tree)) * w.n
+        for _ in range(2):
+            step.ctx.count_async(p, step.T, out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            step.ctx.count_async(p, step.T, out)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        res.append({"bytes": nb, "ms": round(ms, 4), "gbs": round(nb / ms / 1e6, 1), "frac": round(nb / ms / 1e6 / peak, 4)})
+    fr = [r["frac"] for r in res]
+    return {"kernel": "scan_count_kernel", "per_probe": res, "frac_min": min(fr), "frac_mean": round(statistics.mean(fr), 4),
+            "note": "one launch per probe on the context's stream, inputs larger than L2; frac of measured HBM"}
+
+
 # ----------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and --impl reference)
 # ----------------------------------------------------------------------------
@@ -424,6 +506,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-star", action="store_true", help="skip the star-schema batch measurement")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.steps <= 2, "at least 3 warm-up steps"
@@ -531,6 +614,9 @@ def main():
         out["surrogate"] = sur.summary()
     if rank == 0:
         out["batched_vs_separate"] = time_separate_vs_batched(step)
+        out["count_single"] = count_single(step, peak)
+        if not args.no_star:
+            out["star_batch"] = star_batch(sel, peak, dev)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(step, args, step_bytes)
     if rank == 0 and not args.no_cpu:

@@ -73,6 +73,7 @@ struct sel_ctx {
     int n_sm = 0;
     int max_smem = 0;         // opt-in shared memory per block
     int max_smem_scan = 0;    // dynamic shared memory available to the scan kernel
+    int max_smem_pdp = 0;     // dynamic shared memory available to the persistent push-down
     DevBuf counts;            // sel_count / batch staging
     DevBuf err;               // 4 bytes: error flag of the last launches
     DevBuf pd_scratch;        // push-down: tile status | tile counter | total
@@ -310,6 +311,7 @@ extern "C" sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out) {
     SEL_CUDA("cudaDeviceGetAttribute",
              cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     SEL_CUDA("scan smem attribute", scan_kernel_max_smem(c->max_smem, &c->max_smem_scan));
+    SEL_CUDA("push-down smem attribute", pushdown_persistent_max_smem(c->max_smem, &c->max_smem_pdp));
     sel_status s = c->err.ensure(256, "error flag");
     if (s != SEL_OK) return s;
     SEL_CUDA("cudaMemset", cudaMemset(c->err.p, 0, 256));
@@ -469,6 +471,83 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     a.n_slots = ta.n_slots;
     a.row_bytes = ta.row_bytes;
     a.tma = ta.tma;
+    // The persistent kernel: super-tiles of 16384 rows streamed in sub-tiles
+    // through shared-memory stages.  Variant: the context's scan variant, else
+    // 16 consumer warps x 2 chunks per pass.  Sub-tile: the requested tile size,
+    // else the largest power of two with 3 or more stages (else 2).  A tile
+    // size the persistent kernel cannot use, or predicate columns too wide for
+    // two stages, take the one-CTA-per-tile kernel (1024 rows or as requested).
+    {
+        const int req = ctx->shape.tile_rows;
+        const int W = ctx->shape.warps > 0 ? ctx->shape.warps : 16;
+        const int G = ctx->shape.group > 0 ? ctx->shape.group : 2;
+        int best_tr = 0, best_s = 0;
+        if (pushdown_persistent_ok(W, G) && ta.row_bytes > 0) {
+            for (int min_s = 3; min_s >= 2 && best_tr == 0; --min_s) {
+                for (int tr = kPdpSuperRows; tr >= kChunkRows; tr /= 2) {
+                    if (req != 0 && tr != req) continue;
+                    if (!pushdown_persistent_tile_ok((uint32_t)tr, G)) continue;
+                    PushdownArgs p = a;
+                    p.blob_bytes = pred->blob_bytes;
+                    p.row_bytes = ta.row_bytes;
+                    p.tile_rows = (uint32_t)tr;
+                    int S = ctx->shape.stages > 0 ? ctx->shape.stages : 6;
+                    for (; S >= min_s; --S) {
+                        p.stages = (uint32_t)S;
+                        if (pushdown_persistent_layout(p) <= (size_t)ctx->max_smem_pdp) break;
+                    }
+                    if (S >= min_s) {
+                        best_tr = tr;
+                        best_s = S;
+                        break;
+                    }
+                }
+            }
+        }
+        if (best_tr > 0) {
+            const int S = best_s;
+            a.tile_rows = (uint32_t)best_tr;
+            a.stages = (uint32_t)S;
+            a.blob = static_cast<const uint8_t*>(pred->d_blob);
+            a.instr_off = pred->instr_off;
+            a.pool_off = pred->pool_off;
+            a.blob_bytes = pred->blob_bytes;
+            a.n_instr = (uint32_t)pred->prog.instrs.size();
+            a.n_slots = ta.n_slots;
+            a.row_bytes = ta.row_bytes;
+            a.tma = ta.tma;
+            pushdown_persistent_layout(a);
+            uint32_t off = 0;
+            for (uint32_t j = 0; j < ta.n_slots; ++j) {
+                a.col[j] = ta.col[j];
+                a.width[j] = ta.width[j];
+                a.slot_off[j] = off;
+                off += a.tile_rows * ta.width[j];
+            }
+            a.n_rows = table->n_rows;
+            a.n_tiles = (table->n_rows + kPdpSuperRows - 1) / kPdpSuperRows;   // look-back unit: super-tiles
+            a.n_proj = (uint32_t)n_proj;
+            a.rowids = reinterpret_cast<long long*>(dev_out_rowids);
+            a.max_rows = max_rows;
+            a.skip_publish_tile = ctx->debug_skip_tile;
+            a.wait_ns = ctx->debug_wait_ns;
+            const size_t status_bytes = (size_t)a.n_tiles * 8;
+            s = ctx->pd_scratch.ensure(status_bytes + 64, "push-down scratch");
+            if (s != SEL_OK) return s;
+            uint8_t* scr = static_cast<uint8_t*>(ctx->pd_scratch.p);
+            a.status = reinterpret_cast<unsigned long long*>(scr);
+            a.tile_counter64 = reinterpret_cast<unsigned long long*>(scr + status_bytes);
+            a.total = d_total;
+            a.err = static_cast<unsigned int*>(ctx->err.p);
+            SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(scr, 0, status_bytes + 64, ctx->stream));
+            SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(d_total, 0, 8, ctx->stream));
+            const int grid = (int)std::min<int64_t>(a.n_tiles, (int64_t)ctx->n_sm);
+            cudaError_t e = launch_pushdown_persistent(a, grid, W, G, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail("push-down launch", e);
+            if (a.n_tiles > 0) ctx->launches++;
+            return SEL_OK;
+        }
+    }
     a.tile_rows = ctx->shape.tile_rows > 0 ? (uint32_t)std::min(ctx->shape.tile_rows, kPdMaxTileRows) : 1024u;
     {   // shrink the tile until its stage fits in shared memory
         const size_t fixed = ((size_t)pred->blob_bytes + 127) / 128 * 128 + 1024;

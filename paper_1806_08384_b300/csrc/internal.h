@@ -57,6 +57,11 @@ struct sel_pred {
     // (empty when the tree does not have that shape)
     std::vector<std::vector<sel::Clause>> dnf;
     bool dnf_ok = false;
+    // the learned estimator's clause records, built on first use (under mu)
+    bool feat_built = false, feat_ok = false;
+    int32_t feat_max_col = -1;
+    std::vector<uint8_t> feat_rec;
+    std::vector<uint64_t> feat_keys;
     std::string text;
     // lazily uploaded device blob: ProgDesc | Instr[] | pool
     std::mutex mu;

@@ -84,9 +84,28 @@ struct PushdownArgs {
     long long skip_publish_tile;
     unsigned long long wait_ns;
     uint32_t smem_prog_off, smem_stage_off, smem_out_off, smem_bytes;
+    // persistent kernel only: pipeline stages of tile_rows rows each
+    uint32_t stages, stage_bytes;
+    unsigned long long* tile_counter64;   // zeroed; tiles handed out in order
 };
 
 size_t pushdown_layout(PushdownArgs& a);
 cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
+
+// Persistent push-down: one CTA per SM with W consumer warps (8 or 16)
+// evaluating groups of G chunks (1 or 2), a producer warp and a look-back warp;
+// sub-tiles of tile_rows rows stream through `stages` shared-memory stages and
+// the look-back unit (n_tiles, status words) is a super-tile of kPdpMaxChunks
+// chunks = 16384 rows.
+constexpr int kPdpMaxChunks = 64;
+constexpr int kPdpSuperRows = kPdpMaxChunks * kChunkRows;
+bool pushdown_persistent_ok(int warps, int chunks_per_pass);
+// tile_rows: a multiple of chunks_per_pass chunks whose chunk count divides kPdpMaxChunks.
+bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass);
+// Fills the shared-memory offsets for a.stages stages of a.tile_rows rows; returns the bytes needed.
+size_t pushdown_persistent_layout(PushdownArgs& a);
+cudaError_t pushdown_persistent_max_smem(int optin, int* dyn_max);
+cudaError_t launch_pushdown_persistent(const PushdownArgs& a, int grid, int warps, int chunks_per_warp,
+                                       cudaStream_t st);
 
 }  // namespace sel

@@ -540,7 +540,72 @@ sel_status check_pred_schema(const sel_mlp* m, const sel_pred* p) {
     return SEL_OK;
 }
 
-// Host side of a6: clause records of n predicates (ok = 0 where a predicate has no feature form).
+// Feature form of one predicate: kSlots clause records (set_off relative to
+// the predicate's own key list) or false when the predicate has none.  Depends
+// only on the predicate (its dictionary codes and the column types it was
+// compiled against), so it is built once and kept with the predicate.
+bool pred_features(const sel_pred* p, FeatClause* rec, std::vector<uint64_t>& keys, int32_t& max_col) {
+    for (int s = 0; s < kSlots; ++s) rec[s] = FeatClause{};
+    keys.clear();
+    max_col = -1;
+    if (!p->dnf_ok || p->dnf.empty() || p->dnf.size() > 3) return false;
+    size_t total = 0;
+    for (auto& g : p->dnf) {
+        total += g.size();
+        for (auto& c : g) {
+            if (c.col >= kCols) return false;
+            max_col = std::max(max_col, c.col);
+        }
+    }
+    if (total > (size_t)kSlots) return false;
+    int s = 0;
+    for (size_t gi = 0; gi < p->dnf.size(); ++gi) {
+        for (const Clause& c : p->dnf[gi]) {
+            FeatClause& f = rec[s++];
+            f.present = 1;
+            f.col = c.col;
+            f.neg = c.nnf_neg;
+            f.group = (int32_t)gi;
+            const bool isf = p->col_types[c.col] == SEL_F32;
+            auto key = [&](int64_t iv, float fv) { return isf ? key_f32(fv) : key_int(iv); };
+            if (c.kind == SEL_N_CMP) {
+                f.opi = c.op;
+                f.mode = (c.op == SEL_EQ || c.op == SEL_NE) ? M_EQ
+                         : c.op == SEL_LT                  ? M_LT
+                         : c.op == SEL_LE                  ? M_LE
+                         : c.op == SEL_GT                  ? M_GT
+                                                           : M_GE;
+                f.ka = key(c.raw_i0, c.raw_f0);
+            } else if (c.kind == SEL_N_BETWEEN) {
+                f.opi = 6;
+                f.mode = M_BETWEEN;
+                f.ka = key(c.raw_i0, c.raw_f0);
+                f.kb = key(c.raw_i1, c.raw_f1);
+            } else {
+                f.opi = c.kind == SEL_N_IN ? 7 : 8;
+                f.mode = M_SET;
+                std::vector<uint64_t> ks;
+                if (c.kind == SEL_N_IN) {
+                    if (isf)
+                        for (float v : c.fvals) ks.push_back(key_f32(v));
+                    else
+                        for (int64_t v : c.ivals) ks.push_back(key_int(v));
+                } else {
+                    for (int32_t code : c.like_codes) ks.push_back(key_int(code));
+                }
+                std::sort(ks.begin(), ks.end());
+                ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
+                f.set_off = keys.size();
+                f.set_n = (int32_t)ks.size();
+                keys.insert(keys.end(), ks.begin(), ks.end());
+            }
+        }
+    }
+    return true;
+}
+
+// Host side of a6: clause records of n predicates (ok = 0 where a predicate
+// has no feature form), from each predicate's cached feature form.
 sel_status build_clauses(const sel_mlp* m, const sel_pred* const* preds, int32_t n, std::vector<FeatClause>& cl,
                          std::vector<uint64_t>& set_keys, std::vector<uint8_t>& ok) {
     cl.assign((size_t)n * kSlots, FeatClause{});
@@ -548,58 +613,20 @@ sel_status build_clauses(const sel_mlp* m, const sel_pred* const* preds, int32_t
     set_keys.clear();
     for (int32_t i = 0; i < n; ++i) {
         MLP_TRY(check_pred_schema(m, preds[i]));
-        const sel_pred* p = preds[i];
-        if (!p->dnf_ok || p->dnf.empty() || p->dnf.size() > 3) continue;
-        size_t total = 0;
-        bool cols_ok = true;
-        for (auto& g : p->dnf) {
-            total += g.size();
-            for (auto& c : g) cols_ok &= c.col < kCols && c.col < m->n_cols;
+        sel_pred* p = const_cast<sel_pred*>(preds[i]);
+        std::lock_guard<std::mutex> g(p->mu);
+        if (!p->feat_built) {
+            p->feat_rec.resize(kSlots * sizeof(FeatClause));
+            p->feat_ok = pred_features(p, reinterpret_cast<FeatClause*>(p->feat_rec.data()), p->feat_keys,
+                                       p->feat_max_col);
+            p->feat_built = true;
         }
-        if (total > (size_t)kSlots || !cols_ok) continue;
-        int s = 0;
-        for (size_t gi = 0; gi < p->dnf.size(); ++gi) {
-            for (const Clause& c : p->dnf[gi]) {
-                FeatClause& f = cl[(size_t)i * kSlots + s++];
-                f.present = 1;
-                f.col = c.col;
-                f.neg = c.nnf_neg;
-                f.group = (int32_t)gi;
-                const bool isf = m->types[c.col] == SEL_F32;
-                auto key = [&](int64_t iv, float fv) { return isf ? key_f32(fv) : key_int(iv); };
-                if (c.kind == SEL_N_CMP) {
-                    f.opi = c.op;
-                    f.mode = (c.op == SEL_EQ || c.op == SEL_NE) ? M_EQ
-                             : c.op == SEL_LT                  ? M_LT
-                             : c.op == SEL_LE                  ? M_LE
-                             : c.op == SEL_GT                  ? M_GT
-                                                               : M_GE;
-                    f.ka = key(c.raw_i0, c.raw_f0);
-                } else if (c.kind == SEL_N_BETWEEN) {
-                    f.opi = 6;
-                    f.mode = M_BETWEEN;
-                    f.ka = key(c.raw_i0, c.raw_f0);
-                    f.kb = key(c.raw_i1, c.raw_f1);
-                } else {
-                    f.opi = c.kind == SEL_N_IN ? 7 : 8;
-                    f.mode = M_SET;
-                    std::vector<uint64_t> ks;
-                    if (c.kind == SEL_N_IN) {
-                        if (isf)
-                            for (float v : c.fvals) ks.push_back(key_f32(v));
-                        else
-                            for (int64_t v : c.ivals) ks.push_back(key_int(v));
-                    } else {
-                        for (int32_t code : c.like_codes) ks.push_back(key_int(code));
-                    }
-                    std::sort(ks.begin(), ks.end());
-                    ks.erase(std::unique(ks.begin(), ks.end()), ks.end());
-                    f.set_off = set_keys.size();
-                    f.set_n = (int32_t)ks.size();
-                    set_keys.insert(set_keys.end(), ks.begin(), ks.end());
-                }
-            }
-        }
+        if (!p->feat_ok || p->feat_max_col >= m->n_cols) continue;
+        FeatClause* dst = &cl[(size_t)i * kSlots];
+        std::memcpy(dst, p->feat_rec.data(), kSlots * sizeof(FeatClause));
+        for (int s = 0; s < kSlots; ++s)
+            if (dst[s].mode == M_SET) dst[s].set_off += set_keys.size();
+        set_keys.insert(set_keys.end(), p->feat_keys.begin(), p->feat_keys.end());
         ok[i] = 1;
     }
     return SEL_OK;

@@ -17,56 +17,10 @@
 // straight to their output positions.  Rows at output
 // positions >= max_rows are not written; the count stays exact.
 #include "kernels.h"
+#include "lookback.cuh"
 #include "scan.cuh"
 
 namespace sel {
-
-constexpr unsigned long long kFlagAgg = 1ull << 62;
-constexpr unsigned long long kFlagInc = 2ull << 62;
-constexpr unsigned long long kValMask = (1ull << 62) - 1;
-
-__device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long long v) {
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Exclusive prefix of tile t (t >= 1) by warp 0; false if a wait timed out.
-__device__ bool look_back(const PushdownArgs& a, long long t, uint32_t lane, unsigned long long* excl_out) {
-    unsigned long long excl = 0;
-    long long base = t - 1;
-    const unsigned long long t0 = global_ns();
-    while (true) {
-        const long long idx = base - static_cast<long long>(lane);
-        unsigned long long v = (idx >= 0) ? ld_relaxed(&a.status[idx]) : kFlagInc;
-        while (__any_sync(0xFFFFFFFFu, (v >> 62) == 0)) {
-            if (global_ns() - t0 > a.wait_ns) {
-                *excl_out = excl;
-                return false;
-            }
-            if ((v >> 62) == 0) v = ld_relaxed(&a.status[idx]);
-        }
-        const uint32_t inc = __ballot_sync(0xFFFFFFFFu, (v >> 62) == 2);
-        if (inc) {
-            const uint32_t k = __ffs(inc) - 1;   // nearest predecessor with an inclusive prefix
-            unsigned long long x = (lane <= k) ? (v & kValMask) : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-            excl += x;
-            *excl_out = excl;
-            return true;
-        }
-        unsigned long long x = v & kValMask;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-        excl += x;
-        base -= 32;
-    }
-}
 
 __global__ void __launch_bounds__(kPdThreads, 6) pushdown_kernel(const __grid_constant__ PushdownArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -246,6 +200,434 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     if (a.n_tiles <= 0) return cudaSuccess;
     pushdown_kernel<<<static_cast<unsigned>(a.n_tiles), kPdThreads, a.smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+
+// ===========================================================================
+// Persistent push-down over super-tiles (the default path).
+//
+// The look-back unit is a super-tile of 16384 rows; a CTA streams a super-tile
+// through its shared-memory stages a sub-tile (tile_rows rows) at a time and
+// keeps only the row masks (1 bit per row) and the per-chunk counts of it, in
+// one of three super-tile buffers.
+//
+//   producer warp   takes super-tile ids in increasing order from a global
+//                   counter and bulk-copies each sub-tile's predicate columns
+//                   into the next free stage (full[s]);
+//   consumer warps  evaluate chunk groups of each sub-tile (ownership rotates
+//                   from sub-tile to sub-tile), store masks and chunk counts
+//                   into the super-tile's buffer and free the stage at once
+//                   (empty[s]); after their part of super-tile j (evald[b])
+//                   each warp writes its chunks' selected rows of super-tile
+//                   j-1, reading the projected values of those rows from
+//                   global memory, and releases that buffer (freeb[b]);
+//   look-back warp  sums super-tile j's chunk counts, publishes its aggregate,
+//                   finds its exclusive prefix by decoupled look-back,
+//                   publishes the inclusive prefix and the chunk prefixes
+//                   (done[b]) while the consumers already stream j+1.
+// No step waits for all consumer warps at once, so the stages keep streaming.
+// A CTA works on its super-tiles in increasing order, and what a super-tile
+// waits for (free stages, a free buffer, the look-backs of the CTA's earlier
+// super-tiles, the aggregates of smaller super-tiles) only involves smaller
+// super-tiles, so the smallest unfinished super-tile always makes progress.
+// Every wait is bounded; on a timeout the error flag is set, the CTA stops and
+// the producer waits for its copies still in flight.
+// ===========================================================================
+
+namespace {
+
+constexpr uint32_t kPdBufs = 3;   // super-tile buffers: evaluating j+1, look-back of j, scatter of j-1
+
+struct PdSmem {
+    uint64_t *full, *empty;              // [S]
+    uint64_t *evald, *done, *freeb;      // [kPdBufs]
+    long long* tile;                     // [S] super-tile id of each stage (-1: no more work)
+    long long* st_id;                    // [kPdBufs] super-tile id of each buffer (-1: end)
+    unsigned long long* excl;            // [kPdBufs] exclusive prefix of each buffer's super-tile
+    uint32_t* nch;                       // [kPdBufs] chunks of each buffer's super-tile that hold rows
+    uint32_t* cc;                        // [kPdBufs][kPdpMaxChunks] chunk counts (chunks in row order)
+    uint32_t* cp;                        // [kPdBufs][kPdpMaxChunks] chunk prefixes
+    uint8_t* mask;                       // [kPdBufs][kPdpMaxChunks * 32] 8-bit row mask per lane and chunk
+};
+
+__device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S) {
+    PdSmem m;
+    m.full = reinterpret_cast<uint64_t*>(smem);
+    m.empty = m.full + S;
+    m.evald = m.empty + S;
+    m.done = m.evald + kPdBufs;
+    m.freeb = m.done + kPdBufs;
+    m.tile = reinterpret_cast<long long*>(m.freeb + kPdBufs);
+    m.st_id = m.tile + S;
+    m.excl = reinterpret_cast<unsigned long long*>(m.st_id + kPdBufs);
+    m.nch = reinterpret_cast<uint32_t*>(m.excl + kPdBufs);
+    m.cc = m.nch + kPdBufs + 1;   // +1: 8-byte alignment of what follows is not needed, 4 is
+    m.cp = m.cc + kPdBufs * kPdpMaxChunks;
+    m.mask = reinterpret_cast<uint8_t*>(m.cp + kPdBufs * kPdpMaxChunks);
+    return m;
+}
+
+// Bounded wait by lane 0, verdict broadcast to the warp.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t lane) {
+    uint32_t ok = 0;
+    if (lane == 0) ok = mbar_wait_bounded(bar, parity) ? 1u : 0u;
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
+__device__ __forceinline__ void fail_flag(const PushdownArgs& a, uint32_t* s_fail) {
+    atomicOr(a.err, 1u);
+    atomicOr(s_fail, 1u);
+}
+
+__device__ __forceinline__ bool volatile_flag(const uint32_t* f) { return *reinterpret_cast<const volatile uint32_t*>(f) != 0; }
+
+// Writes the selected rows of chunk g of a super-tile (rows R0 + g * 256 ...)
+// whose masks and chunk prefixes are in buffer b.
+__device__ __forceinline__ void scatter_chunk(const PushdownArgs& a, const PdSmem& sm, uint32_t b, uint32_t g,
+                                              int64_t R0, unsigned long long excl, uint32_t lane) {
+    const uint32_t mk = sm.mask[(b * kPdpMaxChunks + g) * 32 + lane];
+    if (!__any_sync(0xFFFFFFFFu, mk != 0)) return;
+    // rank of the lane's rows in the chunk: half A (bits 0-3) rows come before half B
+    const uint32_t mine = __popc(mk & 0xFu) | (__popc(mk >> 4) << 16);
+    uint32_t x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= static_cast<uint32_t>(o)) x += y;
+    }
+    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, x, 31);
+    const uint32_t ex = x - mine;
+    const unsigned long long base = excl + sm.cp[b * kPdpMaxChunks + g];
+    unsigned long long posA = base + (ex & 0xFFFFu);
+    unsigned long long posB = base + (tot & 0xFFFFu) + (ex >> 16);
+    const int64_t rc = R0 + static_cast<int64_t>(g) * kChunkRows;
+    const unsigned long long lim = a.max_rows;
+    for (uint32_t bit = 0; bit < 8; ++bit) {
+        if (!((mk >> bit) & 1u)) continue;
+        const unsigned long long pos = (bit < 4) ? posA++ : posB++;
+        if (pos >= lim) continue;
+        const int64_t row = rc + bit_row(0, lane, bit);
+        for (uint32_t jj = 0; jj < a.n_proj; ++jj) {
+            if (a.proj_width[jj] == 8)
+                reinterpret_cast<unsigned long long*>(a.proj_dst[jj])[pos] =
+                    __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[jj]) + row);
+            else
+                reinterpret_cast<unsigned int*>(a.proj_dst[jj])[pos] =
+                    __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[jj]) + row);
+        }
+        if (a.rowids) a.rowids[pos] = static_cast<long long>(row);
+    }
+}
+
+}  // namespace
+
+// W consumer warps; a warp evaluates groups of G chunks with one pass over the
+// program, and group ownership rotates from sub-tile to sub-tile (as in the
+// count scan), so the sub-tile size (a.tile_rows, a power of two dividing the
+// super-tile, a multiple of G chunks) is independent of W and G.
+template <int W, int G>
+__global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(const __grid_constant__ PushdownArgs a) {
+    const uint32_t TR = a.tile_rows;                   // rows per sub-tile
+    const uint32_t NCH = TR / kChunkRows;              // chunks per sub-tile
+    constexpr uint32_t SR = kPdpSuperRows;             // rows per super-tile
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ uint32_t s_fail;
+    __shared__ long long s_issued;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t S = a.stages;
+    const PdSmem sm = pd_smem(smem, S);
+    uint8_t* stages = smem + a.smem_stage_off;
+    const long long n_super = a.n_tiles;
+
+    if (tid == 0) {
+        for (uint32_t s = 0; s < S; ++s) {
+            mbar_init(&sm.full[s], 1);
+            mbar_init(&sm.empty[s], W);
+        }
+        for (uint32_t b = 0; b < kPdBufs; ++b) {
+            mbar_init(&sm.evald[b], W);
+            mbar_init(&sm.done[b], 1);
+            mbar_init(&sm.freeb[b], W);
+        }
+        fence_mbar_init();
+        s_fail = 0;
+        s_issued = 0;
+    }
+    {
+        uint4* dst = reinterpret_cast<uint4*>(smem + a.smem_prog_off);
+        const uint4* src = reinterpret_cast<const uint4*>(a.blob);
+        for (uint32_t i = tid; i < a.blob_bytes / 16u; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const uint8_t* blob = smem + a.smem_prog_off;
+
+    if (warp == W) {
+        // ------------------------------- producer -------------------------------
+        // the super-tile is gathered again (selected rows only) soon after:
+        // keep it in L2 with the normal policy
+        const uint64_t pol = policy_evict_normal();
+        uint32_t s = 0, ph = 0;
+        long long k = 0;   // stage fills issued
+        bool stop = false;
+        while (!stop) {
+            unsigned long long st_id = 0;
+            if (lane == 0) st_id = atomicAdd(a.tile_counter64, 1ull);
+            st_id = __shfl_sync(0xFFFFFFFFu, st_id, 0);
+            const bool last = st_id >= static_cast<unsigned long long>(n_super);
+            const int64_t R0 = static_cast<int64_t>(st_id) * SR;
+            const uint32_t n_sub = last ? 1u
+                : static_cast<uint32_t>(((a.n_rows - R0 < (int64_t)SR ? a.n_rows - R0 : (int64_t)SR) + TR - 1) / TR);
+            for (uint32_t u = 0; u < n_sub; ++u, ++k) {
+                if (k >= static_cast<long long>(S) && !warp_wait(&sm.empty[s], ph ^ 1u, lane)) {
+                    if (lane == 0) fail_flag(a, &s_fail);
+                    stop = true;
+                    break;
+                }
+                if (volatile_flag(&s_fail)) {
+                    stop = true;
+                    break;
+                }
+                if (last) {
+                    if (lane == 0) {
+                        sm.tile[s] = -1;
+                        mbar_arrive(&sm.full[s]);   // release: the sentinel is visible to the waiters
+                    }
+                    stop = true;
+                } else {
+                    const int64_t r0 = R0 + static_cast<int64_t>(u) * TR;
+                    const uint32_t valid =
+                        static_cast<uint32_t>(a.n_rows - r0 < (int64_t)TR ? a.n_rows - r0 : (int64_t)TR);
+                    uint8_t* st = stages + static_cast<size_t>(s) * a.stage_bytes;
+                    if (lane == 0) sm.tile[s] = static_cast<long long>(st_id);
+                    if (a.tma && valid == TR && a.row_bytes > 0) {
+                        if (lane == 0) {
+                            mbar_arrive_expect_tx(&sm.full[s], TR * a.row_bytes);
+                            for (uint32_t j = 0; j < a.n_slots; ++j)
+                                bulk_g2s(st + a.slot_off[j], a.col[j] + r0 * a.width[j], TR * a.width[j], &sm.full[s],
+                                         pol);
+                        }
+                    } else {
+                        for (uint32_t j = 0; j < a.n_slots; ++j) {
+                            const uint32_t words = valid * a.width[j] / 4u;
+                            const uint32_t* src = reinterpret_cast<const uint32_t*>(a.col[j] + r0 * a.width[j]);
+                            uint32_t* dst = reinterpret_cast<uint32_t*>(st + a.slot_off[j]);
+                            for (uint32_t i = lane; i < words; i += 32) dst[i] = src[i];
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.full[s]);
+                    }
+                }
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+        }
+        if (lane == 0) s_issued = k;
+    } else if (warp == W + 1) {
+        // ------------------------------- look-back ------------------------------
+        for (uint32_t j = 0;; ++j) {
+            const uint32_t b = j % kPdBufs, par = (j / kPdBufs) & 1u;
+            if (!warp_wait(&sm.evald[b], par, lane)) {
+                if (lane == 0) fail_flag(a, &s_fail);
+                break;
+            }
+            const long long t = sm.st_id[b];
+            if (t < 0) break;
+            // chunk prefix in row order (chunks past the super-tile's rows count 0) and the total
+            const uint32_t nch = sm.nch[b];
+            uint32_t carry = 0;
+            for (uint32_t c0 = 0; c0 < kPdpMaxChunks; c0 += 32) {
+                const uint32_t c = c0 + lane;
+                const uint32_t v = c < nch ? sm.cc[b * kPdpMaxChunks + c] : 0u;
+                uint32_t inc = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+                    if (lane >= static_cast<uint32_t>(o)) inc += y;
+                }
+                sm.cp[b * kPdpMaxChunks + c] = carry + inc - v;
+                carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+            }
+            const uint32_t tile_cnt = carry;
+            if (lane == 0 && t != a.skip_publish_tile)
+                st_relaxed(&a.status[t], (t == 0 ? kFlagInc : kFlagAgg) | tile_cnt);
+            unsigned long long excl = 0;
+            bool ok = true;
+            if (t > 0) {
+                ok = look_back(a, t, lane, &excl);
+                if (lane == 0 && ok && t != a.skip_publish_tile)
+                    st_relaxed(&a.status[t], kFlagInc | ((excl + tile_cnt) & kValMask));
+            }
+            if (lane == 0) {
+                if (!ok) fail_flag(a, &s_fail);
+                sm.excl[b] = excl;
+                if (t == n_super - 1) *a.total = excl + tile_cnt;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.done[b]);   // release: offsets visible to the consumers
+            if (!ok) break;
+        }
+    } else {
+        // ------------------------------- consumers ------------------------------
+        const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
+        const uint8_t* pool = blob + a.pool_off;
+        uint32_t s = 0, ph = 0;
+        uint32_t rot = 0;   // running group count: group k of a sub-tile belongs to warp (rot + k) % W
+        long long prev_id = -1;
+        uint32_t prev_nch = 0;
+        for (uint32_t j = 0;; ++j) {
+            const uint32_t b = j % kPdBufs;
+            // ---- the buffer was last used by super-tile j-3: wait until every warp wrote its rows ----
+            if (j >= kPdBufs && !warp_wait(&sm.freeb[b], ((j / kPdBufs) - 1) & 1u, lane)) {
+                if (lane == 0) fail_flag(a, &s_fail);
+                break;
+            }
+            // ---- evaluate super-tile j, sub-tile by sub-tile ----
+            long long t = -1;
+            uint32_t n_sub = 1;
+            bool fail = false;
+            for (uint32_t u = 0; u < n_sub; ++u) {
+                if (!warp_wait(&sm.full[s], ph, lane)) {
+                    if (lane == 0) fail_flag(a, &s_fail);
+                    fail = true;
+                    break;
+                }
+                if (u == 0) {
+                    t = sm.tile[s];
+                    if (t >= 0) {
+                        const int64_t R0 = t * static_cast<int64_t>(SR);
+                        const int64_t rows = a.n_rows - R0 < (int64_t)SR ? a.n_rows - R0 : (int64_t)SR;
+                        n_sub = static_cast<uint32_t>((rows + TR - 1) / TR);
+                    }
+                }
+                if (t < 0) break;   // sentinel (its stage is never reused)
+                const int64_t r0 = t * static_cast<int64_t>(SR) + static_cast<int64_t>(u) * TR;
+                const uint32_t valid = static_cast<uint32_t>(a.n_rows - r0 < (int64_t)TR ? a.n_rows - r0 : (int64_t)TR);
+                const uint32_t n_groups = NCH / G;
+                const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
+                for (uint32_t grp = first; grp < n_groups; grp += W) {
+                    uint32_t c0[G], m[G];
+#pragma unroll
+                    for (int q = 0; q < G; ++q) c0[q] = (grp * G + q) * kChunkRows;
+                    eval_program_g<G>(ins, a.n_instr, pool, smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes),
+                                      a.slot_off, c0, lane, m);
+#pragma unroll
+                    for (int q = 0; q < G; ++q) {
+                        const uint32_t vm = (c0[q] + kChunkRows <= valid) ? 0xFFu
+                                            : c0[q] >= valid             ? 0u
+                                                                         : valid_mask(c0[q], lane, valid);
+                        m[q] &= vm;
+                        const uint32_t g = u * NCH + grp * G + q;   // chunk index in the super-tile (row order)
+                        sm.mask[(b * kPdpMaxChunks + g) * 32 + lane] = static_cast<uint8_t>(m[q]);
+                        const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(m[q])));
+                        if (lane == 0) sm.cc[b * kPdpMaxChunks + g] = c;
+                    }
+                }
+                rot += n_groups;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.empty[s]);   // the stage is no longer read
+                if (++s == S) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+            }
+            if (fail) break;
+            if (warp == 0 && lane == 0) {
+                sm.st_id[b] = t;
+                sm.nch[b] = t >= 0 ? n_sub * NCH : 0u;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.evald[b]);   // release: masks, counts, id visible
+            // ---- write this warp's chunks of super-tile j-1 ----
+            if (prev_id >= 0) {
+                const uint32_t pb = (j + kPdBufs - 1) % kPdBufs;
+                const bool ok = warp_wait(&sm.done[pb], ((j - 1) / kPdBufs) & 1u, lane);
+                if (!ok) {
+                    if (lane == 0) fail_flag(a, &s_fail);
+                    break;
+                }
+                if (!volatile_flag(&s_fail)) {
+                    const unsigned long long excl = sm.excl[pb];
+                    if (excl < a.max_rows)
+                        for (uint32_t g = warp; g < prev_nch; g += W)
+                            scatter_chunk(a, sm, pb, g, prev_id * static_cast<int64_t>(SR), excl, lane);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.freeb[pb]);
+            }
+            if (t < 0 || volatile_flag(&s_fail)) break;
+            prev_id = t;
+            prev_nch = n_sub * NCH;
+        }
+    }
+    __syncthreads();
+    if (s_fail && warp == W && lane == 0) {
+        // copies issued for stages nobody consumed must land before the CTA exits
+        const long long issued = s_issued;
+        for (long long k = issued > (long long)S ? issued - S : 0; k < issued; ++k)
+            mbar_wait_bounded(&sm.full[k % S], static_cast<uint32_t>((k / S) & 1));
+    }
+}
+
+static inline uint32_t align_up_u32(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+bool pushdown_persistent_ok(int warps, int chunks_per_pass) {
+    return (warps == 8 || warps == 16) && (chunks_per_pass == 1 || chunks_per_pass == 2);
+}
+
+bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass) {
+    const uint32_t nch = tile_rows / kChunkRows;
+    return tile_rows % kChunkRows == 0 && nch > 0 && kPdpMaxChunks % nch == 0 && nch % chunks_per_pass == 0;
+}
+
+size_t pushdown_persistent_layout(PushdownArgs& a) {
+    // must match pd_smem(): barriers, stage ids, buffer fields, counts, prefixes, masks
+    const uint32_t S = a.stages, B = 3;
+    const uint32_t meta = S * 16u + B * 24u + S * 8u + B * 8u + B * 8u + (B + 1u) * 4u + 2u * B * kPdpMaxChunks * 4u +
+                          B * kPdpMaxChunks * 32u;
+    a.smem_prog_off = align_up_u32(meta, 16u);
+    a.smem_stage_off = align_up_u32(a.smem_prog_off + align_up_u32(a.blob_bytes, 16u), 128u);
+    a.stage_bytes = align_up_u32(a.tile_rows * a.row_bytes, 128u);   // one sub-tile of the predicate columns
+    a.smem_bytes = a.smem_stage_off + S * a.stage_bytes;
+    return a.smem_bytes;
+}
+
+template <int W, int Q>
+static cudaError_t pdp_set_smem(int optin, int* dyn_max) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, pushdown_persistent_kernel<W, Q>);
+    if (e != cudaSuccess) return e;
+    const int lim = optin - static_cast<int>(fa.sharedSizeBytes);
+    *dyn_max = *dyn_max < 0 ? lim : (lim < *dyn_max ? lim : *dyn_max);
+    return cudaFuncSetAttribute(pushdown_persistent_kernel<W, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+cudaError_t pushdown_persistent_max_smem(int optin, int* dyn_max) {
+    *dyn_max = -1;
+    cudaError_t e = pdp_set_smem<8, 1>(optin, dyn_max);
+    if (e == cudaSuccess) e = pdp_set_smem<8, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = pdp_set_smem<16, 1>(optin, dyn_max);
+    if (e == cudaSuccess) e = pdp_set_smem<16, 2>(optin, dyn_max);
+    return e;
+}
+
+cudaError_t launch_pushdown_persistent(const PushdownArgs& a, int grid, int warps, int chunks_per_warp,
+                                       cudaStream_t st) {
+    if (a.n_tiles <= 0) return cudaSuccess;
+    if (warps == 8 && chunks_per_warp == 1)
+        pushdown_persistent_kernel<8, 1><<<grid, 10 * 32, a.smem_bytes, st>>>(a);
+    else if (warps == 8 && chunks_per_warp == 2)
+        pushdown_persistent_kernel<8, 2><<<grid, 10 * 32, a.smem_bytes, st>>>(a);
+    else if (warps == 16 && chunks_per_warp == 1)
+        pushdown_persistent_kernel<16, 1><<<grid, 18 * 32, a.smem_bytes, st>>>(a);
+    else if (warps == 16 && chunks_per_warp == 2)
+        pushdown_persistent_kernel<16, 2><<<grid, 18 * 32, a.smem_bytes, st>>>(a);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -79,6 +79,14 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     return pol;
 }
 
+// L2 policy for column data that is read again soon (the push-down's gather
+// of the selected rows' projected values).
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 // One bulk copy global -> shared (both 16-byte aligned, bytes % 16 == 0).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
                                          uint64_t pol) {

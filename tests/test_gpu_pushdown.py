@@ -32,7 +32,7 @@ def check_pushdown(ctx, T, ot, tree, proj, max_rows=None, rowids=True):
     return n
 
 
-@pytest.mark.parametrize("n", [0, 1, 3, 33, 255, 256, 257, 1023, 1025, 4097, 20_000])
+@pytest.mark.parametrize("n", [0, 1, 3, 33, 255, 256, 257, 1023, 1025, 4097, 20_000, 32768, 32769, 70_001])
 def test_random_trees_tiny(ctx, dev, n):
     t = dg.tiny_table(n, seed=n + 7)
     ot = oracle.OTable.from_table(t)
@@ -54,12 +54,30 @@ def proj_cfg2(t):
     return [t.index(c) for c in dg.CONFIG2_PROJECTION]
 
 
-@pytest.mark.parametrize("tile_rows", [256, 1024, 4096, 8192])
+@pytest.mark.parametrize("tile_rows", [0, 256, 1024, 1280, 2048, 4096, 8192])
 def test_config2_selectivities(ctx, medium, tile_rows):
     t, ot, T = medium
     ctx.set_scan_shape(tile_rows, 0, 0)
     for s in dg.CONFIG2_TARGETS:
         check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=11), proj_cfg2(t))
+
+
+@pytest.mark.parametrize("variant", [(16, 2), (16, 1), (8, 2), (8, 1)])
+def test_persistent_variants(ctx, dev, medium, variant):
+    """Every persistent push-down variant (consumer warps x chunks per warp), on
+    the 1,000,003-row table (ragged last super-tile and sub-tile) and on sizes at
+    super-tile boundaries."""
+    t, ot, T = medium
+    ctx.set_scan_variant(*variant)
+    for s in (1e-3, 0.1):
+        check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=21), proj_cfg2(t))
+    for n in (32768, 65537):
+        tt = dg.tiny_table(n, seed=n)
+        ott = oracle.OTable.from_table(tt)
+        TT = sel.Table(tt.to(dev).columns)
+        rng = np.random.default_rng(n)
+        for _ in range(6):
+            check_pushdown(ctx, TT, ott, dg.random_tree(tt, rng, depth=4), [0, 1, 2, 3, 4])
 
 
 def test_projection_of_non_predicate_columns_and_no_rowids(ctx, medium):
@@ -107,15 +125,18 @@ def test_unaligned_columns(ctx, medium):
         check_pushdown(ctx, T, sub, dg.config2_predicate(s, seed=13), proj_cfg2(t))
 
 
-def test_lookback_wait_times_out_and_context_recovers(ctx, dev):
+@pytest.mark.parametrize("tile_rows", [1024, 2048, 4096, 1280])
+def test_lookback_wait_times_out_and_context_recovers(ctx, dev, tile_rows):
     """A tile that never publishes makes its successors' bounded waits run out:
-    the call returns SEL_ERR_TIMEOUT, and the context works afterwards."""
-    t = dg.tiny_table(8 * 1024, seed=3)
+    the call returns SEL_ERR_TIMEOUT, and the context works afterwards (the
+    persistent kernel's variants, whose look-back unit is a 16384-row
+    super-tile, and the one-CTA-per-tile kernel)."""
+    t = dg.tiny_table(4 * 32768 + 1000, seed=3)
     ot = oracle.OTable.from_table(t)
     T = sel.Table(t.to(dev).columns)
     tree = dg.p_cmp(0, "<", 2)
     p = sel.Predicate(T, tree)
-    ctx.set_scan_shape(1024, 0, 0)
+    ctx.set_scan_shape(tile_rows, 0, 0)
     ctx.debug_pushdown_fault(2, 50_000_000)          # tile 2 never publishes; waits give up after 50 ms
     with pytest.raises(sel.SelError) as e:
         ctx.pushdown(p, T, [0], T.n_rows)
