@@ -473,7 +473,7 @@ def cpu_rate(ot, types, trees, proj, threads, reps=1):
 def kernel_source_hash(name):
     import hashlib
     h = hashlib.sha256()
-    for f in ("scan.cuh", "program.h", "kernels.h", name):
+    for f in ("scan.cuh", "program.h", "kernels.h", "lookback.cuh", name):
         with open(os.path.join(ROOT, "paper_1806_08384_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -576,7 +576,7 @@ def main():
     kernels = {
         "count": {"name": "scan_count_kernel", "ms": count_ms, "bytes": b_batch, "launches": len(dur["count"]),
                   "total_ms": sum(dur["count"]), "source": "count.cu"},
-        "pushdown": {"name": "pushdown_kernel", "ms": pd_ms, "bytes": (sum(b_pds) / len(b_pds)) if b_pds else 0,
+        "pushdown": {"name": "pushdown_persistent_kernel", "ms": pd_ms, "bytes": (sum(b_pds) / len(b_pds)) if b_pds else 0,
                      "launches": len(dur["pushdown"]), "total_ms": sum(dur["pushdown"]), "source": "pushdown.cu"},
     }
 

@@ -261,12 +261,55 @@ sel_status sel_ctx_set_scan_variant(sel_ctx* ctx, int32_t consumer_warps, int32_
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
 
-/* Test hook for the bounded waits of the push-down look-back: tile skip_tile
- * (-1: none) never publishes its prefix, and a waiting tile gives up after
+/* Test hook for the bounded waits of the push-down look-back: look-back unit
+ * skip_tile (a 16384-row super-tile of the default kernel, a tile of the
+ * one-CTA-per-tile kernel; -1: none) never publishes its prefix, and a waiting tile gives up after
  * wait_ns nanoseconds (0: the default of 2 s), so that later sel_pushdown
  * calls on this context return SEL_ERR_TIMEOUT instead of waiting forever.
  * The context stays usable; set skip_tile back to -1 to disarm. */
 sel_status sel_ctx_debug_pushdown_fault(sel_ctx* ctx, int64_t skip_tile, uint64_t wait_ns);
+
+/* ---------------------------------------------------------------------------
+ * Algorithm 1, EvaluateAndPushDown (Ch4 §4.2): the push-down decision for the
+ * scanned relations of one query.  Relations whose size is greater than
+ * min_table_size (PUSH_DOWN_MIN_TABLE_SIZE) are ordered by size, largest
+ * first (equal sizes keep their input order); the largest is the probed
+ * relation and is never pushed down.  Each other one with a predicate is
+ * pushed down with sel_pushdown and maxSize = floor(size * max_selectivity)
+ * (PUSH_DOWN_MAX_SELECTIVITY as a ratio), or max_rows when that is not 0 (the
+ * absolute form the paper also names): count > maxSize reverts the push-down
+ * (its outputs are then unspecified), otherwise the projected columns of the
+ * selected rows are in the relation's outputs.
+ * ------------------------------------------------------------------------- */
+typedef enum {
+    SEL_SPD_PROBE = 0,          /* the largest relation: not pushed down */
+    SEL_SPD_TOO_SMALL = 1,      /* size <= min_table_size: not considered */
+    SEL_SPD_NO_PREDICATE = 2,   /* nothing to push down */
+    SEL_SPD_PUSHED = 3,         /* count <= maxSize: rows materialised */
+    SEL_SPD_REVERTED = 4        /* count > maxSize: push-down reverted */
+} sel_spd_decision;
+
+typedef struct {
+    const sel_table* table;        /* the scanned relation (device columns) */
+    const sel_pred* pred;          /* its pushed-down selection; NULL: none */
+    const int32_t* proj_cols;      /* columns needed above the relation (host) */
+    int32_t n_proj;
+    void* const* dev_out_cols;     /* caller-owned device outputs, capacity >= maxSize rows each */
+    int64_t* dev_out_rowids;       /* caller-owned, capacity >= maxSize; may be NULL */
+} sel_spd_relation;
+
+typedef struct {
+    uint64_t min_table_size;       /* PUSH_DOWN_MIN_TABLE_SIZE */
+    double max_selectivity;        /* PUSH_DOWN_MAX_SELECTIVITY (ratio, >= 0) */
+    uint64_t max_rows;             /* absolute maxSize instead of the ratio when not 0 */
+} sel_spd_cfg;
+
+/* decisions[i] (sel_spd_decision), counts[i] (exact count of each relation that
+ * was executed, else 0) and, when not NULL, max_sizes[i] are written for the n
+ * relations.  Synchronous.  Errors of a push-down (other than the count being
+ * too large) stop the pass and are returned. */
+sel_status sel_evaluate_and_push_down(sel_ctx* ctx, const sel_spd_relation* rels, int32_t n, const sel_spd_cfg* cfg,
+                                      int32_t* decisions, uint64_t* counts, uint64_t* max_sizes);
 
 /* ---------------------------------------------------------------------------
  * Learned estimator (not in the paper, whose selectivity is always the exact

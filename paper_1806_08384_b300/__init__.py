@@ -13,6 +13,7 @@ Predicate trees use the neutral nested-tuple form (see ``tree_to_postfix``):
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from typing import List, Optional, Sequence
 
@@ -59,6 +60,19 @@ def train_cfg(epochs=5, batch=4096, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, s
     return TrainCfg(epochs, batch, lr, beta1, beta2, eps, seed, apply_update, 0)
 
 
+class sel_spd_relation(C.Structure):
+    _fields_ = [("table", C.POINTER(sel_table)), ("pred", C.c_void_p), ("proj_cols", C.POINTER(C.c_int32)),
+                ("n_proj", C.c_int32), ("dev_out_cols", C.POINTER(C.c_void_p)), ("dev_out_rowids", C.c_void_p)]
+
+
+class sel_spd_cfg(C.Structure):
+    _fields_ = [("min_table_size", C.c_uint64), ("max_selectivity", C.c_double), ("max_rows", C.c_uint64)]
+
+
+SPD_PROBE, SPD_TOO_SMALL, SPD_NO_PREDICATE, SPD_PUSHED, SPD_REVERTED = range(5)
+SPD_NAMES = ("probe", "too_small", "no_predicate", "pushed", "reverted")
+
+
 class SelError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: {STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
@@ -97,6 +111,8 @@ def _load():
         "sel_ctx_launch_count": (C.c_uint64, [V]),
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
+        "sel_evaluate_and_push_down": (C.c_int, [V, P(sel_spd_relation), C.c_int32, P(sel_spd_cfg), P(C.c_int32),
+                                                 P(C.c_uint64), P(C.c_uint64)]),
         "sel_mlp_create": (C.c_int, [V, P(sel_table), C.c_int32, C.c_uint64, P(V)]),
         "sel_mlp_free": (None, [V]),
         "sel_mlp_featurize": (C.c_int, [V, V, P(V), C.c_int32, V, V]),
@@ -577,3 +593,46 @@ def count_many(ctx: "Context", preds: Sequence[Predicate], table, chunk: int = 2
         part = list(preds[i:i + chunk])
         out += BatchPlan(ctx, part, [T] * len(part), autotune=False).run()
     return out
+
+
+def evaluate_and_push_down(ctx: "Context", relations, min_table_size: int = 0, max_selectivity: float = 0.0,
+                           max_rows: int = 0, rowids: bool = True):
+    """Algorithm 1 EvaluateAndPushDown over relations given as (table, predicate
+    or None, projected columns).  Returns one dict per relation: decision,
+    count, max_size, and for pushed relations the projected columns and row ids
+    (device tensors truncated to the count)."""
+    n = len(relations)
+    tabs = [Table.of(t) for t, _, _ in relations]
+    rels = (sel_spd_relation * max(1, n))()
+    keep = []
+    outs = []
+    for i, ((_, pred, proj), T) in enumerate(zip(relations, tabs)):
+        size = T.n_rows
+        cap = max_rows if max_rows else int(math.floor(size * max_selectivity))
+        dev = T.columns[0].data.device if T.columns else torch.device("cuda")
+        cols = [torch.empty(max(cap, 1), dtype=TORCH_TYPES[T.types[c]], device=dev) for c in proj]
+        ids = torch.empty(max(cap, 1), dtype=torch.int64, device=dev) if rowids else None
+        pc = (C.c_int32 * max(1, len(proj)))(*proj)
+        po = (C.c_void_p * max(1, len(proj)))(*[t.data_ptr() for t in cols])
+        keep += [pc, po, T]
+        outs.append((cols, ids))
+        rels[i].table = C.pointer(T.desc)
+        rels[i].pred = pred.h if pred is not None else None
+        rels[i].proj_cols = pc
+        rels[i].n_proj = len(proj)
+        rels[i].dev_out_cols = po
+        rels[i].dev_out_rowids = ids.data_ptr() if ids is not None else None
+    cfg = sel_spd_cfg(int(min_table_size), float(max_selectivity), int(max_rows))
+    dec = (C.c_int32 * max(1, n))()
+    cnt = (C.c_uint64 * max(1, n))()
+    msz = (C.c_uint64 * max(1, n))()
+    _check(lib.sel_evaluate_and_push_down(ctx.h, rels, n, C.byref(cfg), dec, cnt, msz), "sel_evaluate_and_push_down")
+    res = []
+    for i in range(n):
+        d = {"decision": SPD_NAMES[dec[i]], "count": int(cnt[i]), "max_size": int(msz[i])}
+        if dec[i] == SPD_PUSHED:
+            cols, ids = outs[i]
+            d["columns"] = [c[:d["count"]] for c in cols]
+            d["rowids"] = ids[:d["count"]] if ids is not None else None
+        res.append(d)
+    return res

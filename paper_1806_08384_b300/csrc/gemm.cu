@@ -110,7 +110,13 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     if (s_fail) {
         if (tid == 0) atomicOr(g.err, 1u);
     } else {
-        const int row = m0 + (int)(warp * 32 + lane);
+        // Each warp owns 32 accumulator rows; 32 columns at a time go through a
+        // padded shared tile so that global stores run along rows (coalesced)
+        // and column sums are one add per lane.  The stage buffers are free:
+        // every MMA has completed.
+        float* tile = reinterpret_cast<float*>(smem_raw + (base - smem_u32(smem_raw))) + warp * (32 * 33);
+        const int rbase = m0 + (int)(warp * 32);
+        const int row = rbase + (int)lane;
         const bool row_ok = row < g.M;
 #pragma unroll 1
         for (int cc = 0; cc < BN / 32; ++cc) {
@@ -122,52 +128,53 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
                 for (int j = 0; j < 32; ++j) f[j] = 0.f;
             }
             const int c0 = n0 + cc * 32;
-            if (g.epi == EPI_F32) {
-                if (row_ok)
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = c0 + j;
-                        if (col < g.N) {
-                            float* dst = g.C + (size_t)row * g.ldc + col;
-                            if (gridDim.z > 1) atomicAdd(dst, f[j]);
-                            else *dst = f[j];
-                        }
-                    }
-            } else {
-                // EPI_BIAS_RELU: relu(acc + bias); EPI_DRELU: acc where mask > 0 (plus column sums)
+            const int col = c0 + (int)lane;   // this lane's column in the row-wise phase
+            if (g.epi == EPI_DRELU) {   // the 32 x 32 mask block, read along rows, into the tile
+                for (int r = 0; r < 32; ++r)
+                    tile[r * 33 + lane] = (rbase + r < g.M && col < g.N)
+                        ? __bfloat162float(g.mask[(size_t)(rbase + r) * g.ldm + col]) : 0.f;
+                __syncwarp();
+            }
+            if (g.epi != EPI_F32) {
+                // EPI_BIAS_RELU: relu(acc + bias); EPI_DRELU: acc where mask > 0
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const int col = c0 + j;
+                    const int cj = c0 + j;
                     float v = f[j];
-                    if (g.epi == EPI_BIAS_RELU) {
-                        v = fmaxf(v + (col < g.N ? g.bias[col] : 0.f), 0.f);
-                    } else if (row_ok && col < g.N) {
-                        const float mk = __bfloat162float(g.mask[(size_t)row * g.ldm + col]);
-                        v = mk > 0.f ? v : 0.f;
-                    }
+                    if (g.epi == EPI_BIAS_RELU) v = fmaxf(v + (cj < g.N ? g.bias[cj] : 0.f), 0.f);
+                    else v = tile[lane * 33 + j] > 0.f ? v : 0.f;
                     if (!row_ok) v = 0.f;
                     f[j] = v;
                 }
-                if (g.epi == EPI_DRELU && g.colsum) {
+                __syncwarp();
+                if (row_ok && g.outT)   // lanes write consecutive rows of the transposed matrix: coalesced
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        float s = f[j];
+                    for (int j = 0; j < 32; ++j)
+                        if (c0 + j < g.N) g.outT[(size_t)(c0 + j) * g.ldoT + row] = __float2bfloat16_rn(f[j]);
+            }
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-                        if (lane == 0 && c0 + j < g.N) atomicAdd(&g.colsum[c0 + j], s);
+            for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = f[j];
+            __syncwarp();
+            // row-wise phase: lane = column
+            if (g.epi == EPI_F32) {
+                if (col < g.N)
+                    for (int r = 0; r < 32 && rbase + r < g.M; ++r) {
+                        float* dst = g.C + (size_t)(rbase + r) * g.ldc + col;
+                        if (gridDim.z > 1) atomicAdd(dst, tile[r * 33 + lane]);
+                        else *dst = tile[r * 33 + lane];
                     }
-                }
-                if (row_ok) {
-                    if (g.out)
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (c0 + j < g.N) g.out[(size_t)row * g.ldo + c0 + j] = __float2bfloat16_rn(f[j]);
-                    if (g.outT)   // lanes write consecutive rows of the transposed matrix: coalesced
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (c0 + j < g.N) g.outT[(size_t)(c0 + j) * g.ldoT + row] = __float2bfloat16_rn(f[j]);
+            } else {
+                if (g.out && col < g.N)
+                    for (int r = 0; r < 32 && rbase + r < g.M; ++r)
+                        g.out[(size_t)(rbase + r) * g.ldo + col] = __float2bfloat16_rn(tile[r * 33 + lane]);
+                if (g.epi == EPI_DRELU && g.colsum && col < g.N) {
+                    float sum = 0.f;
+#pragma unroll 8
+                    for (int r = 0; r < 32; ++r) sum += tile[r * 33 + lane];   // rows past M hold 0
+                    atomicAdd(&g.colsum[col], sum);
                 }
             }
+            __syncwarp();
         }
     }
     tc_fence_before();

@@ -125,20 +125,33 @@ __device__ inline int upper_bound_u64(const uint64_t* a, int n, uint64_t k) {
     return lo;
 }
 
-// One thread per (predicate, slot): writes the slot's 24 features (bf16).
+// One warp per (predicate, slot): writes the slot's 24 features (bf16).  The
+// lanes split a set's values (an IN list, or the codes of a LIKE prefix);
+// lane 0 does the other comparisons.
 __global__ void featurize_kernel(const FeatClause* cl, const uint64_t* set_keys, const uint64_t* cdf, int32_t m,
                                  int32_t n, __nv_bfloat16* feat) {
-    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= static_cast<int64_t>(n) * kSlots) return;
+    const int64_t t = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t lane = threadIdx.x & 31u;
+    if (t >= static_cast<int64_t>(n) * kSlots) return;   // whole warps leave together
     const FeatClause c = cl[t];
+    const uint64_t* s = cdf + static_cast<size_t>(c.present ? c.col : 0) * m;
+    const float fm = static_cast<float>(m);
+    auto frac = [&](int k) { return static_cast<float>(k) / fm; };
+    float lo = 0.f, hi = 0.f;
+    if (c.present && c.mode == M_SET) {   // sample mass of a set of values
+        int cnt = 0;
+        for (int j = static_cast<int>(lane); j < c.set_n; j += 32) {
+            const uint64_t k = set_keys[c.set_off + j];
+            cnt += upper_bound_u64(s, m, k) - lower_bound_u64(s, m, k);
+        }
+        cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+        hi = frac(min(cnt, m));
+    }
+    if (lane != 0) return;
     float f[kSlot];
 #pragma unroll
     for (int i = 0; i < kSlot; ++i) f[i] = 0.f;
     if (c.present) {
-        const uint64_t* s = cdf + static_cast<size_t>(c.col) * m;
-        const float fm = static_cast<float>(m);
-        auto frac = [&](int k) { return static_cast<float>(k) / fm; };
-        float lo = 0.f, hi = 0.f;
         switch (c.mode) {
         case M_EQ: lo = frac(lower_bound_u64(s, m, c.ka)); hi = frac(upper_bound_u64(s, m, c.ka)); break;
         case M_LT: hi = frac(lower_bound_u64(s, m, c.ka)); break;
@@ -151,14 +164,7 @@ __global__ void featurize_kernel(const FeatClause* cl, const uint64_t* set_keys,
             hi = frac(max(a, upper_bound_u64(s, m, c.kb)));
             break;
         }
-        default: {   // M_SET: sample mass of a set of values
-            int cnt = 0;
-            for (int j = 0; j < c.set_n; ++j) {
-                const uint64_t k = set_keys[c.set_off + j];
-                cnt += upper_bound_u64(s, m, k) - lower_bound_u64(s, m, k);
-            }
-            hi = frac(min(cnt, m));
-        }
+        default: break;   // M_SET: done above
         }
         // log selectivity of the leaf from the sample, in [-1, 0]: ln(max(p, 1/(2m))) / ln(2m),
         // p = hi - lo, complemented for <> and for a negated leaf (evaluated in double)
@@ -180,21 +186,22 @@ __global__ void featurize_kernel(const FeatClause* cl, const uint64_t* set_keys,
 }
 
 // out[i] = (mu, raw log-variance) = a3[i] . W4^T + b4 (one row per thread).
-// With y != nullptr also the training head: loss, dO, dZ3 = (dO W4) * (a3 > 0)
-// written as bf16 rows and columns, and the db3, dW4, db4 and loss sums.
+// With y != nullptr also the training head: the loss and dO of each row, then
+// (one hidden unit per thread, over the block's rows) dZ3 = (dO W4) * (a3 > 0)
+// as bf16 rows and the db3, dW4, db4 and loss sums.
 __global__ void __launch_bounds__(128) head_kernel(const __nv_bfloat16* a3, const __nv_bfloat16* w4b,
                                                    const float* b4, int32_t n, float* out, const float* y,
-                                                   int32_t bsz, __nv_bfloat16* dz3, __nv_bfloat16* dz3t,
-                                                   float* g_b3, float* g_w4, float* g_b4, float* loss_sum) {
+                                                   int32_t bsz, __nv_bfloat16* dz3, float* g_b3, float* g_w4,
+                                                   float* g_b4, float* loss_sum) {
     __shared__ float w[2][kHid];
-    __shared__ float acc[3][kHid];   // db3, dW4[0], dW4[1]
+    __shared__ float sd[2][128];   // dO of the block's rows
     for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
         w[0][k] = __bfloat162float(w4b[k]);
         w[1][k] = __bfloat162float(w4b[kHid + k]);
-        acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r0 = blockIdx.x * blockDim.x;
+    const int i = r0 + threadIdx.x;
     const bool ok = i < n;
     const __nv_bfloat16* row = a3 + static_cast<size_t>(ok ? i : 0) * kHid;
     float o0 = 0.f, o1 = 0.f;
@@ -224,32 +231,9 @@ __global__ void __launch_bounds__(128) head_kernel(const __nv_bfloat16* a3, cons
         d0 = -r * inv / static_cast<float>(bsz);
         d1 = (o1 > kLvMin && o1 < kLvMax) ? 0.5f * (1.f - r * r * inv) / static_cast<float>(bsz) : 0.f;
     }
+    sd[0][threadIdx.x] = d0;
+    sd[1][threadIdx.x] = d1;
     const uint32_t lane = threadIdx.x & 31u;
-    for (int k = 0; k < kHid; k += 8) {
-        const uint4 v = *reinterpret_cast<const uint4*>(row + k);
-        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&v);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const float a = ok ? __bfloat162float(h[j]) : 0.f;
-            const float dz = (a > 0.f) ? d0 * w[0][k + j] + d1 * w[1][k + j] : 0.f;
-            if (ok) {
-                dz3[static_cast<size_t>(i) * kHid + k + j] = __float2bfloat16_rn(dz);
-                dz3t[static_cast<size_t>(k + j) * bsz + i] = __float2bfloat16_rn(dz);
-            }
-            float s0 = dz, s1 = d0 * a, s2 = d1 * a;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
-                s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
-                s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
-            }
-            if (lane == 0) {
-                atomicAdd(&acc[0][k + j], s0);
-                atomicAdd(&acc[1][k + j], s1);
-                atomicAdd(&acc[2][k + j], s2);
-            }
-        }
-    }
     float t0 = d0, t1 = d1, tl = li;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -263,10 +247,23 @@ __global__ void __launch_bounds__(128) head_kernel(const __nv_bfloat16* a3, cons
         atomicAdd(loss_sum, tl);
     }
     __syncthreads();
+    const int nr = min(static_cast<int>(blockDim.x), n - r0);
     for (int k = threadIdx.x; k < kHid; k += blockDim.x) {
-        atomicAdd(&g_b3[k], acc[0][k]);
-        atomicAdd(&g_w4[k], acc[1][k]);
-        atomicAdd(&g_w4[kHid + k], acc[2][k]);
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        const float w0 = w[0][k], w1 = w[1][k];
+        for (int r = 0; r < nr; ++r) {
+            const size_t at = static_cast<size_t>(r0 + r) * kHid + k;
+            const float a = __bfloat162float(a3[at]);
+            const float e0 = sd[0][r], e1 = sd[1][r];
+            const float dz = (a > 0.f) ? e0 * w0 + e1 * w1 : 0.f;
+            dz3[at] = __float2bfloat16_rn(dz);
+            s0 += dz;
+            s1 = fmaf(e0, a, s1);
+            s2 = fmaf(e1, a, s2);
+        }
+        atomicAdd(&g_b3[k], s0);
+        atomicAdd(&g_w4[k], s1);
+        atomicAdd(&g_w4[kHid + k], s2);
     }
 }
 
@@ -463,7 +460,7 @@ sel_status forward(sel_mlp* m, const __nv_bfloat16* x, int n, bool training, cud
     MLP_TRY(run_gemm(g, 1, st));
     if (!training) {
         head_kernel<<<(n + 127) / 128, 128, 0, st>>>(m->a3, m->w4b, m->p + oB4, n, m->out, nullptr, n, nullptr,
-                                                      nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                      nullptr, nullptr, nullptr, nullptr);
         MLP_TRY(cuda_ok(cudaGetLastError(), "head launch"));
     }
     return SEL_OK;
@@ -474,9 +471,10 @@ sel_status backward(sel_mlp* m, const __nv_bfloat16* x, const float* y, int n, c
     MLP_TRY(forward(m, x, n, true, st));
     dim3 tb(32, 8), tg((kFeat + 31) / 32, (n + 31) / 32);
     transpose_bf16<<<tg, tb, 0, st>>>(x, n, kFeat, m->xt);
-    head_kernel<<<(n + 127) / 128, 128, 0, st>>>(m->a3, m->w4b, m->p + oB4, n, m->out, y, n, m->dz3, m->dz3t,
-                                                  m->g + oB3, m->g + oW4, m->g + oB4, m->loss);
+    head_kernel<<<(n + 127) / 128, 128, 0, st>>>(m->a3, m->w4b, m->p + oB4, n, m->out, y, n, m->dz3, m->g + oB3,
+                                                  m->g + oW4, m->g + oB4, m->loss);
     MLP_TRY(cuda_ok(cudaGetLastError(), "head launch"));
+    transpose_bf16<<<dim3((kHid + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(m->dz3, n, kHid, m->dz3t);
     const int splits = std::max(1, std::min(32, n / 256));
     // dW3 = dZ3^T A2 ; dA2 = dZ3 W3 -> dZ2 (ReLU gradient), db2
     GemmArgs g = gemm(m->dz3t, n, m->a2t, n, kHid, kHid, n, EPI_F32, m->err);
@@ -677,7 +675,7 @@ sel_status featurize(sel_mlp* m, cudaStream_t st, const sel_pred* const* preds, 
     if (dev_ok)
         MLP_TRY(cuda_ok(cudaMemcpyAsync(dev_ok, m->d_stage + ok_off, (size_t)n, cudaMemcpyDeviceToDevice, st),
                         "featurize"));
-    const int64_t threads = (int64_t)n * kSlots;
+    const int64_t threads = (int64_t)n * kSlots * 32;   // one warp per (predicate, slot)
     featurize_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
         reinterpret_cast<const FeatClause*>(m->d_stage), reinterpret_cast<const uint64_t*>(m->d_stage + keys_off),
         m->cdf, m->m, n, feat);

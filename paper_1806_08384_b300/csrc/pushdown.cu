@@ -28,7 +28,9 @@ __global__ void __launch_bounds__(kPdThreads, 6) pushdown_kernel(const __grid_co
     __shared__ unsigned long long s_tile, s_excl;
     __shared__ uint32_t s_chunk_cnt[kPdThreads / 32 * 4];
     __shared__ uint32_t s_fail;
+    __shared__ uint32_t s_slot_off[kMaxSlots];
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5, n_warps = blockDim.x >> 5;
+    if (tid < kMaxSlots) s_slot_off[tid] = a.slot_off[tid];
 
     if (tid == 0) {
         s_tile = atomicAdd(a.tile_counter, 1u);
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kPdThreads, 6) pushdown_kernel(const __grid_co
         if (ch < n_chunks) {
             const uint32_t c0 = ch * kChunkRows;
             const uint32_t vm = (c0 + kChunkRows <= valid) ? 0xFFu : valid_mask(c0, lane, valid);
-            const uint32_t m = eval_program(ins, a.n_instr, pool, st_addr, a.slot_off, c0, lane) & vm;
+            const uint32_t m = eval_program(ins, a.n_instr, pool, st_addr, s_slot_off, c0, lane) & vm;
             masks[q] = m;
             // inclusive warp scan of (popc(A half) | popc(B half) << 16)
             const uint32_t mine = __popc(m & 0xFu) | (__popc(m >> 4) << 16);
@@ -336,9 +338,11 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint32_t s_fail;
     __shared__ long long s_issued;
+    __shared__ uint32_t s_slot_off[kMaxSlots];   // read by every leaf: keep it in shared memory
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t S = a.stages;
     const PdSmem sm = pd_smem(smem, S);
+    if (tid < kMaxSlots) s_slot_off[tid] = a.slot_off[tid];
     uint8_t* stages = smem + a.smem_stage_off;
     const long long n_super = a.n_tiles;
 
@@ -476,7 +480,8 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
         const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
         const uint8_t* pool = blob + a.pool_off;
         uint32_t s = 0, ph = 0;
-        uint32_t rot = 0;   // running group count: group k of a sub-tile belongs to warp (rot + k) % W
+        uint32_t k_stage = 0;   // stages this warp has passed (fills of the ring)
+        uint32_t rot = 0;       // running group count: group k of a sub-tile belongs to warp (rot + k) % W
         long long prev_id = -1;
         uint32_t prev_nch = 0;
         for (uint32_t j = 0;; ++j) {
@@ -491,6 +496,27 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             uint32_t n_sub = 1;
             bool fail = false;
             for (uint32_t u = 0; u < n_sub; ++u) {
+                const uint32_t n_groups = NCH / G;
+                const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
+                // A warp with no chunk group in a sub-tile releases the stage without waiting
+                // for its data.  So before any use of a stage every warp waits until the
+                // stage's previous use was released by all warps: that use's data had landed,
+                // so the parity waited on below cannot alias a fill two phases back.
+                if (k_stage >= S && !warp_wait(&sm.empty[s], ph ^ 1u, lane)) {
+                    if (lane == 0) fail_flag(a, &s_fail);
+                    fail = true;
+                    break;
+                }
+                if (u > 0 && first >= n_groups) {
+                    rot += n_groups;
+                    if (lane == 0) mbar_arrive(&sm.empty[s]);
+                    ++k_stage;
+                    if (++s == S) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                    continue;
+                }
                 if (!warp_wait(&sm.full[s], ph, lane)) {
                     if (lane == 0) fail_flag(a, &s_fail);
                     fail = true;
@@ -507,14 +533,12 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
                 if (t < 0) break;   // sentinel (its stage is never reused)
                 const int64_t r0 = t * static_cast<int64_t>(SR) + static_cast<int64_t>(u) * TR;
                 const uint32_t valid = static_cast<uint32_t>(a.n_rows - r0 < (int64_t)TR ? a.n_rows - r0 : (int64_t)TR);
-                const uint32_t n_groups = NCH / G;
-                const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
                 for (uint32_t grp = first; grp < n_groups; grp += W) {
                     uint32_t c0[G], m[G];
 #pragma unroll
                     for (int q = 0; q < G; ++q) c0[q] = (grp * G + q) * kChunkRows;
                     eval_program_g<G>(ins, a.n_instr, pool, smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes),
-                                      a.slot_off, c0, lane, m);
+                                      s_slot_off, c0, lane, m);
 #pragma unroll
                     for (int q = 0; q < G; ++q) {
                         const uint32_t vm = (c0[q] + kChunkRows <= valid) ? 0xFFu
@@ -530,6 +554,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
                 rot += n_groups;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.empty[s]);   // the stage is no longer read
+                ++k_stage;
                 if (++s == S) {
                     s = 0;
                     ph ^= 1u;

@@ -49,10 +49,13 @@ VARIANTS = [(8, 1), (8, 2), (16, 1), (16, 2)]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("shape", [(256, 3, 1), (768, 4, 1), (4096, 3, 1), (1024, 4, 2), (16384, 3, 1)])
+@pytest.mark.parametrize("shape", [(256, 3, 1), (768, 4, 1), (4096, 3, 1), (1024, 4, 2), (16384, 3, 1),
+                                   (512, 2, 1), (1024, 2, 1)])
 def test_scan_variants_config2(ctx, medium, variant, shape):
     """Every kernel variant (consumer warps x chunks per pass) on tiles with an
-    odd number of chunks (a half-empty last group) and a ragged last tile."""
+    odd number of chunks (a half-empty last group) and a ragged last tile, and
+    on tiles with far fewer chunk groups than warps over a 2-stage ring (most
+    warps skip most tiles and come back to a stage one ring later)."""
     t, ot, T = medium
     ctx.set_scan_variant(*variant)
     ctx.set_scan_shape(*shape)
