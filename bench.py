@@ -59,16 +59,19 @@ def load_peaks():
 # ----------------------------------------------------------------------------
 
 class ClockSampler:
-    """SM clock and clock-event reasons sampled every 10 ms through NVML (read
-    only) while the timed region runs."""
+    """SM clock and clock-event reasons sampled through NVML (read only) while
+    the timed region runs, every interval_s seconds (NVML queries take driver
+    locks that also serve this process's CUDA calls: sampling much faster
+    slows the host side of the step)."""
     REASONS = [("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
                ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
                ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
                ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
                ("hw_power_brake_slowdown", "nvmlClocksEventReasonHwPowerBrakeSlowdown")]
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_s: float = 0.05):
         self.index = index
+        self.interval_s = interval_s
         self.samples = []
         self.reasons = set()
         self.max_mhz = None
@@ -97,7 +100,7 @@ class ClockSampler:
                             self.reasons.add(name)
                 except Exception:
                     pass
-                time.sleep(0.01)
+                time.sleep(self.interval_s)
         self._thread = threading.Thread(target=run, daemon=True)
         self._thread.start()
 
@@ -251,7 +254,7 @@ class Surrogate:
         self.final_loss = self.model.train(preds[:n_train], counts[:n_train], self.cfg)
         self.train_s = time.perf_counter() - t0
         self.n_train = n_train
-        self.eval_preds, self.eval_counts = preds[n_train:], counts[n_train:]
+        self.eval_preds, self.eval_counts = sel.PredicateList(preds[n_train:]), counts[n_train:]
         feat, ok = self.model.featurize(self.eval_preds)
         out = self.model.forward(feat).cpu().numpy()
         okm = ok.cpu().numpy().astype(bool)
@@ -280,10 +283,12 @@ class Surrogate:
 
     def run(self, record=False):
         ev = lambda: torch.cuda.Event(enable_timing=True)
-        a, b, c = ev(), ev(), ev()
+        a, a2, b, c = ev(), ev(), ev(), ev()
         if record:
             a.record()
         feat, ok = self.model.featurize(self.eval_preds)              # a6
+        if record:
+            a2.record()
         out = self.model.forward(feat)                                # a7
         if record:
             b.record()
@@ -292,11 +297,13 @@ class Surrogate:
         self.model.train_step(self.train_feat, self.train_y, self.step_cfg)   # a8
         if record:
             c.record()
-            self.events.append((a, b, c))
+            self.events.append((a, a2, b, c))
 
     def summary(self):
-        inf = [x.elapsed_time(y) for x, y, _ in self.events]
-        trn = [y.elapsed_time(z) for _, y, z in self.events]
+        inf = [x.elapsed_time(y) for x, _, y, _ in self.events]
+        fz = [x.elapsed_time(y) for x, y, _, _ in self.events]
+        fw = [x.elapsed_time(y) for _, x, y, _ in self.events]
+        trn = [y.elapsed_time(z) for _, _, y, z in self.events]
         reps = 5
         self.exact_plan.run()
         torch.cuda.synchronize()
@@ -314,6 +321,7 @@ class Surrogate:
             "label_seconds": round(self.label_s, 2), "train_seconds": round(self.train_s, 2),
             "final_train_loss": round(self.final_loss, 4),
             "ms_per_batch_featurize_forward": round(statistics.mean(inf), 3),
+            "ms_featurize": round(statistics.mean(fz), 3), "ms_forward": round(statistics.mean(fw), 3),
             "ms_per_estimate": round(statistics.mean(inf) / n, 6),
             "exact_ms_per_estimate": round(exact_ms / 256, 4),
             "train_step_ms": round(statistics.mean(trn), 3),
@@ -507,6 +515,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-star", action="store_true", help="skip the star-schema batch measurement")
+    ap.add_argument("--clock-interval-ms", type=float, default=50.0, help="NVML clock sampling interval")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.steps <= 2, "at least 3 warm-up steps"
@@ -540,7 +549,7 @@ def main():
     b_batch, b_pds = algorithmic_bytes(w.types, w.n, w.trees, counts, accepted, w.proj)
     step_bytes = b_batch + sum(b_pds)
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, args.clock_interval_ms / 1e3)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()

@@ -478,6 +478,21 @@ class BatchPlan:
 N_FEATURES = 144
 
 
+class PredicateList:
+    """A fixed list of predicates with its C array of handles built once (for
+    calls that pass the same predicates again and again)."""
+
+    def __init__(self, preds: Sequence[Predicate]):
+        self.preds = list(preds)
+        self.handles = (C.c_void_p * max(1, len(self.preds)))(*[p.h.value for p in self.preds])
+
+    def __len__(self):
+        return len(self.preds)
+
+    def __getitem__(self, i):
+        return self.preds[i]
+
+
 class Estimator:
     """sel_mlp: CDF-sampled features, a BF16 tensor-core MLP and the gated
     exact fallback (see include/sel.h)."""
@@ -501,11 +516,12 @@ class Estimator:
     def save(self, path: str):
         _check(lib.sel_mlp_save(self.h, path.encode()), "sel_mlp_save")
 
-    def featurize(self, preds: Sequence[Predicate], device="cuda"):
+    def featurize(self, preds, device="cuda"):
+        """preds: a sequence of Predicate, or a PredicateList (its handle array is built once)."""
         n = len(preds)
         feat = torch.empty(n, N_FEATURES, dtype=torch.bfloat16, device=device)
         ok = torch.empty(n, dtype=torch.uint8, device=device)
-        pa = (C.c_void_p * n)(*[p.h.value for p in preds])
+        pa = preds.handles if isinstance(preds, PredicateList) else (C.c_void_p * n)(*[p.h.value for p in preds])
         _check(lib.sel_mlp_featurize(self.ctx.h, self.h, pa, n, C.c_void_p(feat.data_ptr()),
                                      C.c_void_p(ok.data_ptr())), "sel_mlp_featurize")
         return feat, ok

@@ -136,34 +136,6 @@ __global__ void __launch_bounds__((W + 1) * 32, W == 8 ? 2 : 1) scan_count_kerne
             const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
             const uint32_t n_groups = (n_chunks + G - 1) / G;
             const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
-            // A warp with no chunk group in a tile releases the stage without waiting for
-            // its data.  So before any use of a stage every warp waits until the stage's
-            // previous use was released by all warps: that use's data had landed (its
-            // owners waited for it), so the parity waited on below cannot alias a fill
-            // two phases back, and no warp runs more than one ring ahead.
-            if (k >= S) {
-                uint32_t okp = 0;
-                if (lane == 0) okp = mbar_wait_bounded(&empty[s], parity ^ 1u) ? 1u : 0u;
-                okp = __shfl_sync(0xFFFFFFFFu, okp, 0);
-                if (!okp) {
-                    if (lane == 0) {
-                        atomicOr(a.err, 1u);
-                        atomicOr(&s_fail, 1u);
-                    }
-                    break;
-                }
-            }
-            if (first >= n_groups) {
-                rot += n_groups;
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[s]);
-                if (++s == S) {
-                    s = 0;
-                    parity ^= 1u;
-                }
-                if (*reinterpret_cast<volatile uint32_t*>(&s_fail)) break;
-                continue;
-            }
             // lane 0 waits for the stage; the warp follows its verdict (one decision per warp)
             uint32_t okw = 0;
             if (lane == 0) okw = mbar_wait_bounded(&full[s], parity) ? 1u : 0u;

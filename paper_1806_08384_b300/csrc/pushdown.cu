@@ -480,7 +480,6 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
         const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
         const uint8_t* pool = blob + a.pool_off;
         uint32_t s = 0, ph = 0;
-        uint32_t k_stage = 0;   // stages this warp has passed (fills of the ring)
         uint32_t rot = 0;       // running group count: group k of a sub-tile belongs to warp (rot + k) % W
         long long prev_id = -1;
         uint32_t prev_nch = 0;
@@ -498,25 +497,6 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             for (uint32_t u = 0; u < n_sub; ++u) {
                 const uint32_t n_groups = NCH / G;
                 const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
-                // A warp with no chunk group in a sub-tile releases the stage without waiting
-                // for its data.  So before any use of a stage every warp waits until the
-                // stage's previous use was released by all warps: that use's data had landed,
-                // so the parity waited on below cannot alias a fill two phases back.
-                if (k_stage >= S && !warp_wait(&sm.empty[s], ph ^ 1u, lane)) {
-                    if (lane == 0) fail_flag(a, &s_fail);
-                    fail = true;
-                    break;
-                }
-                if (u > 0 && first >= n_groups) {
-                    rot += n_groups;
-                    if (lane == 0) mbar_arrive(&sm.empty[s]);
-                    ++k_stage;
-                    if (++s == S) {
-                        s = 0;
-                        ph ^= 1u;
-                    }
-                    continue;
-                }
                 if (!warp_wait(&sm.full[s], ph, lane)) {
                     if (lane == 0) fail_flag(a, &s_fail);
                     fail = true;
@@ -554,7 +534,6 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
                 rot += n_groups;
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.empty[s]);   // the stage is no longer read
-                ++k_stage;
                 if (++s == S) {
                     s = 0;
                     ph ^= 1u;

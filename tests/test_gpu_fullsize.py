@@ -1,0 +1,74 @@
+"""Full-size parity for the star schema (480M-row fact table and four
+dimensions, 64 probes in one autotuned batch plan: the launch the bench
+times) and for the 1.2B-row table with its 256 probes.
+
+* Star schema: every batched count equals the threaded oracle's count.
+* 1.2B rows (too many row evaluations for the oracle on all 256 probes):
+  batched counts equal one-launch-per-probe counts; count(A) + count(NOT A) = n;
+  the oracle's counts on a 2M-row window (a view of the same columns); the
+  push-down of 3 columns for a few probes returns exactly count rows, strictly
+  increasing row ids, values equal to the table's, and every returned row
+  satisfies the predicate per the oracle."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import datagen as dg
+import oracle
+import paper_1806_08384_b300 as sel
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+THREADS = max(1, min(64, os.cpu_count() or 1))
+
+
+def test_star_schema_full_size(ctx, dev):
+    tabs = dg.config3_tables(device=dev)
+    T = [sel.Table(t.columns) for t in tabs]
+    probes = dg.config3_predicates()
+    preds = [sel.Predicate(T[ti], tr) for ti, tr in probes]
+    got = sel.BatchPlan(ctx, preds, [T[ti] for ti, _ in probes]).run()
+    for k, t in enumerate(tabs):
+        ot = oracle.OTable.from_table(t)
+        for i, (ti, tr) in enumerate(probes):
+            if ti == k:
+                assert got[i] == oracle.count(ot, tr, threads=THREADS), (i, tr)
+        del ot
+
+
+def test_large_table_full_size(ctx, dev):
+    t = dg.config5_table(device=dev)
+    n = t.n_rows
+    T = sel.Table(t.columns)
+    trees = dg.config5_predicates()
+    preds = [sel.Predicate(T, tr) for tr in trees]
+    batched = sel.BatchPlan(ctx, preds, [T] * len(preds), autotune=False).run()
+    picks = [0, 37, 101, 150, 200, 255]
+    for i in picks:
+        assert ctx.count(preds[i], T) == batched[i]
+        assert ctx.count(sel.Predicate(T, dg.p_not(trees[i])), T) == n - batched[i]
+    # a 2M-row window in the middle of the table, as a view of the same device columns
+    r0, r1 = 700_000_000, 702_000_000
+    W = sel.Table([dg.Column(c.spec, c.data[r0:r1], c.dictionary) for c in t.columns])
+    ow = oracle.OTable([c.data[r0:r1].cpu().numpy() for c in t.columns], [c.type for c in t.columns],
+                       [c.dictionary for c in t.columns])
+    for i in range(0, 256, 8):
+        assert ctx.count(sel.Predicate(W, trees[i]), W) == oracle.count(ow, trees[i], threads=THREADS), i
+    # push-down of the 3 projected columns for probes under 1 % of the rows
+    proj = [t.index(c) for c in dg.CONFIG5_PROJECTION]
+    small = [i for i in range(256) if 0 < batched[i] <= n // 100][::12][:4]
+    assert small
+    for i in small:
+        st, cnt, cols, ids = ctx.pushdown(preds[i], T, proj, batched[i])
+        assert st == sel.SEL_OK and cnt == batched[i]
+        idh = ids.cpu().numpy()
+        assert np.all(np.diff(idh) > 0)
+        sample = np.unique(np.concatenate([idh[:2000], idh[-2000:], idh[:: max(1, len(idh) // 4000)]]))
+        rows = torch.from_numpy(sample).to(dev)
+        for c, out in zip(proj, cols):
+            pos = torch.from_numpy(np.searchsorted(idh, sample)).to(dev)
+            assert torch.equal(out[pos], t.columns[c].data[rows]), (i, c)
+        osub = oracle.OTable([c.data[rows].cpu().numpy() for c in t.columns], [c.type for c in t.columns],
+                             [c.dictionary for c in t.columns])
+        assert oracle.count(osub, trees[i]) == len(sample), i
