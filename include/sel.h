@@ -252,10 +252,12 @@ sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stage
 /* Count-scan kernel variant for sel_count / sel_count_async (both 0 = the
  * library default): consumer_warps 8 or 16 (plus one producer warp per CTA)
  * and chunks_per_pass 1 or 2 (256-row chunks a warp evaluates with one pass
- * over the program's instructions).  Any other pair: SEL_ERR_INVALID_ARG.
+ * over the program's instructions), or 8 warps with 4 chunks per pass.  Any
+ * other pair: SEL_ERR_INVALID_ARG.
  * The same pair selects the persistent push-down kernel's consumer warps and
- * chunks per warp (sub-tiles of warps x chunks x 256 rows).  Results do not
- * depend on the variant. */
+ * chunks per pass where that kernel has the variant (8 or 16 warps, 1 or 2
+ * chunks; otherwise the push-down takes its one-CTA-per-tile kernel).
+ * Results do not depend on the variant. */
 sel_status sel_ctx_set_scan_variant(sel_ctx* ctx, int32_t consumer_warps, int32_t chunks_per_pass);
 
 /* Number of kernels this context has launched so far (all entry points). */

@@ -345,7 +345,7 @@ extern "C" sel_status sel_ctx_set_scan_shape(sel_ctx* c, int32_t tile_rows, int3
 
 extern "C" sel_status sel_ctx_set_scan_variant(sel_ctx* c, int32_t consumer_warps, int32_t chunks_per_pass) {
     if (!c || !((consumer_warps == 0 && chunks_per_pass == 0) || scan_variant_ok(consumer_warps, chunks_per_pass))) {
-        set_error("sel_ctx_set_scan_variant: bad arguments (0,0 or warps 8|16 and chunks 1|2)");
+        set_error("sel_ctx_set_scan_variant: bad arguments (0,0; warps 8|16 with chunks 1|2; warps 8 with chunks 4)");
         return SEL_ERR_INVALID_ARG;
     }
     c->shape.warps = consumer_warps;
@@ -787,7 +787,7 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
         struct Cand { int stage_kb, stages, ctas, warps, group; };
         const Cand cands[] = {{64, 3, 1, 16, 2}, {48, 4, 1, 16, 2}, {96, 2, 1, 16, 2}, {64, 3, 1, 16, 1},
                               {48, 4, 1, 16, 1}, {32, 3, 2, 8, 2},  {24, 4, 2, 8, 2},  {32, 3, 2, 8, 1},
-                              {24, 4, 2, 8, 1},  {16, 4, 3, 8, 1}};
+                              {24, 4, 2, 8, 1},  {16, 4, 3, 8, 1},  {64, 3, 1, 8, 4},  {48, 4, 1, 8, 4}};
         best_ms = 1e30f;
         for (const Cand& c : cands) {
             Shape sh;

@@ -64,7 +64,7 @@ __device__ __forceinline__ void produce_tile(const ScanArgs& a, int64_t g, uint3
 // programs on G chunks at once (G independent mask stacks share one
 // instruction stream, which hides the interpreter's latency).
 template <int W, int G>
-__global__ void __launch_bounds__((W + 1) * 32, W == 8 ? 2 : 1) scan_count_kernel(const __grid_constant__ ScanArgs a) {
+__global__ void __launch_bounds__((W + 1) * 32, (W == 8 && G < 4) ? 2 : 1) scan_count_kernel(const __grid_constant__ ScanArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint32_t s_off[kMaxTables][kMaxSlots];
     __shared__ uint32_t s_fail;
@@ -214,11 +214,12 @@ cudaError_t scan_kernel_max_smem(int optin, int* dyn_max) {
     if (e == cudaSuccess) e = set_smem_limit<8, 2>(optin, dyn_max);
     if (e == cudaSuccess) e = set_smem_limit<16, 1>(optin, dyn_max);
     if (e == cudaSuccess) e = set_smem_limit<16, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = set_smem_limit<8, 4>(optin, dyn_max);
     return e;
 }
 
 bool scan_variant_ok(int warps, int group) {
-    return (warps == 8 || warps == 16) && (group == 1 || group == 2);
+    return ((warps == 8 || warps == 16) && (group == 1 || group == 2)) || (warps == 8 && group == 4);
 }
 
 cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group) {
@@ -230,6 +231,8 @@ cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStre
         scan_count_kernel<16, 1><<<grid, 17 * 32, smem, st>>>(a);
     else if (warps == 16 && group == 2)
         scan_count_kernel<16, 2><<<grid, 17 * 32, smem, st>>>(a);
+    else if (warps == 8 && group == 4)
+        scan_count_kernel<8, 4><<<grid, 9 * 32, smem, st>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -60,6 +60,7 @@ __device__ __forceinline__ bool look_back(const PushdownArgs& a, long long t, ui
                 *excl_out = excl;
                 return false;
             }
+            __nanosleep(100);   // a predecessor is still evaluating: leave the issue slots to other warps
             if ((v >> 62) == 0) v = ld_relaxed(&a.status[idx]);
         }
         unsigned long long x = ((take >> lane) & 1u) ? (v & kValMask) : 0ull;

@@ -270,10 +270,11 @@ __device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S) {
     return m;
 }
 
-// Bounded wait by lane 0, verdict broadcast to the warp.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t lane) {
+// Bounded wait by lane 0, verdict broadcast to the warp.  sleep_ns > 0: the
+// waiter sleeps between tries (for waits off the critical path).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t lane, uint32_t sleep_ns = 0) {
     uint32_t ok = 0;
-    if (lane == 0) ok = mbar_wait_bounded(bar, parity) ? 1u : 0u;
+    if (lane == 0) ok = (sleep_ns ? mbar_wait_bounded_idle(bar, parity, sleep_ns) : mbar_wait_bounded(bar, parity)) ? 1u : 0u;
     ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
     __syncwarp();
     return ok != 0;
@@ -370,16 +371,19 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
 
     if (warp == W) {
         // ------------------------------- producer -------------------------------
-        // the super-tile is gathered again (selected rows only) soon after:
-        // keep it in L2 with the normal policy
-        const uint64_t pol = policy_evict_normal();
+        const uint64_t pol = policy_evict_first();
         uint32_t s = 0, ph = 0;
         long long k = 0;   // stage fills issued
         bool stop = false;
+        // the next super-tile id is taken one super-tile ahead, so that the
+        // atomic's round trip does not stall the copies (taking it early changes
+        // nothing for progress: it is still worked on after the CTA's smaller ids)
+        unsigned long long next_id = 0;
+        if (lane == 0) next_id = atomicAdd(a.tile_counter64, 1ull);
         while (!stop) {
-            unsigned long long st_id = 0;
-            if (lane == 0) st_id = atomicAdd(a.tile_counter64, 1ull);
-            st_id = __shfl_sync(0xFFFFFFFFu, st_id, 0);
+            unsigned long long st_id = __shfl_sync(0xFFFFFFFFu, next_id, 0);
+            if (lane == 0 && st_id < static_cast<unsigned long long>(n_super))
+                next_id = atomicAdd(a.tile_counter64, 1ull);
             const bool last = st_id >= static_cast<unsigned long long>(n_super);
             const int64_t R0 = static_cast<int64_t>(st_id) * SR;
             const uint32_t n_sub = last ? 1u
@@ -435,7 +439,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
         // ------------------------------- look-back ------------------------------
         for (uint32_t j = 0;; ++j) {
             const uint32_t b = j % kPdBufs, par = (j / kPdBufs) & 1u;
-            if (!warp_wait(&sm.evald[b], par, lane)) {
+            if (!warp_wait(&sm.evald[b], par, lane, 500)) {   // a super-tile takes microseconds: sleep meanwhile
                 if (lane == 0) fail_flag(a, &s_fail);
                 break;
             }

@@ -72,18 +72,22 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// The same for a waiter that is not on the critical path (it would otherwise
+// take issue slots from the warps that are): sleeps sleep_ns between tries.
+__device__ __forceinline__ bool mbar_wait_bounded_idle(uint64_t* bar, uint32_t parity, uint32_t sleep_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (true) {
+        __nanosleep(sleep_ns);
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
 // L2 policy for streamed column data: read once, evict first.
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-// L2 policy for column data that is read again soon (the push-down's gather
-// of the selected rows' projected values).
-__device__ __forceinline__ uint64_t policy_evict_normal() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
 
@@ -230,7 +234,7 @@ __device__ __forceinline__ void eval_leaf_g(const Instr& in, uint32_t col_base, 
         uint64_t v[G][8];
 #pragma unroll
         for (int g = 0; g < G; ++g) load8x64(col_base, c0[g], lane, v[g]);
-        in_list<G, (G == 1 ? 8 : 4)>(v, reinterpret_cast<const uint64_t*>(pool + in.off), in.a,
+        in_list<G, (G == 1 ? 8 : G == 2 ? 4 : 2)>(v, reinterpret_cast<const uint64_t*>(pool + in.off), in.a,
                       [](uint64_t x, uint64_t w) { return x == w; }, m);
         break;
     }

@@ -45,7 +45,7 @@ def test_scan_shapes_config2(ctx, medium, shape):
         assert ctx.count(p, T) == oracle.count(ot, tree, threads=8)
 
 
-VARIANTS = [(8, 1), (8, 2), (16, 1), (16, 2)]
+VARIANTS = [(8, 1), (8, 2), (16, 1), (16, 2), (8, 4)]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
@@ -97,7 +97,7 @@ def test_variants_tiny(ctx, dev, variant):
 
 
 def test_bad_variant_is_rejected(ctx):
-    for w, g in [(4, 1), (8, 3), (0, 1), (32, 2)]:
+    for w, g in [(4, 1), (8, 3), (0, 1), (32, 2), (16, 4)]:
         with pytest.raises(sel.SelError):
             ctx.set_scan_variant(w, g)
 
