@@ -574,10 +574,12 @@ def main():
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
+    torch.cuda.nvtx.range_push("timed_steps")
     for _ in range(args.steps):
         step.run(record=True)
         if sur:
             sur.run(record=True)
+    torch.cuda.nvtx.range_pop()
     t1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -621,14 +623,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64/f32 compares, u64 counts",
         "data": "synthetic, seeded (datagen; shapes of the paper's fact tables), resident in HBM",
-        "config": {"workload": f"config2 fact table: {w.n} rows x 8 cols (2 i32 U, i64 Zipf1.1, f32 U, f32 LogN, "
-                               f"date, dict-25, dict-10k), {len(w.trees)} probes OR-of-3-ANDs "
-                               f"s={list(dg.CONFIG2_TARGETS)}, push-down of {list(dg.CONFIG2_PROJECTION)} "
-                               f"when count <= floor(n*{MAX_SELECTIVITY})",
-                   "n_rows": w.n, "table_bytes": w.table.nbytes(), "probes": len(w.trees),
-                   "pushed_down": len(accepted), "max_rows": w.max_rows,
-                   "l2": "inputs larger than L2 (table 10.8 GB vs 126 MB L2), no flush needed",
-                   "parallelism": f"replicas{world}" if world > 1 else "single"},
+        "config": workload_config(w.n, len(w.trees), len(accepted), world),
         "ms_per_estimate": round(elapsed_ms / args.steps / len(w.trees), 4),
         "roofline": roof(dominant),
         "roofline_other": roof(other),
@@ -682,6 +677,18 @@ def run_e2e(step: OurStep, args, step_bytes):
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": k}
 
 
+def workload_config(n: int, probes: int, pushed: int, world: int = 1) -> dict:
+    """The bench's config object (both arms)."""
+    return {"workload": f"config2 fact table: {n} rows x 8 cols (2 i32 U, i64 Zipf1.1, f32 U, f32 LogN, "
+                        f"date, dict-25, dict-10k), {probes} probes OR-of-3-ANDs "
+                        f"s={list(dg.CONFIG2_TARGETS)}, push-down of {list(dg.CONFIG2_PROJECTION)} "
+                        f"when count <= floor(n*{MAX_SELECTIVITY})",
+            "n_rows": n, "table_bytes": n * 36, "probes": probes, "pushed_down": pushed,
+            "max_rows": int(math.floor(n * MAX_SELECTIVITY)),
+            "l2": "inputs larger than L2 (table 10.8 GB vs 126 MB L2), no flush needed",
+            "parallelism": f"replicas{world}" if world > 1 else "single"}
+
+
 def run_reference(args, threads):
     """The oracle as it stands, on the host cores, on a bounded sample per step."""
     dev = "cuda" if torch.cuda.is_available() else "cpu"
@@ -706,7 +713,7 @@ def run_reference(args, threads):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64/f32 compares, u64 counts",
            "data": "synthetic, seeded (datagen)",
-           "config": {"workload": f"config2 fact table (sampled prefix of {n} rows)", "n_rows": ot.n_rows},
+           "config": workload_config(n, len(trees), len(accepted), args.gpus),
            "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": round(gbs, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
