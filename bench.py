@@ -273,6 +273,7 @@ class Surrogate:
         from paper_1806_08384_b300 import baselines
         ind = baselines.independence_selectivity(feat.float().cpu().numpy()) * T.n_rows
         qi = q_error(ind, self.eval_counts)
+        self.traditional = self.traditional_baselines(step, trees[n_train:], okm)
         self.quality = {
             "q_error_p50": round(float(np.median(q[okm])), 3), "q_error_p95": round(float(np.percentile(q[okm], 95)), 3),
             "gated_tau": round(self.tau, 4), "gated_answered_fraction": round(float(acc.mean()), 3),
@@ -288,6 +289,39 @@ class Surrogate:
         self.exact_plan = sel.BatchPlan(ctx, self.eval_preds[:256], [T] * 256, autotune=False)
         self.events = []
         self.accepted = 0
+
+    def traditional_baselines(self, step, eval_trees, okm, sample_rows=65_536):
+        """Ch2's estimators on the same held-out probes: the textbook heuristics
+        (1/V, 1/3) with exact distinct counts, equi-depth histograms (64 buckets)
+        built from a row sample, and the sampling estimator (the library's count
+        on that sample, scaled by |R| / |R'|)."""
+        from paper_1806_08384_b300 import baselines
+        sel, T, w = self.sel, self.T, step.w
+        cols = w.table.columns
+        n = T.n_rows
+        distinct = [int(torch.unique(c.data).numel()) for c in cols]
+        dicts = [c.dictionary for c in cols]
+        g = torch.Generator(device=cols[0].data.device)
+        g.manual_seed(dg.mix_seed("bench_row_sample"))
+        rows = torch.randint(0, n, (sample_rows,), generator=g, device=cols[0].data.device)
+        sample = [dg.Column(c.spec, c.data[rows].contiguous(), c.dictionary) for c in cols]
+        hists = [baselines.EquiDepthHistogram.build(c.data.cpu().numpy(), n, buckets=64) for c in sample]
+        TS = sel.Table(sample)
+        sp = [sel.Predicate(TS, t) for t in eval_trees]
+        t0 = time.perf_counter()
+        sc = np.array(sel.count_many(self.ctx, sp, TS), dtype=np.float64)
+        samp_ms = (time.perf_counter() - t0) * 1e3 / len(sp)
+        est = {"textbook": np.array([baselines.textbook_selectivity(t, distinct, dicts) for t in eval_trees]) * n,
+               "histogram": np.array([baselines.histogram_selectivity(t, hists, dicts) for t in eval_trees]) * n,
+               "sampling": np.array([baselines.sampling_estimate(c, sample_rows, n) for c in sc])}
+        out = {}
+        for name, e in est.items():
+            q = q_error(e, self.eval_counts)[okm]
+            out[name + "_q_error_p50"] = round(float(np.median(q)), 3)
+            out[name + "_q_error_p95"] = round(float(np.percentile(q, 95)), 3)
+        out["sampling_rows"] = sample_rows
+        out["sampling_ms_per_estimate"] = round(samp_ms, 4)
+        return out
 
     def run(self, record=False):
         ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -329,7 +363,7 @@ class Surrogate:
         torch.cuda.synchronize()
         exact_ms = e0.elapsed_time(e1) / reps
         n = len(self.eval_preds)
-        return dict(self.quality, **{
+        return dict(self.quality, **self.traditional, **{
             "workload": f"{n} held-out OR-of-AND probes (<= 6 leaves) on the same table; trained on "
                         f"{self.n_train} probes labelled by the count kernel",
             "label_seconds": round(self.label_s, 2), "train_seconds": round(self.train_s, 2),

@@ -356,6 +356,12 @@ struct sel_mlp {
     uint8_t* d_stage = nullptr;
     size_t stage_cap = 0;
     cudaEvent_t stage_done = nullptr;
+    // what the device staging block holds: the predicates (by id) whose clause
+    // records were uploaded last, their featurizable flags and offsets; a call
+    // with the same predicates in the same order reuses it
+    std::vector<uint64_t> stage_ids;
+    std::vector<uint8_t> stage_ok;
+    size_t stage_keys_off = 0, stage_ok_off = 0;
     ~sel_mlp() {
         if (stage_done) cudaEventSynchronize(stage_done);
         if (h_stage) cudaFreeHost(h_stage);
@@ -658,20 +664,38 @@ sel_status stage_reserve(sel_mlp* m, size_t bytes) {
 // Asynchronous on st (the staging block is protected by stage_done).
 sel_status featurize(sel_mlp* m, cudaStream_t st, const sel_pred* const* preds, int32_t n, __nv_bfloat16* feat,
                      std::vector<uint8_t>* ok_out, uint8_t* dev_ok) {
-    std::vector<FeatClause> cl;
-    std::vector<uint64_t> keys;
-    std::vector<uint8_t> ok;
-    MLP_TRY(build_clauses(m, preds, n, cl, keys, ok));
-    const size_t cl_bytes = cl.size() * sizeof(FeatClause);
-    const size_t keys_off = (cl_bytes + 15) / 16 * 16;
-    const size_t ok_off = keys_off + (keys.size() * 8 + 15) / 16 * 16;
-    const size_t total = ok_off + (size_t)n;
-    MLP_TRY(stage_reserve(m, total));
-    std::memcpy(m->h_stage, cl.data(), cl_bytes);
-    if (!keys.empty()) std::memcpy(m->h_stage + keys_off, keys.data(), keys.size() * 8);
-    std::memcpy(m->h_stage + ok_off, ok.data(), (size_t)n);
-    MLP_TRY(cuda_ok(cudaMemcpyAsync(m->d_stage, m->h_stage, total, cudaMemcpyHostToDevice, st), "featurize"));
-    MLP_TRY(cuda_ok(cudaEventRecord(m->stage_done, st), "featurize"));
+    // predicates are immutable and their ids unique: the same ids in the same
+    // order mean the staged clause records are still the right ones
+    std::vector<uint64_t> ids((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        if (!preds[i]) {
+            set_error("learned estimator: predicate is NULL");
+            return SEL_ERR_INVALID_ARG;
+        }
+        ids[(size_t)i] = preds[i]->id;
+    }
+    if (ids != m->stage_ids) {
+        m->stage_ids.clear();
+        std::vector<FeatClause> cl;
+        std::vector<uint64_t> keys;
+        std::vector<uint8_t> ok;
+        MLP_TRY(build_clauses(m, preds, n, cl, keys, ok));
+        const size_t cl_bytes = cl.size() * sizeof(FeatClause);
+        const size_t keys_off = (cl_bytes + 15) / 16 * 16;
+        const size_t ok_off = keys_off + (keys.size() * 8 + 15) / 16 * 16;
+        const size_t total = ok_off + (size_t)n;
+        MLP_TRY(stage_reserve(m, total));
+        std::memcpy(m->h_stage, cl.data(), cl_bytes);
+        if (!keys.empty()) std::memcpy(m->h_stage + keys_off, keys.data(), keys.size() * 8);
+        std::memcpy(m->h_stage + ok_off, ok.data(), (size_t)n);
+        MLP_TRY(cuda_ok(cudaMemcpyAsync(m->d_stage, m->h_stage, total, cudaMemcpyHostToDevice, st), "featurize"));
+        MLP_TRY(cuda_ok(cudaEventRecord(m->stage_done, st), "featurize"));
+        m->stage_ids = std::move(ids);
+        m->stage_ok = std::move(ok);
+        m->stage_keys_off = keys_off;
+        m->stage_ok_off = ok_off;
+    }
+    const size_t keys_off = m->stage_keys_off, ok_off = m->stage_ok_off;
     if (dev_ok)
         MLP_TRY(cuda_ok(cudaMemcpyAsync(dev_ok, m->d_stage + ok_off, (size_t)n, cudaMemcpyDeviceToDevice, st),
                         "featurize"));
@@ -680,7 +704,7 @@ sel_status featurize(sel_mlp* m, cudaStream_t st, const sel_pred* const* preds, 
         reinterpret_cast<const FeatClause*>(m->d_stage), reinterpret_cast<const uint64_t*>(m->d_stage + keys_off),
         m->cdf, m->m, n, feat);
     MLP_TRY(cuda_ok(cudaGetLastError(), "featurize launch"));
-    if (ok_out) *ok_out = std::move(ok);
+    if (ok_out) *ok_out = m->stage_ok;
     return SEL_OK;
 }
 

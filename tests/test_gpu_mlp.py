@@ -156,3 +156,21 @@ def test_gate_exact_fallback_and_checkpoint(setup, tmp_path):
     again = sel.Estimator.load(ctx, path)
     feat, _ = est.featurize(preds)
     assert torch.equal(est.forward(feat), again.forward(feat))
+
+
+def test_repeated_featurize_reuses_the_staged_records(setup):
+    """The same predicate list featurized again (the staged clause records are
+    reused), interleaved with other lists, gives identical features and flags."""
+    t, T, ctx, est, cdfs, dicts, trees = setup
+    a = sel.PredicateList([sel.Predicate(T, tr) for tr in trees[:300]])
+    b = [sel.Predicate(T, tr) for tr in trees[300:450]]
+    fa, oa = est.featurize(a)
+    fa2, oa2 = est.featurize(a)
+    fb, ob = est.featurize(b)
+    fa3, oa3 = est.featurize(a)
+    fb2, ob2 = est.featurize(b[:149] + [b[149]])   # equal predicates, new list object
+    for f, o in ((fa2, oa2), (fa3, oa3)):
+        assert torch.equal(f, fa) and torch.equal(o, oa)
+    assert torch.equal(fb2, fb) and torch.equal(ob2, ob)
+    fresh, _ = est.featurize([sel.Predicate(T, tr) for tr in trees[:300]])   # recompiled: new ids
+    assert torch.equal(fresh, fa)
