@@ -458,6 +458,25 @@ def star_batch(sel, peak: float, device, reps=5):
     return res
 
 
+def distinct_and_join(step: OurStep, reps=3):
+    """f3: V(R, k2) and V(sigma_P(R), k2) of the int64 key (exact, GPU hash set)
+    and the join-size estimate of sigma_P(R) with R on that key."""
+    sel, w = step.sel, step.w
+    k = w.table.index("k2")
+    p = sel.Predicate(step.T, w.trees[2])   # the s = 1e-2 probe
+    out = {}
+    for name, pred in (("all_rows", None), ("selected_rows", p)):
+        step.ctx.count_distinct(step.T, k, pred)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            d, r = step.ctx.count_distinct(step.T, k, pred)
+        out[name] = {"distinct": d, "rows": r, "ms": round((time.perf_counter() - t0) * 1e3 / reps, 3)}
+    a, b_ = out["selected_rows"], out["all_rows"]
+    out["join_size_estimate"] = round(sel.join_size_estimate(a["rows"], b_["rows"], a["distinct"], b_["distinct"]), 1)
+    out["note"] = "host-timed synchronous calls; with a predicate the time includes the push-down of k2"
+    return out
+
+
 def count_single(step: OurStep, peak: float, reps=5):
     """a2 alone: each probe's exact count as its own launch (sel_count_async,
     the library's default shape), GB/s of its referenced columns."""
@@ -669,6 +688,7 @@ def main():
     if rank == 0:
         out["batched_vs_separate"] = time_separate_vs_batched(step)
         out["count_single"] = count_single(step, peak)
+        out["distinct_and_join"] = distinct_and_join(step)
         if not args.no_star:
             out["star_batch"] = star_batch(sel, peak, dev)
     if rank == 0 and not args.no_e2e:

@@ -272,6 +272,23 @@ uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
 sel_status sel_ctx_debug_pushdown_fault(sel_ctx* ctx, int64_t skip_tile, uint64_t wait_ns);
 
 /* ---------------------------------------------------------------------------
+ * Join-size estimate (§1.1, §3.2): |R join S| = |R||S| / max(V(R,A), V(S,A)),
+ * V(R, A) the number of distinct values of the join attribute.
+ * ------------------------------------------------------------------------- */
+
+/* V(sigma_P(R), col): distinct values of column `col` over the rows that
+ * satisfy `pred` (NULL: all rows), and (when out_rows is not NULL) the number
+ * of those rows.  float32 -0.0 and +0.0 count as one value.  With a predicate
+ * the selected values are compacted by the push-down first.  Device scratch
+ * (owned by the context): the selected values and a hash set of at least
+ * twice as many 8-byte slots.  Synchronous. */
+sel_status sel_count_distinct(sel_ctx* ctx, const sel_table* table, int32_t col, const sel_pred* pred,
+                              uint64_t* out_distinct, uint64_t* out_rows);
+
+/* rows_r * rows_s / max(distinct_r, distinct_s); 0 when both are 0. */
+double sel_join_size_estimate(uint64_t rows_r, uint64_t rows_s, uint64_t distinct_r, uint64_t distinct_s);
+
+/* ---------------------------------------------------------------------------
  * Algorithm 1, EvaluateAndPushDown (Ch4 §4.2): the push-down decision for the
  * scanned relations of one query.  Relations whose size is greater than
  * min_table_size (PUSH_DOWN_MIN_TABLE_SIZE) are ordered by size, largest

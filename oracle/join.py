@@ -1,0 +1,30 @@
+"""CPU oracle of the join-size estimate's inputs (§1.1, §3.2).  TEST
+INFRASTRUCTURE ONLY (imported by tests; never by the library).
+
+* V(sigma_P(R), A): the number of distinct values of column A over the rows
+  that satisfy P (all rows without P).  The rows come from the row-by-row
+  evaluator (``oracle.select``), the distinct values from a Python set of the
+  selected values; float32 -0.0 and +0.0 are one value (they compare equal).
+* |R join S| = |R||S| / max(V(R,A), V(S,A)).
+"""
+from __future__ import annotations
+
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import OTable, select
+
+
+def count_distinct(t: OTable, col: int, tree: Optional[tuple] = None, threads: int = 1) -> Tuple[int, int]:
+    a = t.arrays[col]
+    rows = np.arange(t.n_rows) if tree is None else select(t, tree, threads=threads)
+    vals = a[rows]
+    if vals.dtype == np.float32:
+        vals = np.where(vals == 0, np.float32(0.0), vals)   # -0.0 == +0.0
+    return len(set(vals.tolist())), int(len(rows))
+
+
+def join_size_estimate(rows_r: int, rows_s: int, distinct_r: int, distinct_s: int) -> float:
+    v = max(distinct_r, distinct_s)
+    return 0.0 if v == 0 else rows_r * rows_s / v

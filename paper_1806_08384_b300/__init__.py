@@ -111,6 +111,8 @@ def _load():
         "sel_ctx_launch_count": (C.c_uint64, [V]),
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
+        "sel_count_distinct": (C.c_int, [V, P(sel_table), C.c_int32, V, P(C.c_uint64), P(C.c_uint64)]),
+        "sel_join_size_estimate": (C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]),
         "sel_evaluate_and_push_down": (C.c_int, [V, P(sel_spd_relation), C.c_int32, P(sel_spd_cfg), P(C.c_int32),
                                                  P(C.c_uint64), P(C.c_uint64)]),
         "sel_mlp_create": (C.c_int, [V, P(sel_table), C.c_int32, C.c_uint64, P(V)]),
@@ -316,6 +318,14 @@ class Context:
 
     def set_scan_shape(self, tile_rows=0, stages=0, ctas_per_sm=0):
         _check(lib.sel_ctx_set_scan_shape(self.h, tile_rows, stages, ctas_per_sm), "sel_ctx_set_scan_shape")
+
+    def count_distinct(self, table, col: int, pred: Optional[Predicate] = None):
+        """(V(sigma_P(R), col), |sigma_P(R)|): distinct values of a column over the selected rows."""
+        table = Table.of(table)
+        d, r = C.c_uint64(), C.c_uint64()
+        _check(lib.sel_count_distinct(self.h, table.ref(), int(col), pred.h if pred is not None else None,
+                                      C.byref(d), C.byref(r)), "sel_count_distinct")
+        return int(d.value), int(r.value)
 
     def set_scan_variant(self, consumer_warps=0, chunks_per_pass=0):
         _check(lib.sel_ctx_set_scan_variant(self.h, consumer_warps, chunks_per_pass), "sel_ctx_set_scan_variant")
@@ -652,3 +662,8 @@ def evaluate_and_push_down(ctx: "Context", relations, min_table_size: int = 0, m
             d["rowids"] = ids[:d["count"]] if ids is not None else None
         res.append(d)
     return res
+
+
+def join_size_estimate(rows_r: int, rows_s: int, distinct_r: int, distinct_s: int) -> float:
+    """|R join S| = |R||S| / max(V(R,A), V(S,A)) (sel_join_size_estimate)."""
+    return float(lib.sel_join_size_estimate(int(rows_r), int(rows_s), int(distinct_r), int(distinct_s)))

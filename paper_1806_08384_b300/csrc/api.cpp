@@ -77,6 +77,8 @@ struct sel_ctx {
     DevBuf counts;            // sel_count / batch staging
     DevBuf err;               // 4 bytes: error flag of the last launches
     DevBuf pd_scratch;        // push-down: tile status | tile counter | total
+    DevBuf distinct_vals;     // sel_count_distinct: the selected values
+    DevBuf distinct_table;    // sel_count_distinct: hash set | new-key counter | flags
     unsigned long long* h_pinned = nullptr;   // pinned host results (count, total)
     unsigned int* h_err = nullptr;
     size_t h_cap = 0;
@@ -599,6 +601,74 @@ extern "C" sel_status sel_pushdown_async(sel_ctx* ctx, const sel_pred* pred, con
     }
     return pushdown_enqueue(ctx, pred, table, proj_cols, n_proj, dev_out_cols, dev_out_rowids, max_rows,
                             reinterpret_cast<unsigned long long*>(dev_out_count), "sel_pushdown_async");
+}
+
+// ---------------------------------------------------------------------------
+// V(R, A) and the join-size estimate of §1.1 / §3.2
+// ---------------------------------------------------------------------------
+
+namespace sel {
+cudaError_t launch_distinct(const uint8_t* col, int type, int64_t n, unsigned long long* table, unsigned long long cap,
+                            unsigned long long* n_new, unsigned int* flags, int n_sm, cudaStream_t st);
+}
+
+extern "C" sel_status sel_count_distinct(sel_ctx* ctx, const sel_table* table, int32_t col, const sel_pred* pred,
+                                         uint64_t* out_distinct, uint64_t* out_rows) {
+    const char* who = "sel_count_distinct";
+    if (!ctx || !table || !out_distinct || col < 0 || col >= table->n_cols || table->n_rows < 0) {
+        set_error("%s: bad arguments", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    const sel_column& c = table->cols[col];
+    const int type = c.type == SEL_I64 ? 1 : c.type == SEL_F32 ? 2 : 0;
+    const uint32_t width = c.type == SEL_I64 ? 8u : 4u;
+    if (table->n_rows > 0 && (!c.data || reinterpret_cast<uintptr_t>(c.data) % width)) {
+        set_error("%s: column %d: null or misaligned data", who, col);
+        return SEL_ERR_INVALID_ARG;
+    }
+    const uint8_t* vals = static_cast<const uint8_t*>(c.data);
+    uint64_t nv = (uint64_t)table->n_rows;
+    if (pred) {   // the selected values, compacted by the push-down
+        sel_status s = ctx->distinct_vals.ensure(std::max<size_t>(1, (size_t)table->n_rows) * width, who);
+        if (s != SEL_OK) return s;
+        void* dst = ctx->distinct_vals.p;
+        const int32_t proj = col;
+        uint64_t cnt = 0;
+        s = sel_pushdown(ctx, pred, table, &proj, 1, &dst, nullptr, (uint64_t)table->n_rows, &cnt);
+        if (s != SEL_OK) return s;
+        vals = static_cast<const uint8_t*>(ctx->distinct_vals.p);
+        nv = cnt;
+    }
+    unsigned long long cap = 1024;
+    while (cap < 2 * (unsigned long long)nv) cap <<= 1;
+    sel_status s = ctx->distinct_table.ensure((size_t)cap * 8 + 64, who);
+    if (s != SEL_OK) return s;
+    unsigned long long* tab = static_cast<unsigned long long*>(ctx->distinct_table.p);
+    unsigned long long* n_new = tab + cap;
+    unsigned int* flags = reinterpret_cast<unsigned int*>(tab + cap + 1);
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(tab, 0xFF, (size_t)cap * 8, ctx->stream));
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(n_new, 0, 64, ctx->stream));
+    cudaError_t e = launch_distinct(vals, type, (int64_t)nv, tab, cap, n_new, flags, ctx->n_sm, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail("distinct launch", e);
+    if (nv > 0) ctx->launches++;
+    s = ensure_host(ctx, 2);
+    if (s != SEL_OK) return s;
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_pinned, n_new, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_err, flags, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_and_check(ctx, who);
+    if (s != SEL_OK) return s;
+    if (*ctx->h_err & 1u) {
+        set_error("%s: a probe sequence exceeded the table", who);
+        return SEL_ERR_CUDA;
+    }
+    *out_distinct = ctx->h_pinned[0] + ((*ctx->h_err & 2u) ? 1u : 0u);
+    if (out_rows) *out_rows = nv;
+    return SEL_OK;
+}
+
+extern "C" double sel_join_size_estimate(uint64_t rows_r, uint64_t rows_s, uint64_t distinct_r, uint64_t distinct_s) {
+    const uint64_t v = std::max(distinct_r, distinct_s);
+    return v == 0 ? 0.0 : (double)rows_r * (double)rows_s / (double)v;
 }
 
 extern "C" sel_status sel_pushdown(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
