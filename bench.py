@@ -443,8 +443,24 @@ def star_batch(sel, peak: float, device, reps=5):
         res[mode + "_counts"] = out.cpu().tolist()
     assert res["batched_counts"] == res["separate_counts"]
     del res["batched_counts"], res["separate_counts"]
+    # f3 / f4 on the star: the exact COUNT of sigma(fact) join sigma(dim) on fact.a1 = dim.key
+    # next to the join-size estimate from exact selectivities and distinct counts
+    joins = []
+    fact_p = preds[0]
+    for k in (1, 2, 3):
+        dim_i = next(i for i, (ti, _) in enumerate(probes) if ti == k)
+        t0 = time.perf_counter()
+        exact, nr, ns = ctx.join_count(T[0], 1, fact_p, T[k], 0, preds[dim_i])
+        join_ms = (time.perf_counter() - t0) * 1e3
+        vr, _ = ctx.count_distinct(T[0], 1, fact_p)
+        vs, _ = ctx.count_distinct(T[k], 0, preds[dim_i])
+        est = sel.join_size_estimate(nr, ns, vr, vs)
+        joins.append({"dimension_rows": tabs[k].n_rows, "fact_selected": nr, "dim_selected": ns,
+                      "join_count": exact, "join_count_ms": round(join_ms, 3), "estimate": round(est, 1),
+                      "estimate_q_error": round(max(est, 1.0, exact) / max(min(est, exact), 1.0), 3)})
     info = plan.info()
     res.update({
+        "join_counts": joins,
         "workload": "config3 star: fact 480M x 6 cols (i32 U/Zipf/U, f32 U/N/U) + dims 2k/200k/2.4M/16M x 4 cols; "
                     "32 fact probes + 8 per dimension, OR of 1-3 ANDs, s log-uniform in [1e-4, 0.5]",
         "speedup": round(res["separate_ms"] / res["batched_ms"], 3),

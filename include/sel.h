@@ -285,6 +285,19 @@ sel_status sel_ctx_debug_pushdown_fault(sel_ctx* ctx, int64_t skip_tile, uint64_
 sel_status sel_count_distinct(sel_ctx* ctx, const sel_table* table, int32_t col, const sel_pred* pred,
                               uint64_t* out_distinct, uint64_t* out_rows);
 
+/* The exact COUNT(*) of sigma_P(R) join sigma_Q(S) on R.col_r = S.col_s (the
+ * two-relation COUNT query of the paper's experiments, Ch5): the selected keys
+ * of both sides (compacted by the push-down when a predicate is given), a
+ * key -> multiplicity hash map of the side with fewer rows, probed with the
+ * other side.  Keys are compared as values: both columns int32-like (int32,
+ * date, dictionary code) or both int64 or both float32 (-0.0 == +0.0; a
+ * float32 key with an integer key: SEL_ERR_TYPE; int32 with int64:
+ * SEL_ERR_UNSUPPORTED).  out_rows_r / out_rows_s (nullable): the selected row
+ * counts.  Device scratch owned by the context.  Synchronous. */
+sel_status sel_join_count(sel_ctx* ctx, const sel_table* r, int32_t col_r, const sel_pred* pred_r,
+                          const sel_table* s, int32_t col_s, const sel_pred* pred_s, uint64_t* out_count,
+                          uint64_t* out_rows_r, uint64_t* out_rows_s);
+
 /* rows_r * rows_s / max(distinct_r, distinct_s); 0 when both are 0. */
 double sel_join_size_estimate(uint64_t rows_r, uint64_t rows_s, uint64_t distinct_r, uint64_t distinct_s);
 

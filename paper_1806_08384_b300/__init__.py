@@ -113,6 +113,8 @@ def _load():
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
         "sel_count_distinct": (C.c_int, [V, P(sel_table), C.c_int32, V, P(C.c_uint64), P(C.c_uint64)]),
         "sel_join_size_estimate": (C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]),
+        "sel_join_count": (C.c_int, [V, P(sel_table), C.c_int32, V, P(sel_table), C.c_int32, V, P(C.c_uint64),
+                                     P(C.c_uint64), P(C.c_uint64)]),
         "sel_evaluate_and_push_down": (C.c_int, [V, P(sel_spd_relation), C.c_int32, P(sel_spd_cfg), P(C.c_int32),
                                                  P(C.c_uint64), P(C.c_uint64)]),
         "sel_mlp_create": (C.c_int, [V, P(sel_table), C.c_int32, C.c_uint64, P(V)]),
@@ -326,6 +328,15 @@ class Context:
         _check(lib.sel_count_distinct(self.h, table.ref(), int(col), pred.h if pred is not None else None,
                                       C.byref(d), C.byref(r)), "sel_count_distinct")
         return int(d.value), int(r.value)
+
+    def join_count(self, r, col_r: int, pred_r: Optional[Predicate], s, col_s: int, pred_s: Optional[Predicate]):
+        """(COUNT(*) of sigma_P(R) join sigma_Q(S) on R.col_r = S.col_s, |sigma_P(R)|, |sigma_Q(S)|)."""
+        r, s = Table.of(r), Table.of(s)
+        c, nr, ns = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib.sel_join_count(self.h, r.ref(), int(col_r), pred_r.h if pred_r is not None else None, s.ref(),
+                                  int(col_s), pred_s.h if pred_s is not None else None, C.byref(c), C.byref(nr),
+                                  C.byref(ns)), "sel_join_count")
+        return int(c.value), int(nr.value), int(ns.value)
 
     def set_scan_variant(self, consumer_warps=0, chunks_per_pass=0):
         _check(lib.sel_ctx_set_scan_variant(self.h, consumer_warps, chunks_per_pass), "sel_ctx_set_scan_variant")

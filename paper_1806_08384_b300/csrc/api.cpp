@@ -79,6 +79,7 @@ struct sel_ctx {
     DevBuf pd_scratch;        // push-down: tile status | tile counter | total
     DevBuf distinct_vals;     // sel_count_distinct: the selected values
     DevBuf distinct_table;    // sel_count_distinct: hash set | new-key counter | flags
+    DevBuf join_vals;         // sel_join_count: the second side's selected keys
     unsigned long long* h_pinned = nullptr;   // pinned host results (count, total)
     unsigned int* h_err = nullptr;
     size_t h_cap = 0;
@@ -663,6 +664,96 @@ extern "C" sel_status sel_count_distinct(sel_ctx* ctx, const sel_table* table, i
     }
     *out_distinct = ctx->h_pinned[0] + ((*ctx->h_err & 2u) ? 1u : 0u);
     if (out_rows) *out_rows = nv;
+    return SEL_OK;
+}
+
+namespace sel {
+cudaError_t launch_join_count(const uint8_t* build, int64_t n_build, const uint8_t* probe, int64_t n_probe, int type,
+                              unsigned long long* keys, unsigned long long* mult, unsigned long long cap,
+                              unsigned long long* counters, unsigned int* flags, int n_sm, cudaStream_t st);
+
+// The key values of the selected rows of one side: the column itself, or the
+// push-down's compaction of it into `buf`.
+static sel_status join_side(sel_ctx* ctx, const sel_table* t, int32_t col, const sel_pred* pred, DevBuf& buf,
+                            const uint8_t** vals, uint64_t* n, const char* who) {
+    const sel_column& c = t->cols[col];
+    const uint32_t width = c.type == SEL_I64 ? 8u : 4u;
+    if (t->n_rows > 0 && (!c.data || reinterpret_cast<uintptr_t>(c.data) % width)) {
+        set_error("%s: column %d: null or misaligned data", who, col);
+        return SEL_ERR_INVALID_ARG;
+    }
+    *vals = static_cast<const uint8_t*>(c.data);
+    *n = (uint64_t)t->n_rows;
+    if (!pred) return SEL_OK;
+    sel_status s = buf.ensure(std::max<size_t>(1, (size_t)t->n_rows) * width, who);
+    if (s != SEL_OK) return s;
+    void* dst = buf.p;
+    uint64_t cnt = 0;
+    s = sel_pushdown(ctx, pred, t, &col, 1, &dst, nullptr, (uint64_t)t->n_rows, &cnt);
+    if (s != SEL_OK) return s;
+    *vals = static_cast<const uint8_t*>(buf.p);
+    *n = cnt;
+    return SEL_OK;
+}
+}  // namespace sel
+
+extern "C" sel_status sel_join_count(sel_ctx* ctx, const sel_table* r, int32_t col_r, const sel_pred* pred_r,
+                                     const sel_table* s_tab, int32_t col_s, const sel_pred* pred_s,
+                                     uint64_t* out_count, uint64_t* out_rows_r, uint64_t* out_rows_s) {
+    const char* who = "sel_join_count";
+    if (!ctx || !r || !s_tab || !out_count || col_r < 0 || col_r >= r->n_cols || col_s < 0 || col_s >= s_tab->n_cols) {
+        set_error("%s: bad arguments", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    const bool fr = r->cols[col_r].type == SEL_F32, fs = s_tab->cols[col_s].type == SEL_F32;
+    if (fr != fs) {
+        set_error("%s: a float32 key joins only a float32 key", who);
+        return SEL_ERR_TYPE;
+    }
+    const uint8_t *vr = nullptr, *vs = nullptr;
+    uint64_t nr = 0, ns = 0;
+    sel_status st = join_side(ctx, r, col_r, pred_r, ctx->distinct_vals, &vr, &nr, who);
+    if (st != SEL_OK) return st;
+    st = join_side(ctx, s_tab, col_s, pred_s, ctx->join_vals, &vs, &ns, who);
+    if (st != SEL_OK) return st;
+    // keys of different widths: widen both sides to the same 64-bit keys (type codes of distinct.cu)
+    const int type_r = r->cols[col_r].type == SEL_I64 ? 1 : fr ? 2 : 0;
+    const int type_s = s_tab->cols[col_s].type == SEL_I64 ? 1 : fs ? 2 : 0;
+    if (type_r != type_s) {
+        set_error("%s: int32 and int64 keys: join columns of the same width", who);
+        return SEL_ERR_UNSUPPORTED;
+    }
+    const bool build_r = nr <= ns;
+    const uint8_t* build = build_r ? vr : vs;
+    const uint8_t* probe = build_r ? vs : vr;
+    const uint64_t nb = build_r ? nr : ns, np = build_r ? ns : nr;
+    unsigned long long cap = 1024;
+    while (cap < 2 * (unsigned long long)nb) cap <<= 1;
+    st = ctx->distinct_table.ensure((size_t)cap * 16 + 64, who);
+    if (st != SEL_OK) return st;
+    unsigned long long* keys = static_cast<unsigned long long*>(ctx->distinct_table.p);
+    unsigned long long* mult = keys + cap;
+    unsigned long long* counters = keys + 2 * cap;
+    unsigned int* flags = reinterpret_cast<unsigned int*>(keys + 2 * cap + 2);
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(keys, 0xFF, (size_t)cap * 8, ctx->stream));
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(mult, 0, (size_t)cap * 8 + 64, ctx->stream));
+    cudaError_t e = launch_join_count(build, (int64_t)nb, probe, (int64_t)np, type_r, keys, mult, cap, counters, flags,
+                                      ctx->n_sm, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail("join count launch", e);
+    ctx->launches += (nb > 0 ? 1 : 0) + (nb > 0 && np > 0 ? 1 : 0);
+    st = ensure_host(ctx, 2);
+    if (st != SEL_OK) return st;
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_pinned, counters, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_err, flags, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    st = sync_and_check(ctx, who);
+    if (st != SEL_OK) return st;
+    if (*ctx->h_err & 1u) {
+        set_error("%s: a probe sequence exceeded the table", who);
+        return SEL_ERR_CUDA;
+    }
+    *out_count = ctx->h_pinned[0];
+    if (out_rows_r) *out_rows_r = nr;
+    if (out_rows_s) *out_rows_s = ns;
     return SEL_OK;
 }
 

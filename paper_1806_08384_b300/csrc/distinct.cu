@@ -88,3 +88,100 @@ cudaError_t launch_distinct(const uint8_t* col, int type, int64_t n, unsigned lo
 }
 
 }  // namespace sel
+
+// ---------------------------------------------------------------------------
+// COUNT(*) over a key join of two (selected) relations: the build side's keys
+// go into an open-addressing map key -> multiplicity (same hashing, empty
+// marker and -0.0 folding as above), then every key of the probe side adds
+// the multiplicity of its key.  Build-side keys equal to the empty marker are
+// counted apart and matched by probe keys equal to it.
+// ---------------------------------------------------------------------------
+
+namespace sel {
+
+__global__ void __launch_bounds__(256) join_build_kernel(const uint8_t* col, int type, int64_t n,
+                                                         unsigned long long* keys, unsigned long long* mult,
+                                                         unsigned long long cap, unsigned long long* marker_mult,
+                                                         unsigned int* flags) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long k = key_of(col, type, i);
+        if (k == kEmpty) {
+            atomicAdd(marker_mult, 1ull);
+            continue;
+        }
+        unsigned long long h = mix64(k) & (cap - 1);
+        for (unsigned long long probes = 0;; ++probes) {
+            if (probes > cap) {
+                atomicOr(flags, 1u);
+                break;
+            }
+            const unsigned long long prev = atomicCAS(&keys[h], kEmpty, k);
+            if (prev == kEmpty || prev == k) {
+                atomicAdd(&mult[h], 1ull);
+                break;
+            }
+            h = (h + 1) & (cap - 1);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) join_probe_kernel(const uint8_t* col, int type, int64_t n,
+                                                         const unsigned long long* keys,
+                                                         const unsigned long long* mult, unsigned long long cap,
+                                                         const unsigned long long* marker_mult,
+                                                         unsigned long long* total, unsigned int* flags) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const uint32_t lane = threadIdx.x & 31u;
+    unsigned long long acc = 0;
+    for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        if (i < n) {
+            const unsigned long long k = key_of(col, type, i);
+            if (k == kEmpty) {
+                acc += *marker_mult;
+            } else {
+                unsigned long long h = mix64(k) & (cap - 1);
+                for (unsigned long long probes = 0;; ++probes) {
+                    if (probes > cap) {
+                        atomicOr(flags, 1u);
+                        break;
+                    }
+                    const unsigned long long kk = keys[h];
+                    if (kk == k) {
+                        acc += mult[h];
+                        break;
+                    }
+                    if (kk == kEmpty) break;   // not on the build side
+                    h = (h + 1) & (cap - 1);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0 && acc) atomicAdd(total, acc);
+}
+
+cudaError_t launch_join_count(const uint8_t* build, int64_t n_build, const uint8_t* probe, int64_t n_probe, int type,
+                              unsigned long long* keys, unsigned long long* mult, unsigned long long cap,
+                              unsigned long long* counters, unsigned int* flags, int n_sm, cudaStream_t st) {
+    // counters[0]: the join count; counters[1]: build-side keys equal to the empty marker
+    auto grid_for = [&](int64_t n) {
+        const int64_t b = (n + 255) / 256;
+        return static_cast<int>(b < (int64_t)n_sm * 8 ? (b > 0 ? b : 1) : (int64_t)n_sm * 8);
+    };
+    if (n_build > 0) {
+        join_build_kernel<<<grid_for(n_build), 256, 0, st>>>(build, type, n_build, keys, mult, cap, counters + 1, flags);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (n_probe > 0 && n_build > 0) {
+        join_probe_kernel<<<grid_for(n_probe), 256, 0, st>>>(probe, type, n_probe, keys, mult, cap, counters + 1,
+                                                             counters, flags);
+        return cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
+}  // namespace sel

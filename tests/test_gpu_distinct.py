@@ -69,3 +69,44 @@ def test_full_size_key_columns(ctx, dev):
     d, r = ctx.count_distinct(T, 2, sel.Predicate(T, tree))
     st, cnt, cols, ids = ctx.pushdown(sel.Predicate(T, tree), T, [2], r)
     assert cnt == r and d == int(torch.unique(cols[0]).numel())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_join_count_tiny(ctx, dev, seed):
+    rng = np.random.default_rng(seed)
+    tr = dg.tiny_table(int(rng.integers(0, 30_000)), seed=seed)
+    ts = dg.tiny_table(int(rng.integers(0, 3_000)), seed=seed + 100)
+    otr, ots = oracle.OTable.from_table(tr), oracle.OTable.from_table(ts)
+    Tr, Ts = sel.Table(tr.to(dev).columns), sel.Table(ts.to(dev).columns)
+    for col in range(5):   # same-type key columns: i32, i64, f32, date, dict
+        for _ in range(3):
+            pr = dg.random_tree(tr, rng, depth=3) if rng.random() < 0.8 else None
+            ps = dg.random_tree(ts, rng, depth=3) if rng.random() < 0.8 else None
+            got = ctx.join_count(Tr, col, sel.Predicate(Tr, pr) if pr else None, Ts, col,
+                                 sel.Predicate(Ts, ps) if ps else None)
+            assert got == join.join_count(otr, col, pr, ots, col, ps), (col, pr, ps)
+
+
+def test_join_count_star_dimension(ctx, dev):
+    """Fact a0 (uniform over 2^31) would rarely meet a dimension key: join the fact's
+    Zipf column a1 (1000 values) with each dimension's key under their predicates."""
+    tabs = dg.config3_tables(fact_rows=2_000_000, device=dev)
+    ot = [oracle.OTable.from_table(t) for t in tabs]
+    T = [sel.Table(t.columns) for t in tabs]
+    probes = dg.config3_predicates()
+    fact_tree = next(tr for ti, tr in probes if ti == 0)
+    for k in range(1, len(tabs)):
+        dim_tree = next(tr for ti, tr in probes if ti == k)
+        got = ctx.join_count(T[0], 1, sel.Predicate(T[0], fact_tree), T[k], 0, sel.Predicate(T[k], dim_tree))
+        assert got == join.join_count(ot[0], 1, fact_tree, ot[k], 0, dim_tree, threads=8), k
+
+
+def test_join_count_type_rules(ctx, dev):
+    t = dg.tiny_table(100, seed=1)
+    T = sel.Table(t.to(dev).columns)
+    with pytest.raises(sel.SelError) as e:
+        ctx.join_count(T, 0, None, T, 2, None)       # int32 with float32
+    assert e.value.status == sel.SEL_ERR_TYPE
+    with pytest.raises(sel.SelError) as e:
+        ctx.join_count(T, 0, None, T, 1, None)       # int32 with int64
+    assert e.value.status == sel.SEL_ERR_UNSUPPORTED

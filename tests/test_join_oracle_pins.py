@@ -32,3 +32,24 @@ def test_distinct_counts_by_construction():
     d, r = join.count_distinct(t, 1, dg.p_cmp(0, "<", 100))
     assert r == 100 and d == len(set(mod[perm < 100].tolist()))
     assert join.count_distinct(t, 1, dg.P_FALSE) == (0, 0)
+
+
+def test_join_count_brute_force_and_key_join():
+    rng = np.random.default_rng(5)
+    a = rng.integers(0, 6, 300).astype(np.int32)
+    b = rng.integers(2, 9, 200).astype(np.int32)
+    r = oracle.OTable([a], ["i32"], [None])
+    s = oracle.OTable([b], ["i32"], [None])
+    brute = sum(1 for x in a for y in b if x == y)
+    assert join.join_count(r, 0, None, s, 0, None) == (brute, 300, 200)
+    sel_r = dg.p_cmp(0, ">=", 3)
+    brute = sum(1 for x in a if x >= 3 for y in b if x == y)
+    assert join.join_count(r, 0, sel_r, s, 0, None)[0] == brute
+    # a join on S's distinct key (§1.1: primary keys are distinct): every selected R row matches once,
+    # so the join has exactly |sigma(R)| rows, as the plan sizes of §1.1 assume
+    keys = np.arange(1000, dtype=np.int64)
+    fk = rng.integers(0, 1000, 5000).astype(np.int64)
+    rr = oracle.OTable([fk], ["i64"], [None])
+    ss = oracle.OTable([keys], ["i64"], [None])
+    c, nr, ns = join.join_count(rr, 0, dg.p_cmp(0, "<", 100), ss, 0, None)
+    assert c == nr == int(np.sum(fk < 100)) and ns == 1000
