@@ -653,14 +653,7 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = step.ctx.launches - launches0
-    elapsed_ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-        dist.barrier()
-    total_bytes = step_bytes * args.steps * world
-    value = total_bytes / (elapsed_ms / 1e3) / 1e9
+    elapsed_ms, value = replica_throughput(t0.elapsed_time(t1), step_bytes, args.steps, world, dev)
 
     # per-kernel durations inside the timed region
     dur = {"count": [], "pushdown": []}
@@ -745,6 +738,18 @@ def run_e2e(step: OurStep, args, step_bytes):
     ms = t0.elapsed_time(t1) / k
     return {"value": round(step_bytes / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": k}
+
+
+def replica_throughput(elapsed_ms: float, step_bytes: int, steps: int, world: int, device) -> tuple:
+    """Replicas (one per GPU, each over its own table): the job's time is the
+    slowest rank's (all-reduce MAX), its throughput all ranks' bytes over it."""
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+        dist.barrier()
+    return elapsed_ms, step_bytes * steps * world / (elapsed_ms / 1e3) / 1e9
 
 
 def workload_config(n: int, probes: int, pushed: int, world: int = 1) -> dict:
