@@ -474,32 +474,32 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     a.n_slots = ta.n_slots;
     a.row_bytes = ta.row_bytes;
     a.tma = ta.tma;
-    // The persistent kernel: super-tiles of 16384 rows streamed in sub-tiles
-    // through shared-memory stages.  Variant: the context's scan variant, else
-    // 16 consumer warps x 2 chunks per pass.  Sub-tile: the requested tile size,
-    // else the largest power of two with 3 or more stages (else 2).  A tile
-    // size the persistent kernel cannot use, or predicate columns too wide for
-    // two stages, take the one-CTA-per-tile kernel (1024 rows or as requested).
+    // The persistent kernel: super-tiles (the largest multiple of the sub-tile
+    // up to 16384 rows) streamed in sub-tiles through shared-memory stages.
+    // Variant: the context's scan variant, else 16 consumer warps x 2 chunks
+    // per pass.  Sub-tile and stages: the requested ones, else the count
+    // scan's rule (about 64 KB per stage, 3 stages), the sub-tile rounded down
+    // to whole chunk groups and shrunk until the stages fit.  A tile size the
+    // persistent kernel cannot use, or predicate columns too wide for two
+    // stages, take the one-CTA-per-tile kernel (1024 rows or as requested).
     {
         const int req = ctx->shape.tile_rows;
         const int W = ctx->shape.warps > 0 ? ctx->shape.warps : 16;
         const int G = ctx->shape.group > 0 ? ctx->shape.group : 2;
+        const int unit = kChunkRows * G;
         int best_tr = 0, best_s = 0;
         if (pushdown_persistent_ok(W, G) && ta.row_bytes > 0) {
-            for (int min_s = 3; min_s >= 2 && best_tr == 0; --min_s) {
-                for (int tr = kPdpSuperRows; tr >= kChunkRows; tr /= 2) {
-                    if (req != 0 && tr != req) continue;
-                    if (!pushdown_persistent_tile_ok((uint32_t)tr, G)) continue;
-                    PushdownArgs p = a;
-                    p.blob_bytes = pred->blob_bytes;
-                    p.row_bytes = ta.row_bytes;
-                    p.tile_rows = (uint32_t)tr;
-                    int S = ctx->shape.stages > 0 ? ctx->shape.stages : 6;
-                    for (; S >= min_s; --S) {
-                        p.stages = (uint32_t)S;
-                        if (pushdown_persistent_layout(p) <= (size_t)ctx->max_smem_pdp) break;
-                    }
-                    if (S >= min_s) {
+            const int tr0 = req > 0 ? req : std::max(unit, default_tile_rows(ta.row_bytes, 64 * 1024) / unit * unit);
+            for (int tr = tr0; tr >= unit && best_tr == 0; tr -= unit) {
+                if (req > 0 && tr != req) break;
+                if (!pushdown_persistent_tile_ok((uint32_t)tr, G)) continue;
+                PushdownArgs p = a;
+                p.blob_bytes = pred->blob_bytes;
+                p.row_bytes = ta.row_bytes;
+                p.tile_rows = (uint32_t)tr;
+                for (int S = ctx->shape.stages > 0 ? ctx->shape.stages : 3; S >= 2; --S) {
+                    p.stages = (uint32_t)S;
+                    if (pushdown_persistent_layout(p) <= (size_t)ctx->max_smem_pdp) {
                         best_tr = tr;
                         best_s = S;
                         break;
@@ -528,7 +528,8 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
                 off += a.tile_rows * ta.width[j];
             }
             a.n_rows = table->n_rows;
-            a.n_tiles = (table->n_rows + kPdpSuperRows - 1) / kPdpSuperRows;   // look-back unit: super-tiles
+            a.super_rows = pushdown_super_rows(a.tile_rows);
+            a.n_tiles = (table->n_rows + a.super_rows - 1) / a.super_rows;   // look-back unit: super-tiles
             a.n_proj = (uint32_t)n_proj;
             a.rowids = reinterpret_cast<long long*>(dev_out_rowids);
             a.max_rows = max_rows;

@@ -136,11 +136,9 @@ __global__ void __launch_bounds__((W + 1) * 32, (W == 8 && G < 4) ? 2 : 1) scan_
             const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
             const uint32_t n_groups = (n_chunks + G - 1) / G;
             const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
-            // lane 0 waits for the stage; the warp follows its verdict (one decision per warp)
-            uint32_t okw = 0;
-            if (lane == 0) okw = mbar_wait_bounded(&full[s], parity) ? 1u : 0u;
-            okw = __shfl_sync(0xFFFFFFFFu, okw, 0);
-            __syncwarp();
+            // every lane waits for the stage (a lane-0-only wait with the other
+            // lanes parked at a shuffle resumes much later); one verdict per warp
+            const bool okw = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(&full[s], parity));
             if (!okw) {
                 if (lane == 0) {
                     atomicOr(a.err, 1u);

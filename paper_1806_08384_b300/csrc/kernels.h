@@ -84,8 +84,9 @@ struct PushdownArgs {
     long long skip_publish_tile;
     unsigned long long wait_ns;
     uint32_t smem_prog_off, smem_stage_off, smem_out_off, smem_bytes;
-    // persistent kernel only: pipeline stages of tile_rows rows each
-    uint32_t stages, stage_bytes;
+    // persistent kernel only: pipeline stages of tile_rows rows each; the
+    // look-back unit (n_tiles of them) is a super-tile of super_rows rows
+    uint32_t stages, stage_bytes, super_rows;
     unsigned long long* tile_counter64;   // zeroed; tiles handed out in order
 };
 
@@ -95,13 +96,14 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
 // Persistent push-down: one CTA per SM with W consumer warps (8 or 16)
 // evaluating groups of G chunks (1 or 2), a producer warp and a look-back warp;
 // sub-tiles of tile_rows rows stream through `stages` shared-memory stages and
-// the look-back unit (n_tiles, status words) is a super-tile of kPdpMaxChunks
-// chunks = 16384 rows.
+// the look-back unit (n_tiles, status words) is a super-tile of super_rows
+// rows: the largest multiple of tile_rows that is at most kPdpMaxChunks chunks
+// (16384 rows).
 constexpr int kPdpMaxChunks = 64;
-constexpr int kPdpSuperRows = kPdpMaxChunks * kChunkRows;
 bool pushdown_persistent_ok(int warps, int chunks_per_pass);
-// tile_rows: a multiple of chunks_per_pass chunks whose chunk count divides kPdpMaxChunks.
+// tile_rows: a multiple of chunks_per_pass chunks, at most kPdpMaxChunks chunks.
 bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass);
+uint32_t pushdown_super_rows(uint32_t tile_rows);
 // Fills the shared-memory offsets for a.stages stages of a.tile_rows rows; returns the bytes needed.
 size_t pushdown_persistent_layout(PushdownArgs& a);
 cudaError_t pushdown_persistent_max_smem(int optin, int* dyn_max);

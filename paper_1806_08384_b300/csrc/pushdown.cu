@@ -209,10 +209,11 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 // ===========================================================================
 // Persistent push-down over super-tiles (the default path).
 //
-// The look-back unit is a super-tile of 16384 rows; a CTA streams a super-tile
-// through its shared-memory stages a sub-tile (tile_rows rows) at a time and
-// keeps only the row masks (1 bit per row) and the per-chunk counts of it, in
-// one of three super-tile buffers.
+// The look-back unit is a super-tile: the largest multiple of the sub-tile
+// (tile_rows rows) that is at most 16384 rows.  A CTA streams a super-tile
+// through its shared-memory stages a sub-tile at a time and keeps only the row
+// masks (1 bit per row, in row order) and the per-chunk counts of it, in one
+// of three super-tile buffers.
 //
 //   producer warp   takes super-tile ids in increasing order from a global
 //                   counter and bulk-copies each sub-tile's predicate columns
@@ -221,13 +222,17 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 //                   from sub-tile to sub-tile), store masks and chunk counts
 //                   into the super-tile's buffer and free the stage at once
 //                   (empty[s]); after their part of super-tile j (evald[b])
-//                   each warp writes its chunks' selected rows of super-tile
-//                   j-1, reading the projected values of those rows from
-//                   global memory, and releases that buffer (freeb[b]);
+//                   they write the selected rows of super-tile j-1, reading
+//                   the projected values of those rows from global memory,
+//                   and release that buffer (freeb[b]);
 //   look-back warp  sums super-tile j's chunk counts, publishes its aggregate,
 //                   finds its exclusive prefix by decoupled look-back,
 //                   publishes the inclusive prefix and the chunk prefixes
 //                   (done[b]) while the consumers already stream j+1.
+// The write step ranks the super-tile's selected rows in row order and hands
+// out batches of 32 consecutive ranks to the warps: a lane finds its row from
+// the chunk prefixes and the row-order mask words, all its loads are in
+// flight together, and a batch's stores are contiguous.
 // No step waits for all consumer warps at once, so the stages keep streaming.
 // A CTA works on its super-tiles in increasing order, and what a super-tile
 // waits for (free stages, a free buffer, the look-backs of the CTA's earlier
@@ -239,7 +244,24 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 
 namespace {
 
-constexpr uint32_t kPdBufs = 3;   // super-tile buffers: evaluating j+1, look-back of j, scatter of j-1
+constexpr uint32_t kPdBufs = 3;      // super-tile buffers: evaluating j+1, look-back of j, scatter of j-1
+constexpr uint32_t kMaskWords = 8;   // 256 rows of a chunk, 32 per word, in row order
+
+// Shared-memory layout (bytes from the dynamic base) for S stages.
+struct PdLayout {
+    uint32_t tile, st_id, excl, nch, stot, cc, cp, mask, end;
+    __host__ __device__ explicit PdLayout(uint32_t S) {
+        tile = 16u * S + 3u * 8u * kPdBufs;           // after full[S], empty[S], evald/done/freeb[kPdBufs]
+        st_id = tile + 8u * S;
+        excl = st_id + 8u * kPdBufs;
+        nch = excl + 8u * kPdBufs;
+        stot = nch + 4u * kPdBufs;
+        cc = stot + 4u * kPdBufs;
+        cp = cc + 4u * kPdBufs * kPdpMaxChunks;
+        mask = (cp + 4u * kPdBufs * kPdpMaxChunks + 15u) & ~15u;   // read as uint4
+        end = mask + 4u * kPdBufs * kPdpMaxChunks * kMaskWords;
+    }
+};
 
 struct PdSmem {
     uint64_t *full, *empty;              // [S]
@@ -248,36 +270,40 @@ struct PdSmem {
     long long* st_id;                    // [kPdBufs] super-tile id of each buffer (-1: end)
     unsigned long long* excl;            // [kPdBufs] exclusive prefix of each buffer's super-tile
     uint32_t* nch;                       // [kPdBufs] chunks of each buffer's super-tile that hold rows
+    uint32_t* stot;                      // [kPdBufs] selected rows of each buffer's super-tile
     uint32_t* cc;                        // [kPdBufs][kPdpMaxChunks] chunk counts (chunks in row order)
     uint32_t* cp;                        // [kPdBufs][kPdpMaxChunks] chunk prefixes
-    uint8_t* mask;                       // [kPdBufs][kPdpMaxChunks * 32] 8-bit row mask per lane and chunk
+    uint32_t* mask;                      // [kPdBufs][kPdpMaxChunks][kMaskWords] row masks, row order
 };
 
 __device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S) {
+    const PdLayout L(S);
     PdSmem m;
     m.full = reinterpret_cast<uint64_t*>(smem);
     m.empty = m.full + S;
     m.evald = m.empty + S;
     m.done = m.evald + kPdBufs;
     m.freeb = m.done + kPdBufs;
-    m.tile = reinterpret_cast<long long*>(m.freeb + kPdBufs);
-    m.st_id = m.tile + S;
-    m.excl = reinterpret_cast<unsigned long long*>(m.st_id + kPdBufs);
-    m.nch = reinterpret_cast<uint32_t*>(m.excl + kPdBufs);
-    m.cc = m.nch + kPdBufs + 1;   // +1: 8-byte alignment of what follows is not needed, 4 is
-    m.cp = m.cc + kPdBufs * kPdpMaxChunks;
-    m.mask = reinterpret_cast<uint8_t*>(m.cp + kPdBufs * kPdpMaxChunks);
+    m.tile = reinterpret_cast<long long*>(smem + L.tile);
+    m.st_id = reinterpret_cast<long long*>(smem + L.st_id);
+    m.excl = reinterpret_cast<unsigned long long*>(smem + L.excl);
+    m.nch = reinterpret_cast<uint32_t*>(smem + L.nch);
+    m.stot = reinterpret_cast<uint32_t*>(smem + L.stot);
+    m.cc = reinterpret_cast<uint32_t*>(smem + L.cc);
+    m.cp = reinterpret_cast<uint32_t*>(smem + L.cp);
+    m.mask = reinterpret_cast<uint32_t*>(smem + L.mask);
     return m;
 }
 
-// Bounded wait by lane 0, verdict broadcast to the warp.  sleep_ns > 0: the
-// waiter sleeps between tries (for waits off the critical path).
+// Bounded wait by the whole warp; the warp goes on only if every lane saw the
+// phase complete.  Every lane waits itself: a warp whose lane 0 waits alone
+// while the other lanes park at a shuffle resumes much later after the phase
+// completes (measured: the count-like loop of this kernel ran 1.7x slower).
+// sleep_ns > 0: the waiters sleep between tries (waits off the critical path).
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32_t lane, uint32_t sleep_ns = 0) {
-    uint32_t ok = 0;
-    if (lane == 0) ok = (sleep_ns ? mbar_wait_bounded_idle(bar, parity, sleep_ns) : mbar_wait_bounded(bar, parity)) ? 1u : 0u;
-    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-    __syncwarp();
-    return ok != 0;
+    (void)lane;
+    const bool ok = sleep_ns ? mbar_wait_bounded_idle(bar, parity, sleep_ns) : mbar_wait_bounded(bar, parity);
+    return __all_sync(0xFFFFFFFFu, ok);
 }
 
 __device__ __forceinline__ void fail_flag(const PushdownArgs& a, uint32_t* s_fail) {
@@ -287,41 +313,101 @@ __device__ __forceinline__ void fail_flag(const PushdownArgs& a, uint32_t* s_fai
 
 __device__ __forceinline__ bool volatile_flag(const uint32_t* f) { return *reinterpret_cast<const volatile uint32_t*>(f) != 0; }
 
-// Writes the selected rows of chunk g of a super-tile (rows R0 + g * 256 ...)
-// whose masks and chunk prefixes are in buffer b.
-__device__ __forceinline__ void scatter_chunk(const PushdownArgs& a, const PdSmem& sm, uint32_t b, uint32_t g,
-                                              int64_t R0, unsigned long long excl, uint32_t lane) {
-    const uint32_t mk = sm.mask[(b * kPdpMaxChunks + g) * 32 + lane];
-    if (!__any_sync(0xFFFFFFFFu, mk != 0)) return;
-    // rank of the lane's rows in the chunk: half A (bits 0-3) rows come before half B
-    const uint32_t mine = __popc(mk & 0xFu) | (__popc(mk >> 4) << 16);
-    uint32_t x = mine;
+// Stores a warp's 8-bit lane masks of one chunk (bit i < 4: row 4*lane + i,
+// bit 4 + i: row 128 + 4*lane + i) as 8 row-order words: word k holds rows
+// 32k .. 32k + 31, i.e. the nibbles of lanes 8(k % 4) .. 8(k % 4) + 7 of half
+// k / 4.
+__device__ __forceinline__ void store_row_words(uint32_t* words, uint32_t m, uint32_t lane) {
+    const uint32_t sh = 4u * (lane & 7u);
+    uint32_t lo = (m & 0xFu) << sh, hi = (m >> 4) << sh;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-        if (lane >= static_cast<uint32_t>(o)) x += y;
+    for (int o = 1; o < 8; o <<= 1) {
+        lo |= __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        hi |= __shfl_xor_sync(0xFFFFFFFFu, hi, o);
     }
-    const uint32_t tot = __shfl_sync(0xFFFFFFFFu, x, 31);
-    const uint32_t ex = x - mine;
-    const unsigned long long base = excl + sm.cp[b * kPdpMaxChunks + g];
-    unsigned long long posA = base + (ex & 0xFFFFu);
-    unsigned long long posB = base + (tot & 0xFFFFu) + (ex >> 16);
-    const int64_t rc = R0 + static_cast<int64_t>(g) * kChunkRows;
-    const unsigned long long lim = a.max_rows;
-    for (uint32_t bit = 0; bit < 8; ++bit) {
-        if (!((mk >> bit) & 1u)) continue;
-        const unsigned long long pos = (bit < 4) ? posA++ : posB++;
-        if (pos >= lim) continue;
-        const int64_t row = rc + bit_row(0, lane, bit);
-        for (uint32_t jj = 0; jj < a.n_proj; ++jj) {
-            if (a.proj_width[jj] == 8)
-                reinterpret_cast<unsigned long long*>(a.proj_dst[jj])[pos] =
-                    __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[jj]) + row);
-            else
-                reinterpret_cast<unsigned int*>(a.proj_dst[jj])[pos] =
-                    __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[jj]) + row);
+    if ((lane & 7u) == 0u) words[lane >> 3] = lo;
+    else if ((lane & 7u) == 1u) words[4u + (lane >> 3)] = hi;
+}
+
+// Position of the (o+1)-th set bit of w (o < popc(w)).
+__device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t o) {
+    uint32_t pos = 0, c;
+    c = __popc(w & 0xFFFFu); if (o >= c) { o -= c; pos += 16; w >>= 16; }
+    c = __popc(w & 0xFFu);   if (o >= c) { o -= c; pos += 8;  w >>= 8; }
+    c = __popc(w & 0xFu);    if (o >= c) { o -= c; pos += 4;  w >>= 4; }
+    c = __popc(w & 0x3u);    if (o >= c) { o -= c; pos += 2;  w >>= 2; }
+    if (o >= (w & 1u)) pos += 1;
+    return pos;
+}
+
+// Writes the selected rows of the super-tile in buffer b (first row R0) to
+// output positions excl + rank.  This warp takes the batches of 32 ranks
+// first, first + step, ...; ranks at positions >= max_rows are not written.
+__device__ __forceinline__ void scatter_super(const PushdownArgs& a, const PdSmem& sm, uint32_t b, int64_t R0,
+                                              unsigned long long excl, uint32_t first, uint32_t step, uint32_t lane) {
+    const uint32_t tot = sm.stot[b];
+    const unsigned long long room = a.max_rows - excl;   // excl < max_rows
+    const uint32_t n = room < tot ? static_cast<uint32_t>(room) : tot;
+    const uint32_t nch = sm.nch[b];
+    const uint32_t* cp = sm.cp + b * kPdpMaxChunks;
+    const uint32_t* mw = sm.mask + b * kPdpMaxChunks * kMaskWords;
+    for (uint32_t r0 = first * 32u; r0 < n; r0 += step * 32u) {
+        const uint32_t r = r0 + lane;
+        const bool act = r < n;
+        int64_t row = 0;
+        if (act) {
+            // the chunk: the last one whose prefix is <= r (cp[0] = 0)
+            uint32_t lo = 0, hi = nch;
+            while (hi - lo > 1u) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (cp[mid] <= r) lo = mid;
+                else hi = mid;
+            }
+            uint32_t o = r - cp[lo];
+            const uint4* w4 = reinterpret_cast<const uint4*>(mw + lo * kMaskWords);
+            const uint4 x = w4[0], y = w4[1];
+            const uint32_t wv[kMaskWords] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+            uint32_t word = 0, wbase = 0;
+            bool found = false;
+#pragma unroll
+            for (uint32_t k = 0; k < kMaskWords; ++k) {
+                const uint32_t c = __popc(wv[k]);
+                if (!found) {
+                    if (o < c) {
+                        found = true;
+                        word = wv[k];
+                        wbase = 32u * k;
+                    } else {
+                        o -= c;
+                    }
+                }
+            }
+            row = R0 + static_cast<int64_t>(lo) * kChunkRows + wbase + select_bit(word, o);
         }
-        if (a.rowids) a.rowids[pos] = static_cast<long long>(row);
+        const unsigned long long pos = excl + r;
+        for (uint32_t j0 = 0; j0 < a.n_proj; j0 += 8) {
+            unsigned long long v[8];
+#pragma unroll
+            for (uint32_t q = 0; q < 8; ++q) {   // all loads first: they are in flight together
+                const uint32_t j = j0 + q;
+                v[q] = 0;
+                if (act && j < a.n_proj)
+                    v[q] = a.proj_width[j] == 8
+                               ? __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[j]) + row)
+                               : __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[j]) + row);
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < 8; ++q) {
+                const uint32_t j = j0 + q;
+                if (act && j < a.n_proj) {
+                    if (a.proj_width[j] == 8)
+                        reinterpret_cast<unsigned long long*>(a.proj_dst[j])[pos] = v[q];
+                    else
+                        reinterpret_cast<unsigned int*>(a.proj_dst[j])[pos] = static_cast<unsigned int>(v[q]);
+                }
+            }
+        }
+        if (act && a.rowids) a.rowids[pos] = static_cast<long long>(row);
     }
 }
 
@@ -329,13 +415,13 @@ __device__ __forceinline__ void scatter_chunk(const PushdownArgs& a, const PdSme
 
 // W consumer warps; a warp evaluates groups of G chunks with one pass over the
 // program, and group ownership rotates from sub-tile to sub-tile (as in the
-// count scan), so the sub-tile size (a.tile_rows, a power of two dividing the
-// super-tile, a multiple of G chunks) is independent of W and G.
+// count scan), so the sub-tile size (a.tile_rows, a multiple of G chunks) is
+// independent of W and G.
 template <int W, int G>
 __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(const __grid_constant__ PushdownArgs a) {
     const uint32_t TR = a.tile_rows;                   // rows per sub-tile
     const uint32_t NCH = TR / kChunkRows;              // chunks per sub-tile
-    constexpr uint32_t SR = kPdpSuperRows;             // rows per super-tile
+    const uint32_t SR = a.super_rows;                  // rows per super-tile
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint32_t s_fail;
     __shared__ long long s_issued;
@@ -473,6 +559,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             if (lane == 0) {
                 if (!ok) fail_flag(a, &s_fail);
                 sm.excl[b] = excl;
+                sm.stot[b] = tile_cnt;
                 if (t == n_super - 1) *a.total = excl + tile_cnt;
             }
             __syncwarp();
@@ -483,10 +570,10 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
         // ------------------------------- consumers ------------------------------
         const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
         const uint8_t* pool = blob + a.pool_off;
+        const bool writes = a.n_proj > 0 || a.rowids != nullptr;
         uint32_t s = 0, ph = 0;
         uint32_t rot = 0;       // running group count: group k of a sub-tile belongs to warp (rot + k) % W
         long long prev_id = -1;
-        uint32_t prev_nch = 0;
         for (uint32_t j = 0;; ++j) {
             const uint32_t b = j % kPdBufs;
             // ---- the buffer was last used by super-tile j-3: wait until every warp wrote its rows ----
@@ -530,7 +617,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
                                                                          : valid_mask(c0[q], lane, valid);
                         m[q] &= vm;
                         const uint32_t g = u * NCH + grp * G + q;   // chunk index in the super-tile (row order)
-                        sm.mask[(b * kPdpMaxChunks + g) * 32 + lane] = static_cast<uint8_t>(m[q]);
+                        store_row_words(sm.mask + (b * kPdpMaxChunks + g) * kMaskWords, m[q], lane);
                         const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(m[q])));
                         if (lane == 0) sm.cc[b * kPdpMaxChunks + g] = c;
                     }
@@ -550,7 +637,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.evald[b]);   // release: masks, counts, id visible
-            // ---- write this warp's chunks of super-tile j-1 ----
+            // ---- write this warp's batches of super-tile j-1's selected rows ----
             if (prev_id >= 0) {
                 const uint32_t pb = (j + kPdBufs - 1) % kPdBufs;
                 const bool ok = warp_wait(&sm.done[pb], ((j - 1) / kPdBufs) & 1u, lane);
@@ -558,18 +645,17 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
                     if (lane == 0) fail_flag(a, &s_fail);
                     break;
                 }
-                if (!volatile_flag(&s_fail)) {
+                if (writes && !volatile_flag(&s_fail)) {
                     const unsigned long long excl = sm.excl[pb];
-                    if (excl < a.max_rows)
-                        for (uint32_t g = warp; g < prev_nch; g += W)
-                            scatter_chunk(a, sm, pb, g, prev_id * static_cast<int64_t>(SR), excl, lane);
+                    // the first batch goes to a different warp for each super-tile
+                    const uint32_t first = (warp + W - static_cast<uint32_t>(prev_id % W)) % W;
+                    if (excl < a.max_rows) scatter_super(a, sm, pb, prev_id * static_cast<int64_t>(SR), excl, first, W, lane);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&sm.freeb[pb]);
             }
             if (t < 0 || volatile_flag(&s_fail)) break;
             prev_id = t;
-            prev_nch = n_sub * NCH;
         }
     }
     __syncthreads();
@@ -588,19 +674,21 @@ bool pushdown_persistent_ok(int warps, int chunks_per_pass) {
 }
 
 bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass) {
-    const uint32_t nch = tile_rows / kChunkRows;
-    return tile_rows % kChunkRows == 0 && nch > 0 && kPdpMaxChunks % nch == 0 && nch % chunks_per_pass == 0;
+    const uint32_t unit = kChunkRows * static_cast<uint32_t>(chunks_per_pass);
+    return tile_rows > 0 && tile_rows % unit == 0 && tile_rows <= static_cast<uint32_t>(kPdpMaxChunks * kChunkRows);
+}
+
+uint32_t pushdown_super_rows(uint32_t tile_rows) {
+    const uint32_t cap = kPdpMaxChunks * kChunkRows;
+    return tile_rows == 0 ? 0u : cap / tile_rows * tile_rows;
 }
 
 size_t pushdown_persistent_layout(PushdownArgs& a) {
-    // must match pd_smem(): barriers, stage ids, buffer fields, counts, prefixes, masks
-    const uint32_t S = a.stages, B = 3;
-    const uint32_t meta = S * 16u + B * 24u + S * 8u + B * 8u + B * 8u + (B + 1u) * 4u + 2u * B * kPdpMaxChunks * 4u +
-                          B * kPdpMaxChunks * 32u;
-    a.smem_prog_off = align_up_u32(meta, 16u);
+    const PdLayout L(a.stages);
+    a.smem_prog_off = align_up_u32(L.end, 16u);
     a.smem_stage_off = align_up_u32(a.smem_prog_off + align_up_u32(a.blob_bytes, 16u), 128u);
     a.stage_bytes = align_up_u32(a.tile_rows * a.row_bytes, 128u);   // one sub-tile of the predicate columns
-    a.smem_bytes = a.smem_stage_off + S * a.stage_bytes;
+    a.smem_bytes = a.smem_stage_off + a.stages * a.stage_bytes;
     return a.smem_bytes;
 }
 
@@ -626,6 +714,9 @@ cudaError_t pushdown_persistent_max_smem(int optin, int* dyn_max) {
 cudaError_t launch_pushdown_persistent(const PushdownArgs& a, int grid, int warps, int chunks_per_warp,
                                        cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
+    if (a.super_rows == 0 || a.super_rows % a.tile_rows != 0 ||
+        a.super_rows > static_cast<uint32_t>(kPdpMaxChunks * kChunkRows))
+        return cudaErrorInvalidValue;
     if (warps == 8 && chunks_per_warp == 1)
         pushdown_persistent_kernel<8, 1><<<grid, 10 * 32, a.smem_bytes, st>>>(a);
     else if (warps == 8 && chunks_per_warp == 2)
