@@ -245,8 +245,11 @@ sel_status sel_batch_plan_variant(const sel_batch_plan* plan, int32_t* consumer_
 void sel_batch_plan_free(sel_batch_plan* plan);
 
 /* Launch configuration override for sel_count / sel_count_async / sel_pushdown
- * (0 = keep the library default).  tile_rows must be a multiple of 256 and at
- * most 16384 (the push-down uses at most 4096). */
+ * (0 = keep the library default: 3 stages of the largest tile that fits in
+ * shared memory).  tile_rows must be a multiple of 256 and at most 16384; a
+ * larger tile than fits is shrunk.  The push-down's persistent kernel takes
+ * tiles that are whole chunk groups (256 x chunks_per_pass rows); other
+ * tiles run on its one-CTA-per-tile kernel, which uses at most 4096 rows. */
 sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stages, int32_t ctas_per_sm);
 
 /* Count-scan kernel variant for sel_count / sel_count_async (both 0 = the
@@ -264,8 +267,9 @@ sel_status sel_ctx_set_scan_variant(sel_ctx* ctx, int32_t consumer_warps, int32_
 uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
 
 /* Test hook for the bounded waits of the push-down look-back: look-back unit
- * skip_tile (a 16384-row super-tile of the default kernel, a tile of the
- * one-CTA-per-tile kernel; -1: none) never publishes its prefix, and a waiting tile gives up after
+ * skip_tile (a super-tile of the default kernel -- the largest multiple of
+ * its tile up to 16384 rows --, a tile of the one-CTA-per-tile kernel; -1:
+ * none) never publishes its prefix, and a waiting tile gives up after
  * wait_ns nanoseconds (0: the default of 2 s), so that later sel_pushdown
  * calls on this context return SEL_ERR_TIMEOUT instead of waiting forever.
  * The context stays usable; set skip_tile back to -1 to disarm. */

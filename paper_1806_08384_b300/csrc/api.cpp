@@ -261,11 +261,13 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
 
 static Shape single_shape(sel_ctx* ctx, uint32_t row_bytes) {
     Shape s;
-    // measured on the 300M-row fact table: 3 stages of about 64 KB, one CTA of
-    // 16 consumer warps per SM, 2 chunks per instruction pass
+    // measured on the 300M-row fact table: 3 stages that fill shared memory
+    // (the tile is shrunk to fit by run_scan), one CTA of 16 consumer warps
+    // per SM, 2 chunks per instruction pass
+    (void)row_bytes;
     s.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 3;
     s.ctas_per_sm = ctx->shape.ctas_per_sm > 0 ? ctx->shape.ctas_per_sm : 1;
-    s.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : default_tile_rows(row_bytes, 64 * 1024);
+    s.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : kMaxTileRows;
     s.warps = ctx->shape.warps > 0 ? ctx->shape.warps : kScanDefaultWarps;
     s.group = ctx->shape.group > 0 ? ctx->shape.group : kScanDefaultGroup;
     return s;
@@ -478,8 +480,8 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     // up to 16384 rows) streamed in sub-tiles through shared-memory stages.
     // Variant: the context's scan variant, else 16 consumer warps x 2 chunks
     // per pass.  Sub-tile and stages: the requested ones, else the count
-    // scan's rule (about 64 KB per stage, 3 stages), the sub-tile rounded down
-    // to whole chunk groups and shrunk until the stages fit.  A tile size the
+    // scan's rule: 3 stages (2 if 3 do not fit) of the largest sub-tile, in
+    // whole chunk groups, that fits in shared memory.  A tile size the
     // persistent kernel cannot use, or predicate columns too wide for two
     // stages, take the one-CTA-per-tile kernel (1024 rows or as requested).
     {
@@ -489,15 +491,15 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
         const int unit = kChunkRows * G;
         int best_tr = 0, best_s = 0;
         if (pushdown_persistent_ok(W, G) && ta.row_bytes > 0) {
-            const int tr0 = req > 0 ? req : std::max(unit, default_tile_rows(ta.row_bytes, 64 * 1024) / unit * unit);
-            for (int tr = tr0; tr >= unit && best_tr == 0; tr -= unit) {
-                if (req > 0 && tr != req) break;
-                if (!pushdown_persistent_tile_ok((uint32_t)tr, G)) continue;
-                PushdownArgs p = a;
-                p.blob_bytes = pred->blob_bytes;
-                p.row_bytes = ta.row_bytes;
-                p.tile_rows = (uint32_t)tr;
-                for (int S = ctx->shape.stages > 0 ? ctx->shape.stages : 3; S >= 2; --S) {
+            const int tr0 = req > 0 ? req : kPdpMaxChunks * kChunkRows / unit * unit;
+            for (int S = ctx->shape.stages > 0 ? ctx->shape.stages : 3; S >= 2 && best_tr == 0; --S) {
+                for (int tr = tr0; tr >= unit; tr -= unit) {
+                    if (req > 0 && tr != req) break;
+                    if (!pushdown_persistent_tile_ok((uint32_t)tr, G)) continue;
+                    PushdownArgs p = a;
+                    p.blob_bytes = pred->blob_bytes;
+                    p.row_bytes = ta.row_bytes;
+                    p.tile_rows = (uint32_t)tr;
                     p.stages = (uint32_t)S;
                     if (pushdown_persistent_layout(p) <= (size_t)ctx->max_smem_pdp) {
                         best_tr = tr;
@@ -938,24 +940,22 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     for (auto& t : p->tables) max_rb = std::max(max_rb, t.row_bytes);
     // default shape, then the autotuner's candidates (stage size, stages, CTAs
     // per SM, consumer warps, chunks per instruction pass)
-    Shape best;
-    best.stages = 3;
-    best.ctas_per_sm = 1;
-    best.tile_rows = default_tile_rows(max_rb, 64 * 1024);
-    best.warps = 16;
-    best.group = 2;
+    // (stage_kb 0: the largest tile whose stages fit in shared memory); the
+    // default shape is the single-probe count's, with the context's overrides
+    Shape best = single_shape(ctx, max_rb);
     float best_ms = 0.f;
     if (autotune) {
         struct Cand { int stage_kb, stages, ctas, warps, group; };
-        const Cand cands[] = {{64, 3, 1, 16, 2}, {48, 4, 1, 16, 2}, {96, 2, 1, 16, 2}, {64, 3, 1, 16, 1},
-                              {48, 4, 1, 16, 1}, {32, 3, 2, 8, 2},  {24, 4, 2, 8, 2},  {32, 3, 2, 8, 1},
-                              {24, 4, 2, 8, 1},  {16, 4, 3, 8, 1},  {64, 3, 1, 8, 4},  {48, 4, 1, 8, 4}};
+        const Cand cands[] = {{0, 3, 1, 16, 2},  {64, 3, 1, 16, 2}, {48, 4, 1, 16, 2}, {96, 2, 1, 16, 2},
+                              {64, 3, 1, 16, 1}, {48, 4, 1, 16, 1}, {32, 3, 2, 8, 2},  {24, 4, 2, 8, 2},
+                              {32, 3, 2, 8, 1},  {24, 4, 2, 8, 1},  {16, 4, 3, 8, 1},  {64, 3, 1, 8, 4},
+                              {48, 4, 1, 8, 4}};
         best_ms = 1e30f;
         for (const Cand& c : cands) {
             Shape sh;
             sh.stages = c.stages;
             sh.ctas_per_sm = c.ctas;
-            sh.tile_rows = default_tile_rows(max_rb, c.stage_kb * 1024);
+            sh.tile_rows = c.stage_kb > 0 ? default_tile_rows(max_rb, c.stage_kb * 1024) : kMaxTileRows;
             sh.warps = c.warps;
             sh.group = c.group;
             float ms = 0;

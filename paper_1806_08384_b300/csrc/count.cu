@@ -60,6 +60,75 @@ __device__ __forceinline__ void produce_tile(const ScanArgs& a, int64_t g, uint3
     }
 }
 
+// Consumer warps: evaluate every tile's chunk groups for all programs of the
+// tile's table.  blob is the program blob (shared or global memory); the
+// kernel calls this with a pointer the compiler can trace to shared memory
+// when the blob is staged there, so instruction and pool reads are shared loads.
+template <int W, int G>
+__device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* blob, uint64_t* full, uint64_t* empty,
+                                              unsigned long long* cnt, uint8_t* stages,
+                                              const uint32_t (&s_off)[kMaxTables][kMaxSlots], uint32_t* s_fail,
+                                              uint32_t warp, uint32_t lane) {
+    const int64_t NB = gridDim.x;
+    const uint32_t S = a.stages;
+    const ProgDesc* pd = reinterpret_cast<const ProgDesc*>(blob);
+    const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
+    const uint8_t* pool = blob + a.pool_off;
+    uint32_t rot = 0;   // running chunk count: chunk c of a tile belongs to warp (rot + c) % W
+    uint32_t s = 0, parity = 0;
+    for (int64_t k = 0;; ++k) {
+        const int64_t g = blockIdx.x + k * NB;
+        if (g >= a.total_tiles) break;
+        const int ti = find_table(a, g);
+        const TableArg& T = a.t[ti];
+        const uint32_t valid = tile_valid(a, T, g);
+        const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
+        const uint32_t n_groups = (n_chunks + G - 1) / G;
+        const uint32_t first = (warp + W - rot % W) % W;
+        // every lane waits for the stage (a lane-0-only wait with the other
+        // lanes parked at a shuffle resumes much later); one verdict per warp
+        const bool okw = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(&full[s], parity));
+        if (!okw) {
+            if (lane == 0) {
+                atomicOr(a.err, 1u);
+                atomicOr(s_fail, 1u);
+                mbar_wait_bounded(&full[s], parity);   // a copy still in flight lands before we leave
+            }
+            break;
+        }
+        if (*reinterpret_cast<volatile uint32_t*>(s_fail)) break;
+        const uint32_t st_addr = smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes);
+        for (uint32_t grp = first; grp < n_groups; grp += W) {
+            uint32_t c0[G], vm[G];
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+                const uint32_t ch = grp * G + q;
+                // a missing chunk of the last group re-reads the group's first chunk, masked out
+                c0[q] = (ch < n_chunks ? ch : grp * G) * kChunkRows;
+                vm[q] = ch >= n_chunks ? 0u
+                        : (c0[q] + kChunkRows <= valid) ? 0xFFu
+                                                          : valid_mask(c0[q], lane, valid);
+            }
+            for (uint32_t p = T.prog_begin; p < T.prog_end; ++p) {
+                uint32_t m[G];
+                eval_program_g<G>(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane, m);
+                uint32_t pc = 0;
+#pragma unroll
+                for (int q = 0; q < G; ++q) pc += __popc(m[q] & vm[q]);
+                const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
+                if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
+            }
+        }
+        rot += n_groups;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            parity ^= 1u;
+        }
+    }
+}
+
 // W consumer warps (+1 producer warp); each consumer pass evaluates the
 // programs on G chunks at once (G independent mask stacks share one
 // instruction stream, which hides the interpreter's latency).
@@ -120,64 +189,11 @@ __global__ void __launch_bounds__((W + 1) * 32, (W == 8 && G < 4) ? 2 : 1) scan_
                 phase ^= 1u;
             }
         }
+    } else if (a.prog_in_smem) {
+        // the program's address space is visible to the compiler: shared loads
+        consume_tiles<W, G>(a, smem + a.prog_off, full, empty, cnt, stages, s_off, &s_fail, warp, lane);
     } else {
-        // ------------------------------- consumers ------------------------------
-        const ProgDesc* pd = reinterpret_cast<const ProgDesc*>(blob);
-        const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
-        const uint8_t* pool = blob + a.pool_off;
-        uint32_t rot = 0;   // running chunk count: chunk c of a tile belongs to warp (rot + c) % W
-        uint32_t s = 0, parity = 0;
-        for (int64_t k = 0;; ++k) {
-            const int64_t g = blockIdx.x + k * NB;
-            if (g >= a.total_tiles) break;
-            const int ti = find_table(a, g);
-            const TableArg& T = a.t[ti];
-            const uint32_t valid = tile_valid(a, T, g);
-            const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
-            const uint32_t n_groups = (n_chunks + G - 1) / G;
-            const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
-            // every lane waits for the stage (a lane-0-only wait with the other
-            // lanes parked at a shuffle resumes much later); one verdict per warp
-            const bool okw = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(&full[s], parity));
-            if (!okw) {
-                if (lane == 0) {
-                    atomicOr(a.err, 1u);
-                    atomicOr(&s_fail, 1u);
-                    mbar_wait_bounded(&full[s], parity);   // a copy still in flight lands before we leave
-                }
-                break;
-            }
-            if (*reinterpret_cast<volatile uint32_t*>(&s_fail)) break;
-            const uint32_t st_addr = smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes);
-            for (uint32_t grp = first; grp < n_groups; grp += W) {
-                uint32_t c0[G], vm[G];
-#pragma unroll
-                for (int q = 0; q < G; ++q) {
-                    const uint32_t ch = grp * G + q;
-                    // a missing chunk of the last group re-reads the group's first chunk, masked out
-                    c0[q] = (ch < n_chunks ? ch : grp * G) * kChunkRows;
-                    vm[q] = ch >= n_chunks ? 0u
-                            : (c0[q] + kChunkRows <= valid) ? 0xFFu
-                                                              : valid_mask(c0[q], lane, valid);
-                }
-                for (uint32_t p = T.prog_begin; p < T.prog_end; ++p) {
-                    uint32_t m[G];
-                    eval_program_g<G>(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane, m);
-                    uint32_t pc = 0;
-#pragma unroll
-                    for (int q = 0; q < G; ++q) pc += __popc(m[q] & vm[q]);
-                    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
-                    if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
-                }
-            }
-            rot += n_groups;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);
-            if (++s == S) {
-                s = 0;
-                parity ^= 1u;
-            }
-        }
+        consume_tiles<W, G>(a, a.blob, full, empty, cnt, stages, s_off, &s_fail, warp, lane);
     }
     __syncthreads();
     if (s_fail) return;   // counts are invalid; the error flag is set
@@ -231,6 +247,7 @@ cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStre
         scan_count_kernel<16, 2><<<grid, 17 * 32, smem, st>>>(a);
     else if (warps == 8 && group == 4)
         scan_count_kernel<8, 4><<<grid, 9 * 32, smem, st>>>(a);
+
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

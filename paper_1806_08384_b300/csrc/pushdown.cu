@@ -587,7 +587,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             bool fail = false;
             for (uint32_t u = 0; u < n_sub; ++u) {
                 const uint32_t n_groups = NCH / G;
-                const uint32_t first = (warp + W - (rot & (W - 1))) & (W - 1);   // W is a power of two
+                const uint32_t first = (warp + W - rot % W) % W;
                 if (!warp_wait(&sm.full[s], ph, lane)) {
                     if (lane == 0) fail_flag(a, &s_fail);
                     fail = true;
