@@ -249,15 +249,14 @@ constexpr uint32_t kMaskWords = 8;   // 256 rows of a chunk, 32 per word, in row
 
 // Shared-memory layout (bytes from the dynamic base) for S stages.
 struct PdLayout {
-    uint32_t tile, st_id, excl, nch, stot, cc, cp, mask, end;
+    uint32_t tile, st_id, excl, nch, stot, cp, mask, end;
     __host__ __device__ explicit PdLayout(uint32_t S) {
         tile = 16u * S + 3u * 8u * kPdBufs;           // after full[S], empty[S], evald/done/freeb[kPdBufs]
         st_id = tile + 8u * S;
         excl = st_id + 8u * kPdBufs;
         nch = excl + 8u * kPdBufs;
         stot = nch + 4u * kPdBufs;
-        cc = stot + 4u * kPdBufs;
-        cp = cc + 4u * kPdBufs * kPdpMaxChunks;
+        cp = stot + 4u * kPdBufs;
         mask = (cp + 4u * kPdBufs * kPdpMaxChunks + 15u) & ~15u;   // read as uint4
         end = mask + 4u * kPdBufs * kPdpMaxChunks * kMaskWords;
     }
@@ -271,7 +270,6 @@ struct PdSmem {
     unsigned long long* excl;            // [kPdBufs] exclusive prefix of each buffer's super-tile
     uint32_t* nch;                       // [kPdBufs] chunks of each buffer's super-tile that hold rows
     uint32_t* stot;                      // [kPdBufs] selected rows of each buffer's super-tile
-    uint32_t* cc;                        // [kPdBufs][kPdpMaxChunks] chunk counts (chunks in row order)
     uint32_t* cp;                        // [kPdBufs][kPdpMaxChunks] chunk prefixes
     uint32_t* mask;                      // [kPdBufs][kPdpMaxChunks][kMaskWords] row masks, row order
 };
@@ -289,7 +287,6 @@ __device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S) {
     m.excl = reinterpret_cast<unsigned long long*>(smem + L.excl);
     m.nch = reinterpret_cast<uint32_t*>(smem + L.nch);
     m.stot = reinterpret_cast<uint32_t*>(smem + L.stot);
-    m.cc = reinterpret_cast<uint32_t*>(smem + L.cc);
     m.cp = reinterpret_cast<uint32_t*>(smem + L.cp);
     m.mask = reinterpret_cast<uint32_t*>(smem + L.mask);
     return m;
@@ -531,12 +528,19 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             }
             const long long t = sm.st_id[b];
             if (t < 0) break;
-            // chunk prefix in row order (chunks past the super-tile's rows count 0) and the total
+            // chunk counts from the row words, their prefix in row order (chunks
+            // past the super-tile's rows count 0) and the total
             const uint32_t nch = sm.nch[b];
             uint32_t carry = 0;
             for (uint32_t c0 = 0; c0 < kPdpMaxChunks; c0 += 32) {
                 const uint32_t c = c0 + lane;
-                const uint32_t v = c < nch ? sm.cc[b * kPdpMaxChunks + c] : 0u;
+                uint32_t v = 0;
+                if (c < nch) {
+                    const uint4* w4 = reinterpret_cast<const uint4*>(sm.mask + (b * kPdpMaxChunks + c) * kMaskWords);
+                    const uint4 x = w4[0], y = w4[1];
+                    v = __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w) + __popc(y.x) + __popc(y.y) +
+                        __popc(y.z) + __popc(y.w);
+                }
                 uint32_t inc = v;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -618,8 +622,6 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
                         m[q] &= vm;
                         const uint32_t g = u * NCH + grp * G + q;   // chunk index in the super-tile (row order)
                         store_row_words(sm.mask + (b * kPdpMaxChunks + g) * kMaskWords, m[q], lane);
-                        const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, static_cast<uint32_t>(__popc(m[q])));
-                        if (lane == 0) sm.cc[b * kPdpMaxChunks + g] = c;
                     }
                 }
                 rot += n_groups;
