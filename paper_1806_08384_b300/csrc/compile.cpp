@@ -573,6 +573,27 @@ struct Compiler {
     }
 };
 
+// Peephole over the postfix program: an instruction that pushes a mask (a
+// leaf, CONST or LOAD) directly followed by AND / OR combines its mask into
+// the top of the stack instead (Instr.comb), which saves the binary
+// operator's dispatch and a push and pop of the mask stack.  The pushed mask
+// is always the operator's second operand, so the result is the same.
+static void combine_into_top(Program& p) {
+    std::vector<Instr> out;
+    out.reserve(p.instrs.size());
+    for (size_t i = 0; i < p.instrs.size(); ++i) {
+        Instr in = p.instrs[i];
+        const bool pushes = in.opc != OP_AND && in.opc != OP_OR && in.opc != OP_SAVE;
+        if (pushes && !out.empty() && i + 1 < p.instrs.size() &&
+            (p.instrs[i + 1].opc == OP_AND || p.instrs[i + 1].opc == OP_OR)) {
+            in.comb = p.instrs[i + 1].opc;
+            ++i;
+        }
+        out.push_back(in);
+    }
+    p.instrs.swap(out);
+}
+
 std::string describe(const Program& p) {
     std::ostringstream o;
     static const char* names[] = {"?", "AND", "OR", "CONST", "RANGE32", "RANGE64", "RANGEF",
@@ -652,6 +673,8 @@ std::string describe(const Program& p) {
         }
         default: break;
         }
+        if (in.comb == OP_AND) o << " +AND";
+        else if (in.comb == OP_OR) o << " +OR";
         o << "\n";
     }
     return o.str();
@@ -707,6 +730,7 @@ extern "C" sel_status sel_compile_predicate(const sel_table* schema, const sel_n
         prog.need = e.need;
         cp.count_leaves(e);
         cp.emit(e, prog, col_slot);
+        combine_into_top(prog);
         if (prog.leaves > SEL_MAX_LEAVES) fail(SEL_ERR_UNSUPPORTED, "more than SEL_MAX_LEAVES leaves");
         if (prog.need > kMaxDepth) fail(SEL_ERR_UNSUPPORTED, "tree needs a deeper evaluation stack than 8");
         if (prog.pool.size() > (1u << 20)) fail(SEL_ERR_UNSUPPORTED, "constant pool above 1 MiB");

@@ -37,7 +37,7 @@ struct Instr {
     uint8_t opc;
     uint8_t slot;     // column slot (leaves)
     uint8_t neg;      // 1: complement the leaf's row mask
-    uint8_t pad;
+    uint8_t comb;     // leaves, CONST, LOAD: 0 = push the mask; OP_AND / OP_OR = combine it into the top
     uint32_t off;     // byte offset into the pool (RANGE64, IN*, BITMAP)
     uint32_t a;       // see opcode
     uint32_t b;

@@ -337,19 +337,27 @@ __device__ __forceinline__ void eval_program_g(const Instr* __restrict__ prog, u
             const uint32_t sh = 8u * in.a;
 #pragma unroll
             for (int g = 0; g < G; ++g) memo[g] = (memo[g] & ~(0xFFu << sh)) | (top[g] << sh);
-        } else if (in.opc == OP_LOAD) {
-#pragma unroll
-            for (int g = 0; g < G; ++g) {
-                stk[g] = (stk[g] << 8) | top[g];
-                top[g] = (memo[g] >> (8u * in.a)) & 0xFFu;
-            }
         } else {
+            // a leaf, CONST or LOAD: push its mask, or combine it into the top
             uint32_t m[G];
-            eval_leaf_g<G>(in, stage_base + slot_off[in.slot], c0, lane, pool, m);
+            if (in.opc == OP_LOAD) {
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                stk[g] = (stk[g] << 8) | top[g];
-                top[g] = m[g];
+                for (int g = 0; g < G; ++g) m[g] = (memo[g] >> (8u * in.a)) & 0xFFu;
+            } else {
+                eval_leaf_g<G>(in, stage_base + slot_off[in.slot], c0, lane, pool, m);
+            }
+            if (in.comb == OP_AND) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) top[g] &= m[g];
+            } else if (in.comb == OP_OR) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) top[g] |= m[g];
+            } else {
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    stk[g] = (stk[g] << 8) | top[g];
+                    top[g] = m[g];
+                }
             }
         }
     }

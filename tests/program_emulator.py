@@ -24,6 +24,8 @@ def parse(text: str):
         parts = ln.split()
         op = parts[0]
         kv = dict(p.split("=", 1) for p in parts[1:] if "=" in p)
+        # "+AND" / "+OR": the mask is combined into the top instead of pushed
+        kv["comb"] = "AND" if "+AND" in parts[1:] else "OR" if "+OR" in parts[1:] else ""
         prog.append((op, kv))
     return slots, prog
 
@@ -91,15 +93,20 @@ def evaluate(text: str, arrays: List[np.ndarray], n_rows: int) -> np.ndarray:
         if op == "SAVE":
             memo[kv["m"]] = stack[-1]
             continue
-        if op == "LOAD":
-            stack.append(memo[kv["m"]])
-            continue
         if op in ("AND", "OR"):
             b, a = stack.pop(), stack.pop()
             stack.append(a & b if op == "AND" else a | b)
+            continue
+        if op == "LOAD":
+            v = memo[kv["m"]]
         else:
             col = arrays[slots[int(kv["slot"])][0]] if op != "CONST" else np.zeros(n_rows)
-            stack.append(_leaf_mask(op, kv, col))
+            v = _leaf_mask(op, kv, col)
+        if kv["comb"]:
+            a = stack.pop()
+            stack.append(a & v if kv["comb"] == "AND" else a | v)
+        else:
+            stack.append(v)
     assert len(stack) == 1
     return stack[0]
 
