@@ -82,10 +82,6 @@ __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* 
         const int ti = find_table(a, g);
         const TableArg& T = a.t[ti];
         const uint32_t valid = tile_valid(a, T, g);
-        // read the table's program range once per tile (a parameter load with a
-        // run-time index is a long-latency load)
-        const uint32_t p_begin = T.prog_begin, p_end = T.prog_end;
-        const uint32_t* slot_off = s_off[ti];
         const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
         const uint32_t n_groups = (n_chunks + G - 1) / G;
         const uint32_t first = (warp + W - rot % W) % W;
@@ -113,9 +109,9 @@ __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* 
                         : (c0[q] + kChunkRows <= valid) ? 0xFFu
                                                           : valid_mask(c0[q], lane, valid);
             }
-            for (uint32_t p = p_begin; p < p_end; ++p) {
+            for (uint32_t p = T.prog_begin; p < T.prog_end; ++p) {
                 uint32_t m[G];
-                eval_program_g<G>(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, slot_off, c0, lane, m);
+                eval_program_g<G>(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane, m);
                 uint32_t pc = 0;
 #pragma unroll
                 for (int q = 0; q < G; ++q) pc += __popc(m[q] & vm[q]);
