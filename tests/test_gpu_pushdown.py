@@ -54,7 +54,10 @@ def proj_cfg2(t):
     return [t.index(c) for c in dg.CONFIG2_PROJECTION]
 
 
-@pytest.mark.parametrize("tile_rows", [0, 256, 1024, 1280, 2048, 4096, 8192])
+# 1536, 2560 and 3584 rows are sub-tiles of the persistent kernel whose
+# super-tiles (15360, 15360, 14336 rows) are not powers of two; 256 and 1280
+# are not whole 2-chunk groups and run on the one-CTA-per-tile kernel.
+@pytest.mark.parametrize("tile_rows", [0, 256, 1024, 1280, 1536, 2048, 2560, 3584, 4096, 8192])
 def test_config2_selectivities(ctx, medium, tile_rows):
     t, ot, T = medium
     ctx.set_scan_shape(tile_rows, 0, 0)
@@ -71,6 +74,10 @@ def test_persistent_variants(ctx, dev, medium, variant):
     ctx.set_scan_variant(*variant)
     for s in (1e-3, 0.1):
         check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=21), proj_cfg2(t))
+    if variant[1] == 1:   # 3-chunk sub-tiles: 21 of them make a 16128-row super-tile
+        ctx.set_scan_shape(768, 0, 0)
+        check_pushdown(ctx, T, ot, dg.config2_predicate(0.1, seed=22), proj_cfg2(t))
+        ctx.set_scan_shape(0, 0, 0)
     for n in (32768, 65537):
         tt = dg.tiny_table(n, seed=n)
         ott = oracle.OTable.from_table(tt)
@@ -114,6 +121,19 @@ def test_max_rows_contract(ctx, medium):
     # the written prefix of a rejected push-down is still the start of the true result
     want = oracle.select(ot, tree, threads=THREADS)
     assert np.array_equal(ids[:m].cpu().numpy(), want[:m])
+    # a limit that cuts the result inside a super-tile: the first max_rows rows
+    # in row order are written, nothing after them
+    m = n // 3
+    ids.fill_(-5)
+    for o in outs:
+        o.fill_(7)
+    st, cnt, _, _ = ctx.pushdown(p, T, proj, m, out_cols=outs, out_rowids=ids)
+    assert st == sel.SEL_ERR_TOO_LARGE and cnt == n
+    assert np.array_equal(ids[:m].cpu().numpy(), want[:m])
+    assert bool((ids[m:] == -5).all())
+    for c, o in zip(proj, outs):
+        assert np.array_equal(o[:m].cpu().numpy(), ot.arrays[c][want[:m]])
+        assert bool((o[m:] == 7).all())
 
 
 def test_unaligned_columns(ctx, medium):
