@@ -85,6 +85,26 @@ def test_leaf_lowering(tree, expect):
     assert expect in _compile(t, tree).describe()
 
 
+def test_leaf_before_and_or_combines_into_top():
+    """A leaf (or LOAD) directly followed by AND/OR folds into the top of the
+    mask stack: the operator's instruction disappears, the program's meaning
+    does not (the emulator models the folded form)."""
+    t = dg.tiny_table(64, seed=9)
+    chain = dg.p_and(dg.p_cmp(0, ">", 1), dg.p_cmp(3, ">", dg.DATE_BASE), dg.p_cmp(1, "<", 5))
+    txt = _compile(t, chain).describe()
+    body = txt.strip().splitlines()[3:]
+    assert len(body) == 3 and body[0].split()[0] != "AND"
+    assert [ln.split()[-1] for ln in body[1:]] == ["+AND", "+AND"]
+    dnf = dg.p_or(dg.p_and(dg.p_cmp(0, ">", 1), dg.p_cmp(1, "<", 5)), dg.p_cmp(2, "<", 0.5))
+    txt = _compile(t, dnf).describe()
+    assert "+AND" in txt and "+OR" in txt and not any(ln.strip() == "AND" for ln in txt.splitlines())
+    ot = oracle.OTable.from_table(t)
+    arrays = [c.data.numpy() for c in t.columns]
+    for tree in (chain, dnf):
+        got = emu.evaluate(_compile(t, tree).describe(), arrays, t.n_rows)
+        assert int(got.sum()) == oracle.count(ot, tree)
+
+
 def test_unsorted_dictionary_prefix_is_a_bitmap():
     d = [b"ab", b"c", b"ax", b"d", b"aa"]
     col = dg.Column(dg.ColumnSpec("s", "dict", "zipf", n_values=5), torch.zeros(4, dtype=torch.int32), d)
