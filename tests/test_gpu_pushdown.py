@@ -145,12 +145,13 @@ def test_unaligned_columns(ctx, medium):
         check_pushdown(ctx, T, sub, dg.config2_predicate(s, seed=13), proj_cfg2(t))
 
 
-@pytest.mark.parametrize("tile_rows", [1024, 2048, 4096, 1280])
+@pytest.mark.parametrize("tile_rows", [1024, 2048, 3584, 4096, 1280])
 def test_lookback_wait_times_out_and_context_recovers(ctx, dev, tile_rows):
     """A tile that never publishes makes its successors' bounded waits run out:
     the call returns SEL_ERR_TIMEOUT, and the context works afterwards (the
-    persistent kernel's variants, whose look-back unit is a 16384-row
-    super-tile, and the one-CTA-per-tile kernel)."""
+    persistent kernel, whose look-back unit is a super-tile of up to 16384
+    rows -- 14336 for 3584-row sub-tiles --, and the one-CTA-per-tile kernel
+    for 1280-row tiles)."""
     t = dg.tiny_table(4 * 32768 + 1000, seed=3)
     ot = oracle.OTable.from_table(t)
     T = sel.Table(t.to(dev).columns)
