@@ -474,6 +474,130 @@ def star_batch(sel, peak: float, device, reps=5):
     return res
 
 
+def config1_latency(sel, device, reps=200):
+    """Config 1: one exact count over a 1M-row table (12 B/row of referenced
+    columns, 12 MB: it fits in L2), so the time is launch latency and is
+    reported per estimate.  Plain launch (sel_count_async) and graph replay (a
+    one-probe batch plan), each with L2 warm (back-to-back launches) and L2
+    flushed (a 512 MB buffer overwritten before each timed launch), and the
+    synchronous host call an optimiser waiting for the answer sees."""
+    tab = dg.config1_table(device=device)
+    T = sel.Table(tab.columns)
+    p = sel.Predicate(T, dg.config1_predicate(0))
+    ctx = sel.Context()
+    out = torch.zeros(1, dtype=torch.int64, device=device)
+    plan = sel.BatchPlan(ctx, [p], [T], autotune=False)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=device)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {}
+    for name, fn in (("plain", lambda: ctx.count_async(p, T, out)), ("graph", lambda: plan.run(out))):
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        res[name + "_l2_warm_us"] = round(a.elapsed_time(b) * 1e3 / reps, 2)
+        pairs = []
+        for i in range(reps // 4):
+            flush.fill_(i & 0xFF)
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            pairs.append((a, b))
+        torch.cuda.synchronize()
+        res[name + "_l2_flushed_us"] = round(statistics.median(x.elapsed_time(y) for x, y in pairs) * 1e3, 2)
+    n = ctx.count(p, T)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        n = ctx.count(p, T)
+    res["sync_call_us"] = round((time.perf_counter() - t0) * 1e6 / reps, 2)
+    assert int(out.item()) == n
+    cols = dg.tree_columns(dg.config1_predicate(0))
+    nbytes = sum(tab.columns[c].spec.width for c in set(cols)) * tab.n_rows
+    res.update({"count": n, "bytes": nbytes,
+                "workload": "config1: 1M rows x 4 cols (i32 U, i32 Zipf1.2/1000, f32 N(0,1), date); "
+                            "c0 BETWEEN a AND b AND c1 IN {5} AND c2 < t",
+                "note": "device time per launch from CUDA events; flushed = 512 MB written before each launch"})
+    del plan, flush
+    torch.cuda.empty_cache()
+    return res
+
+
+def config5_batch(sel, peak, device, reps=3):
+    """Config 5: 256 probes (s log-spaced in [1e-6, 0.9], OR of 1-3 ANDs) over
+    a 1.2B-row table of 24 B/row (28.8 GB): the exact batched count as one
+    autotuned plan (ms per estimate), single-probe counts, and the push-down of
+    3 columns for the probes at s = 1e-4 and 1e-2."""
+    tab = dg.config5_table(device=device)
+    T = sel.Table(tab.columns)
+    trees = dg.config5_predicates()
+    preds = [sel.Predicate(T, tr) for tr in trees]
+    ctx = sel.Context()
+    t0 = time.perf_counter()
+    plan = sel.BatchPlan(ctx, preds, [T] * len(preds))
+    plan_s = time.perf_counter() - t0
+    out = torch.zeros(len(preds), dtype=torch.int64, device=device)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, r):
+        fn()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(r):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / r
+    n = tab.n_rows
+    width = lambda cols: sum(tab.columns[c].spec.width for c in set(cols))
+    union = sorted({c for tr in trees for c in dg.tree_columns(tr)})
+    batch_ms = timed(lambda: plan.run(out), reps)
+    counts = out.cpu().tolist()
+    res = {"batched_ms": round(batch_ms, 3), "ms_per_estimate_batched": round(batch_ms / len(preds), 4),
+           "shared_pass_bytes": width(union) * n,
+           "batched_gbs_shared_pass": round(width(union) * n / batch_ms / 1e6, 1),
+           "rows_per_s_per_probe": round(n * len(preds) / batch_ms * 1e3, 1),
+           "autotune_pick": plan.info(), "plan_create_s": round(plan_s, 2)}
+    targets = np.logspace(-6, np.log10(0.9), len(trees))
+    singles = []
+    for i in (0, len(trees) // 2, len(trees) - 1):
+        one = torch.zeros(1, dtype=torch.int64, device=device)
+        ms = timed(lambda: ctx.count_async(preds[i], T, one), reps)
+        assert int(one.item()) == counts[i]
+        b = width(dg.tree_columns(trees[i])) * n
+        singles.append({"target_s": float(f"{targets[i]:.3g}"), "count": counts[i], "ms": round(ms, 3),
+                        "gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4)})
+    res["count_single"] = singles
+    proj = [tab.index(c) for c in dg.CONFIG5_PROJECTION]
+    pds = []
+    for s in (1e-4, 1e-2):
+        i = int(np.argmin(np.abs(np.log(targets) - np.log(s))))
+        mr = max(1, counts[i])
+        cols_out = [torch.empty(mr, dtype=tab.columns[c].data.dtype, device=device) for c in proj]
+        ids = torch.empty(mr, dtype=torch.int64, device=device)
+        cnt = torch.zeros(1, dtype=torch.int64, device=device)
+        ms = timed(lambda: ctx.pushdown_async(preds[i], T, proj, mr, cols_out, ids, cnt), reps)
+        assert int(cnt.item()) == counts[i]
+        pc = set(dg.tree_columns(trees[i]))
+        b = width(pc) * n + counts[i] * (sum(tab.columns[c].spec.width for c in proj if c not in pc)
+                                         + sum(tab.columns[c].spec.width for c in proj) + 8)
+        pds.append({"target_s": s, "count": counts[i], "ms": round(ms, 3), "gbs": round(b / ms / 1e6, 1),
+                    "frac": round(b / ms / 1e6 / peak, 4)})
+        del cols_out, ids
+    res["pushdown"] = pds
+    res["workload"] = ("config5: 1.2B rows x 6 cols (i32 U/Zipf1.1/U, f32 N/U, dict-1000 Zipf), 24 B/row; "
+                       "256 probes s log-spaced in [1e-6, 0.9]; push-down of u0, z1, g1")
+    del plan, preds, T, tab
+    torch.cuda.empty_cache()
+    return res
+
+
 def distinct_and_join(step: OurStep, reps=3):
     """f3: V(R, k2) and V(sigma_P(R), k2) of the int64 key (exact, GPU hash set)
     and the join-size estimate of sigma_P(R) with R on that key."""
@@ -600,6 +724,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-star", action="store_true", help="skip the star-schema batch measurement")
+    ap.add_argument("--no-cfg1", action="store_true", help="skip the 1M-row latency measurement")
+    ap.add_argument("--no-cfg5", action="store_true", help="skip the 1.2B-row, 256-probe measurement")
     ap.add_argument("--clock-interval-ms", type=float, default=50.0, help="NVML clock sampling interval")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -700,6 +826,10 @@ def main():
         out["distinct_and_join"] = distinct_and_join(step)
         if not args.no_star:
             out["star_batch"] = star_batch(sel, peak, dev)
+        if not args.no_cfg1:
+            out["config1_latency"] = config1_latency(sel, dev)
+        if not args.no_cfg5:
+            out["config5_batch"] = config5_batch(sel, peak, dev)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(step, args, step_bytes)
     if rank == 0 and not args.no_cpu:

@@ -61,6 +61,7 @@ struct DevBuf {
 struct Shape {
     int tile_rows = 0, stages = 0, ctas_per_sm = 0;
     int warps = 0, group = 0;   // count-scan variant: consumer warps, chunks per instruction pass
+    bool auto_tile = false;     // tile_rows is the library's choice: run_scan may shrink it for small tables
 };
 
 }  // namespace sel
@@ -177,38 +178,57 @@ static int default_tile_rows(uint32_t row_bytes, int stage_target) {
     return std::max(kChunkRows, std::min(kMaxTileRows, r));
 }
 
+// The launch shape actually used for a scan: the largest tile (multiple of
+// 256 rows, at most the requested one) whose stages fit in shared memory next
+// to the counters and the programs, and, when the tile is the library's
+// choice, small enough for about 4 tiles per CTA on small tables.
+static sel_status resolve_shape(sel_ctx* ctx, uint32_t blob_bytes, uint32_t n_progs,
+                                const std::vector<TableArg>& tables, const Shape& sh_in, Shape* out) {
+    Shape sh = sh_in;
+    uint32_t max_rb = 0;
+    for (auto& t : tables) max_rb = std::max(max_rb, t.row_bytes);
+    ScanArgs probe;
+    std::memset(&probe, 0, sizeof(probe));
+    probe.n_progs = n_progs;
+    probe.stages = (uint32_t)sh.stages;
+    probe.blob_bytes = blob_bytes;
+    probe.prog_in_smem = blob_bytes <= 48u * 1024u ? 1u : 0u;
+    const size_t fixed = scan_layout(probe);
+    if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem_scan || sh.stages < 1) {
+        set_error("scan: %u programs and %d stages do not fit in shared memory", n_progs, sh.stages);
+        return SEL_ERR_UNSUPPORTED;
+    }
+    if (max_rb > 0) {
+        const size_t per_stage = ((size_t)ctx->max_smem_scan - fixed) / (size_t)sh.stages;
+        const int fit = (int)(per_stage / max_rb) / kChunkRows * kChunkRows;
+        if (fit < kChunkRows) {
+            set_error("scan: %d stages of 256 rows x %u bytes do not fit in shared memory", sh.stages, max_rb);
+            return SEL_ERR_UNSUPPORTED;
+        }
+        sh.tile_rows = std::min(sh.tile_rows, fit);
+    }
+    if (sh.auto_tile) {
+        int64_t rows = 0;
+        for (auto& t : tables) rows += t.n_rows;
+        const int64_t want = 4ll * ctx->n_sm * std::max(1, sh.ctas_per_sm);
+        const int64_t cap = rows / want / kChunkRows * kChunkRows;
+        if (cap < sh.tile_rows) sh.tile_rows = (int)std::max<int64_t>(kChunkRows, cap);
+        sh.auto_tile = false;
+    }
+    *out = sh;
+    return SEL_OK;
+}
+
 // Fills shape-dependent fields and launches (several launches when the
 // tables do not fit in one).
 static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_bytes, uint32_t instr_off,
                            uint32_t pool_off, uint32_t n_progs, std::vector<TableArg> tables,
                            unsigned long long* d_counts, const Shape& sh_in, int* n_launches) {
     int launches = 0;
-    // largest tile (multiple of 256 rows, at most the requested one) whose
-    // stages fit in shared memory next to the counters and the programs
-    Shape sh = sh_in;
+    Shape sh;
     {
-        uint32_t max_rb = 0;
-        for (auto& t : tables) max_rb = std::max(max_rb, t.row_bytes);
-        ScanArgs probe;
-        std::memset(&probe, 0, sizeof(probe));
-        probe.n_progs = n_progs;
-        probe.stages = (uint32_t)sh.stages;
-        probe.blob_bytes = blob_bytes;
-        probe.prog_in_smem = blob_bytes <= 48u * 1024u ? 1u : 0u;
-        const size_t fixed = scan_layout(probe);
-        if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem_scan || sh.stages < 1) {
-            set_error("scan: %u programs and %d stages do not fit in shared memory", n_progs, sh.stages);
-            return SEL_ERR_UNSUPPORTED;
-        }
-        if (max_rb > 0) {
-            const size_t per_stage = ((size_t)ctx->max_smem_scan - fixed) / (size_t)sh.stages;
-            const int fit = (int)(per_stage / max_rb) / kChunkRows * kChunkRows;
-            if (fit < kChunkRows) {
-                set_error("scan: %d stages of 256 rows x %u bytes do not fit in shared memory", sh.stages, max_rb);
-                return SEL_ERR_UNSUPPORTED;
-            }
-            sh.tile_rows = std::min(sh.tile_rows, fit);
-        }
+        const sel_status rs = resolve_shape(ctx, blob_bytes, n_progs, tables, sh_in, &sh);
+        if (rs != SEL_OK) return rs;
     }
     for (size_t t0 = 0; t0 < tables.size(); t0 += kMaxTables) {
         ScanArgs a;
@@ -268,6 +288,7 @@ static Shape single_shape(sel_ctx* ctx, uint32_t row_bytes) {
     s.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 3;
     s.ctas_per_sm = ctx->shape.ctas_per_sm > 0 ? ctx->shape.ctas_per_sm : 1;
     s.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : kMaxTileRows;
+    s.auto_tile = ctx->shape.tile_rows <= 0;
     s.warps = ctx->shape.warps > 0 ? ctx->shape.warps : kScanDefaultWarps;
     s.group = ctx->shape.group > 0 ? ctx->shape.group : kScanDefaultGroup;
     return s;
@@ -956,6 +977,7 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
             sh.stages = c.stages;
             sh.ctas_per_sm = c.ctas;
             sh.tile_rows = c.stage_kb > 0 ? default_tile_rows(max_rb, c.stage_kb * 1024) : kMaxTileRows;
+            sh.auto_tile = true;
             sh.warps = c.warps;
             sh.group = c.group;
             float ms = 0;
@@ -968,7 +990,10 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
             }
         }
     }
-    p->shape = best;
+    {   // the shape the plan's launches use (reported by sel_batch_plan_info)
+        const sel_status rs = resolve_shape(ctx, p->blob_bytes, p->n_progs, p->tables, best, &p->shape);
+        if (rs != SEL_OK) return rs;
+    }
     p->ms = best_ms;
     sel_status s = plan_capture(p.get());
     if (s != SEL_OK) return s;
