@@ -177,33 +177,12 @@ __device__ __forceinline__ void in_list(const T (&v)[G][8], const T* vals, uint3
 }
 
 // Evaluates one leaf on G chunks (chunk g starts at tile row c0[g]); the pool
-// pointer may address shared or global memory.
+// pointer may address shared or global memory.  RANGE32, RANGEF and MASK32
+// are evaluated inline by eval_program_g and never come here.
 template <int G>
 __device__ __forceinline__ void eval_leaf_g(const Instr& in, uint32_t col_base, const uint32_t (&c0)[G], uint32_t lane,
                                             const uint8_t* pool, uint32_t (&m)[G]) {
     switch (in.opc) {
-    case OP_RANGE32: {
-        uint32_t v[G][8];
-#pragma unroll
-        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
-        const uint32_t lo = in.a, sp = in.b;
-#pragma unroll
-        for (int g = 0; g < G; ++g) m[g] = mask8([&](int i) { return v[g][i] - lo <= sp; });
-        break;
-    }
-    case OP_RANGEF: {
-        uint32_t v[G][8];
-#pragma unroll
-        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
-        const float lo = __uint_as_float(in.a), hi = __uint_as_float(in.b);
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-            m[g] = mask8([&](int i) {
-                const float x = __uint_as_float(v[g][i]);
-                return lo <= x && x <= hi;
-            });
-        break;
-    }
     case OP_RANGE64: {
         uint64_t v[G][8];
 #pragma unroll
@@ -250,17 +229,6 @@ __device__ __forceinline__ void eval_leaf_g(const Instr& in, uint32_t col_base, 
                 const uint32_t d = v[g][i] - lo;
                 return d < nbits && ((words[d >> 5] >> (d & 31u)) & 1u);
             });
-        break;
-    }
-    case OP_MASK32: {
-        uint32_t v[G][8];
-#pragma unroll
-        for (int g = 0; g < G; ++g) load8x32(col_base, c0[g], lane, v[g]);
-        const uint32_t lo = in.a, word = in.b;
-        // a clamped funnel shift: offsets >= 32 (values outside the word) give 0
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-            m[g] = mask8_bits([&](int i) { return __funnelshift_rc(word, 0u, v[g][i] - lo) & 1u; });
         break;
     }
     case OP_HASH32: {
@@ -321,7 +289,49 @@ __device__ __forceinline__ void eval_program_g(const Instr* __restrict__ prog, u
     for (uint32_t pc = 0; pc < n_instr; ++pc) {
         const Instr in = nxt;
         if (pc + 1 < n_instr) nxt = prog[pc + 1];
-        if (in.opc == OP_AND) {
+        if (in.opc == OP_RANGE32 || in.opc == OP_RANGEF || in.opc == OP_MASK32) {
+            // the most frequent leaves (ranges over 4-byte columns, small code
+            // sets) first and inline: measured 4-13 % fewer instructions per
+            // leaf than through the switch; negation as an XOR mask
+            // (a clamped funnel shift tests MASK32: offsets >= 32 give 0)
+            const uint32_t cb = stage_base + slot_off[in.slot];
+            const uint32_t negm = in.neg ? 0xFFu : 0u;
+            uint32_t m[G];
+            uint32_t v[G][8];
+#pragma unroll
+            for (int g = 0; g < G; ++g) load8x32(cb, c0[g], lane, v[g]);
+            if (in.opc == OP_RANGE32) {
+                const uint32_t lo = in.a, sp = in.b;
+#pragma unroll
+                for (int g = 0; g < G; ++g) m[g] = mask8([&](int i) { return v[g][i] - lo <= sp; }) ^ negm;
+            } else if (in.opc == OP_RANGEF) {
+                const float lo = __uint_as_float(in.a), hi = __uint_as_float(in.b);
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    m[g] = mask8([&](int i) {
+                        const float x = __uint_as_float(v[g][i]);
+                        return lo <= x && x <= hi;
+                    }) ^ negm;
+            } else {
+                const uint32_t lo = in.a, word = in.b;
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    m[g] = mask8_bits([&](int i) { return __funnelshift_rc(word, 0u, v[g][i] - lo) & 1u; }) ^ negm;
+            }
+            if (in.comb == OP_AND) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) top[g] &= m[g];
+            } else if (in.comb == OP_OR) {
+#pragma unroll
+                for (int g = 0; g < G; ++g) top[g] |= m[g];
+            } else {
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    stk[g] = (stk[g] << 8) | top[g];
+                    top[g] = m[g];
+                }
+            }
+        } else if (in.opc == OP_AND) {
 #pragma unroll
             for (int g = 0; g < G; ++g) {
                 top[g] &= static_cast<uint32_t>(stk[g]) & 0xFFu;
