@@ -383,6 +383,15 @@ extern "C" uint64_t sel_ctx_launch_count(const sel_ctx* c) { return c ? c->launc
 
 namespace sel {
 cudaStream_t ctx_stream(sel_ctx* c) { return c->stream; }
+uint64_t& thread_launches() {
+    thread_local uint64_t n = 0;
+    return n;
+}
+int& thread_tally_depth() {
+    thread_local int d = 0;
+    return d;
+}
+void ctx_add_launches(sel_ctx* c, uint64_t n) { c->launches += n; }
 }
 
 extern "C" sel_status sel_ctx_debug_pushdown_fault(sel_ctx* c, int64_t skip_tile, uint64_t wait_ns) {

@@ -81,4 +81,24 @@ sel_status pred_upload(const sel_pred* p);
 namespace sel {
 // The CUDA stream a context is bound to.
 cudaStream_t ctx_stream(sel_ctx* ctx);
+
+// Kernels launched by this host thread from the estimator's code.  The
+// estimator's entry points add what they launched to their context's launch
+// count (sel_ctx_launch_count) through a LaunchTally; when one entry point
+// calls another, only the outermost tally adds.
+uint64_t& thread_launches();
+int& thread_tally_depth();
+void ctx_add_launches(sel_ctx* ctx, uint64_t n);
+struct LaunchTally {
+    sel_ctx* ctx;
+    uint64_t start;
+    bool outer;
+    explicit LaunchTally(sel_ctx* c) : ctx(c), start(thread_launches()), outer(thread_tally_depth()++ == 0) {}
+    ~LaunchTally() {
+        --thread_tally_depth();
+        if (outer && ctx) ctx_add_launches(ctx, thread_launches() - start);
+    }
+    LaunchTally(const LaunchTally&) = delete;
+    LaunchTally& operator=(const LaunchTally&) = delete;
+};
 }

@@ -435,6 +435,7 @@ GemmArgs gemm(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, lon
 }
 
 sel_status run_gemm(const GemmArgs& g, int splits, cudaStream_t st) {
+    ++thread_launches();
     return cuda_ok(launch_gemm(g, splits, st), "tensor-core GEMM launch");
 }
 
@@ -465,6 +466,7 @@ sel_status forward(sel_mlp* m, const __nv_bfloat16* x, int n, bool training, cud
     g.ldo = kHid;
     MLP_TRY(run_gemm(g, 1, st));
     if (!training) {
+        ++thread_launches();
         head_kernel<<<(n + 127) / 128, 128, 0, st>>>(m->a3, m->w4b, m->p + oB4, n, m->out, nullptr, n, nullptr,
                                                       nullptr, nullptr, nullptr, nullptr);
         MLP_TRY(cuda_ok(cudaGetLastError(), "head launch"));
@@ -476,10 +478,13 @@ sel_status forward(sel_mlp* m, const __nv_bfloat16* x, int n, bool training, cud
 sel_status backward(sel_mlp* m, const __nv_bfloat16* x, const float* y, int n, cudaStream_t st) {
     MLP_TRY(forward(m, x, n, true, st));
     dim3 tb(32, 8), tg((kFeat + 31) / 32, (n + 31) / 32);
+    ++thread_launches();
     transpose_bf16<<<tg, tb, 0, st>>>(x, n, kFeat, m->xt);
+    ++thread_launches();
     head_kernel<<<(n + 127) / 128, 128, 0, st>>>(m->a3, m->w4b, m->p + oB4, n, m->out, y, n, m->dz3, m->g + oB3,
                                                   m->g + oW4, m->g + oB4, m->loss);
     MLP_TRY(cuda_ok(cudaGetLastError(), "head launch"));
+    ++thread_launches();
     transpose_bf16<<<dim3((kHid + 31) / 32, (n + 31) / 32), dim3(32, 8), 0, st>>>(m->dz3, n, kHid, m->dz3t);
     const int splits = std::max(1, std::min(32, n / 256));
     // dW3 = dZ3^T A2 ; dA2 = dZ3 W3 -> dZ2 (ReLU gradient), db2
@@ -525,6 +530,7 @@ sel_status adam(sel_mlp* m, const sel_train_cfg* cfg, bool update, cudaStream_t 
         c1 = (float)(1.0 / (1.0 - std::pow((double)cfg->beta1, (double)m->step)));
         c2 = (float)(1.0 / (1.0 - std::pow((double)cfg->beta2, (double)m->step)));
     }
+    ++thread_launches();
     adam_kernel<<<(unsigned)((kParams + 255) / 256), 256, 0, st>>>(
         m->p, m->g, m->mm, m->vv, cfg ? cfg->lr : 0.f, cfg ? cfg->beta1 : 0.f, cfg ? cfg->beta2 : 0.f,
         cfg ? cfg->eps : 1.f, c1, c2, m->w1b, m->w2b, m->w3b, m->w4b, m->w2t, m->w3t, update ? 1 : 0);
@@ -700,6 +706,7 @@ sel_status featurize(sel_mlp* m, cudaStream_t st, const sel_pred* const* preds, 
         MLP_TRY(cuda_ok(cudaMemcpyAsync(dev_ok, m->d_stage + ok_off, (size_t)n, cudaMemcpyDeviceToDevice, st),
                         "featurize"));
     const int64_t threads = (int64_t)n * kSlots * 32;   // one warp per (predicate, slot)
+    ++thread_launches();
     featurize_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
         reinterpret_cast<const FeatClause*>(m->d_stage), reinterpret_cast<const uint64_t*>(m->d_stage + keys_off),
         m->cdf, m->m, n, feat);
@@ -733,6 +740,7 @@ sel_status alloc_model(sel_mlp* m) {
 
 extern "C" sel_status sel_mlp_create(sel_ctx* ctx, const sel_table* table, int32_t sample_rows, uint64_t seed,
                                      sel_mlp** out) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !table || !out || table->n_cols <= 0 || !table->cols || table->n_rows <= 0 || sample_rows < 2 ||
         sample_rows > 8192 || (sample_rows & (sample_rows - 1))) {
         set_error("sel_mlp_create: bad arguments (sample_rows: a power of two in [2, 8192]; a non-empty table)");
@@ -784,6 +792,7 @@ extern "C" sel_status sel_mlp_create(sel_ctx* ctx, const sel_table* table, int32
     const size_t smem = (size_t)sample_rows * 8;
     MLP_TRY(cuda_ok(cudaFuncSetAttribute(cdf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                     "sel_mlp_create"));
+    ++thread_launches();
     cdf_kernel<<<m->n_cols, 1024, smem, st>>>(static_cast<const uint8_t* const*>(dptr.p),
                                              static_cast<const int32_t*>(dty.p), table->n_rows, sample_rows, seed,
                                              m->cdf);
@@ -797,6 +806,7 @@ extern "C" void sel_mlp_free(sel_mlp* m) { delete m; }
 
 extern "C" sel_status sel_mlp_featurize(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds, int32_t n,
                                         void* dev_features, uint8_t* dev_ok) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !m || !preds || n <= 0 || !dev_features) {
         set_error("sel_mlp_featurize: bad arguments");
         return SEL_ERR_INVALID_ARG;
@@ -805,6 +815,7 @@ extern "C" sel_status sel_mlp_featurize(sel_ctx* ctx, sel_mlp* m, const sel_pred
 }
 
 extern "C" sel_status sel_mlp_forward(sel_ctx* ctx, sel_mlp* m, const void* dev_features, int32_t n, float* dev_out) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !m || !dev_features || n <= 0 || !dev_out || reinterpret_cast<uintptr_t>(dev_features) % 16) {
         set_error("sel_mlp_forward: bad arguments");
         return SEL_ERR_INVALID_ARG;
@@ -825,6 +836,7 @@ static sel_status check_cfg(const sel_train_cfg* cfg) {
 
 extern "C" sel_status sel_mlp_train_step(sel_ctx* ctx, sel_mlp* m, const void* dev_features, const float* dev_y,
                                          int32_t n, const sel_train_cfg* cfg, float* loss_out) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !m || !dev_features || !dev_y || n <= 0 || n % 8 || reinterpret_cast<uintptr_t>(dev_features) % 16) {
         set_error("sel_mlp_train_step: bad arguments (batch rows a positive multiple of 8)");
         return SEL_ERR_INVALID_ARG;
@@ -850,6 +862,7 @@ extern "C" sel_status sel_mlp_train_step(sel_ctx* ctx, sel_mlp* m, const void* d
 extern "C" sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds,
                                     const uint64_t* exact_counts, int64_t n, const sel_train_cfg* cfg,
                                     float* final_loss) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !m || !preds || !exact_counts || n <= 0 || n > (1ll << 30)) {
         set_error("sel_mlp_train: bad arguments");
         return SEL_ERR_INVALID_ARG;
@@ -907,6 +920,7 @@ extern "C" sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* co
                         "sel_mlp_train"));
         double sum = 0.0;
         for (int64_t s = 0; s < steps; ++s) {
+            ++thread_launches();
             gather_kernel<<<cfg->batch, 32, 0, st>>>(static_cast<const __nv_bfloat16*>(feat.p),
                                                     static_cast<const float*>(y.p),
                                                     static_cast<const int32_t*>(idx.p) + s * cfg->batch, cfg->batch,
@@ -928,6 +942,7 @@ extern "C" sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* co
 extern "C" sel_status sel_mlp_estimate(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds,
                                        const sel_table* table, int32_t n, float tau, double* est, float* sigma,
                                        uint8_t* used_exact) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !m || !preds || !table || n <= 0 || !est) {
         set_error("sel_mlp_estimate: bad arguments");
         return SEL_ERR_INVALID_ARG;
@@ -993,6 +1008,7 @@ extern "C" sel_status sel_mlp_get_grads(const sel_mlp* m, float* host, int64_t n
 }
 
 extern "C" sel_status sel_mlp_set_params(sel_ctx* ctx, sel_mlp* m, const float* host, int64_t n_floats) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !m || !host || n_floats != kParams) {
         set_error("sel_mlp_set_params: need %lld floats", (long long)kParams);
         return SEL_ERR_INVALID_ARG;
@@ -1040,6 +1056,7 @@ extern "C" sel_status sel_mlp_save(const sel_mlp* m, const char* path) {
 }
 
 extern "C" sel_status sel_mlp_load(sel_ctx* ctx, const char* path, sel_mlp** out) {
+    LaunchTally tally(ctx);   // this call's kernel launches count on ctx
     if (!ctx || !path || !out) {
         set_error("sel_mlp_load: bad arguments");
         return SEL_ERR_INVALID_ARG;

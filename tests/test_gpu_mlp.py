@@ -174,3 +174,27 @@ def test_repeated_featurize_reuses_the_staged_records(setup):
     assert torch.equal(fb2, fb) and torch.equal(ob2, ob)
     fresh, _ = est.featurize([sel.Predicate(T, tr) for tr in trees[:300]])   # recompiled: new ids
     assert torch.equal(fresh, fa)
+
+
+def test_launch_count_includes_the_estimator(setup):
+    """sel_ctx_launch_count counts every kernel the context launches, the
+    estimator's included: featurize is one kernel, the forward pass three
+    GEMMs and the head, and a training step a whole number of launches that is
+    the same every time; a training run made of steps counts each step once."""
+    t, T, ctx, est, cdfs, dicts, trees = setup
+    preds = [sel.Predicate(T, tr) for tr in trees[:64]]
+    l0 = ctx.launches
+    feat, _ = est.featurize(preds)
+    assert ctx.launches - l0 == 1
+    l1 = ctx.launches
+    est.forward(feat)
+    assert ctx.launches - l1 == 4
+    y = torch.zeros(64, dtype=torch.float32, device=feat.device)
+    cfg = sel.train_cfg(batch=64, lr=0.0, apply_update=0)
+    l2 = ctx.launches
+    est.train_step(feat, y, cfg)
+    per_step = ctx.launches - l2
+    assert per_step >= 8
+    l3 = ctx.launches
+    est.train_step(feat, y, cfg)
+    assert ctx.launches - l3 == per_step
