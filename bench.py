@@ -711,6 +711,28 @@ def traffic_for(kernel: str, source: str, algorithmic_bytes: float):
     return int(e["traffic_per_algorithmic_byte"] * algorithmic_bytes)
 
 
+def issue_roofline(kernel: str, source: str, n_rows: int, launch_ms: float, sm_mhz: float):
+    """The count scan's instruction-issue roofline, for launches bound by the
+    interpreter rather than by HBM.  Achieved: the warp instructions per row
+    that ncu measured on a smaller case of the same kernel and program set
+    (profiles/traffic.json) times this launch's rows, over the launch time.
+    Peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x the SM
+    clock.  None when the kernel source changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p) or launch_ms <= 0:
+        return None
+    with open(p) as f:
+        e = json.load(f).get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash(source) or "warp_instructions_per_row" not in e:
+        return None
+    achieved = e["warp_instructions_per_row"] * n_rows / (launch_ms / 1e3) / 1e9
+    peak = 148 * 4 * sm_mhz / 1e3
+    return {"bound": "alu", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp instructions/s", "frac": round(achieved / peak, 4), "kernel": kernel,
+            "warp_instructions_per_row": e["warp_instructions_per_row"],
+            "peak_source": f"148 SMs x 4 schedulers x 1 warp instruction/cycle x {sm_mhz:.0f} MHz"}
+
+
 # ----------------------------------------------------------------------------
 
 def main():
@@ -815,6 +837,8 @@ def main():
         "ms_per_estimate": round(elapsed_ms / args.steps / len(w.trees), 4),
         "roofline": roof(dominant),
         "roofline_other": roof(other),
+        "roofline_issue": issue_roofline("scan_count_kernel", "count.cu", w.n, count_ms,
+                                         float((clk or {}).get("sm_max_mhz") or 2032.0)),
         "gpu_launches": int(launches),
         "clocks": clk,
     }
