@@ -183,18 +183,20 @@ sel_status sel_pushdown_async(sel_ctx* ctx, const sel_pred* pred, const sel_tabl
  * query pipelines where an allocation may synchronise the whole device.
  * This entry point needs no sel_ctx and makes no cudaMalloc / cudaFree or
  * other allocating call: its scratch (look-back status words, tile counter,
- * program, error flag) lives in one fixed 4 MiB __device__ array inside the
- * library, which every GPU that loads the library holds until exit.
- * Limit: the table may have at most 516,064 tiles of the push-down's tile
- * (1024 rows, fewer when the rows are wide), i.e. about 528 million rows;
- * larger tables and programs above 64 KiB return SEL_ERR_UNSUPPORTED with a
- * message.  The caller passes the stream (cudaStream_t, NULL = legacy default
- * stream), the inputs, and all outputs, all caller-owned device memory:
- * dev_out_cols / dev_out_rowids as for sel_pushdown, dev_out_count (8 bytes,
- * receives the exact count; compare it with max_rows -- rows past max_rows
- * are never written) and dev_out_error (4 bytes, may be NULL; nonzero after
- * the stream reaches the end of the call means a look-back wait timed out
- * and the outputs are invalid).  Enqueue only: nothing waits for the GPU.
+ * program) lives in one fixed 4 MiB __device__ array inside the library,
+ * which every GPU that loads the library holds until exit.  The compiled
+ * program is handed to the GPU as kernel parameters (a copy kernel per
+ * 16 KiB), so no host buffer is read after the call returns.
+ * Limit: the table may have at most 516,064 tiles of 1024 rows, i.e.
+ * 528,449,536 rows; larger tables and programs above 64 KiB return
+ * SEL_ERR_UNSUPPORTED with a message.  The caller passes the stream
+ * (cudaStream_t, NULL = legacy default stream), the inputs, and all outputs,
+ * all caller-owned device memory: dev_out_cols / dev_out_rowids as for
+ * sel_pushdown, dev_out_count (8 bytes, receives the exact count; compare it
+ * with max_rows -- rows past max_rows are never written) and dev_out_error
+ * (4 bytes, required: NULL gives SEL_ERR_INVALID_ARG; nonzero after the
+ * stream reaches the end of the call means a look-back wait timed out and
+ * the count and rows are invalid).  Enqueue only: nothing waits for the GPU.
  * The first call on each device looks up the array's device address, so make
  * that first call before any stream capture.  All calls share the one array:
  * each call clears the parts that must start at zero, and calls that overlap

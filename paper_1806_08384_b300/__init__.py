@@ -422,9 +422,11 @@ class Context:
 
 def pushdown_noalloc(pred: Predicate, table, proj: Sequence[int], max_rows: int, out_cols: List[torch.Tensor],
                      out_rowids: Optional[torch.Tensor], out_count: torch.Tensor,
-                     out_error: Optional[torch.Tensor] = None, stream: Optional[torch.cuda.Stream] = None):
+                     out_error: Optional[torch.Tensor], stream: Optional[torch.cuda.Stream] = None):
     """sel_pushdown_noalloc: the push-down with the library's fixed scratch and
-    caller-owned outputs only (no context, no device allocation); enqueue only."""
+    caller-owned outputs only (no context, no device allocation); enqueue only.
+    out_error (int32, 1 element) is required; None is passed on as NULL and
+    the library rejects it."""
     table = Table.of(table)
     stream = stream or torch.cuda.current_stream()
     pc = (C.c_int32 * max(1, len(proj)))(*proj)

@@ -7,6 +7,11 @@
 // same kernel with all of that scratch in one file-scope __device__ array of
 // fixed size instead, so that it makes no cudaMalloc / cudaFree call and
 // needs no context.  The caller passes the inputs and every output.
+//
+// The compiled program reaches the array through kernel parameters: a small
+// copy kernel takes up to 16 KiB of the program by value per launch, so the
+// call reads no host buffer after it returns (a cudaMemcpyAsync from pageable
+// host memory could read it later, or wait for the GPU).
 #include <cstring>
 #include <mutex>
 
@@ -17,7 +22,7 @@ namespace {
 
 constexpr size_t kNaBytes = size_t(4) << 20;          // the whole array: 4 MiB per device
 constexpr size_t kNaBlobBytes = size_t(64) << 10;     // [0, 64 KiB): program blob
-constexpr size_t kNaMiscOff = kNaBlobBytes;           // tile counter (4 B) | error flag (4 B)
+constexpr size_t kNaMiscOff = kNaBlobBytes;           // tile counter (4 B)
 constexpr size_t kNaStatusOff = kNaBlobBytes + 256;   // [.., 4 MiB): one 8-byte status word per tile
 constexpr size_t kNaMaxTiles = (kNaBytes - kNaStatusOff) / 8;
 
@@ -76,6 +81,35 @@ bool blob_into(const Program& p, uint8_t* dst, size_t cap, uint32_t* bytes, uint
 
 thread_local uint8_t t_blob[kNaBlobBytes];
 
+// One piece of the program, passed by value to the copy kernel.
+constexpr uint32_t kNaPieceBytes = 16u << 10;
+struct BlobPiece {
+    uint4* dst;
+    uint32_t words;   // 16-byte words in this piece
+    uint32_t pad;
+    uint4 data[kNaPieceBytes / 16];
+};
+
+__global__ void __launch_bounds__(256) blob_piece_kernel(const __grid_constant__ BlobPiece p) {
+    for (uint32_t i = threadIdx.x; i < p.words; i += blockDim.x) p.dst[i] = p.data[i];
+}
+
+// Enqueues the copy of the laid-out program (bytes, a multiple of 16) into dst.
+cudaError_t upload_blob(uint8_t* dst, const uint8_t* src, uint32_t bytes, cudaStream_t st) {
+    BlobPiece piece;
+    for (uint32_t off = 0; off < bytes; off += kNaPieceBytes) {
+        const uint32_t n = bytes - off < kNaPieceBytes ? bytes - off : kNaPieceBytes;
+        piece.dst = reinterpret_cast<uint4*>(dst + off);
+        piece.words = n / 16u;
+        piece.pad = 0;
+        std::memcpy(piece.data, src + off, n);
+        blob_piece_kernel<<<1, 256, 0, st>>>(piece);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 }  // namespace sel
 
@@ -87,7 +121,7 @@ extern "C" sel_status sel_pushdown_noalloc(void* cuda_stream, const sel_pred* pr
                                            uint32_t* dev_out_error) {
     const char* who = "sel_pushdown_noalloc";
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    if (!pred || !table || !dev_out_count || n_proj < 0 || n_proj > kPdMaxProj ||
+    if (!pred || !table || !dev_out_count || !dev_out_error || n_proj < 0 || n_proj > kPdMaxProj ||
         (n_proj > 0 && (!proj_cols || !dev_out_cols)) || table->n_rows < 0 || table->n_cols < 0 ||
         (table->n_cols > 0 && !table->cols)) {
         set_error("%s: bad arguments", who);
@@ -118,7 +152,6 @@ extern "C" sel_status sel_pushdown_noalloc(void* cuda_stream, const sel_pred* pr
         a.width[j] = prog.slot_width[j];
         row_bytes += prog.slot_width[j];
     }
-    uint32_t proj_bytes = dev_out_rowids ? 8u : 0u;
     for (int32_t j = 0; j < n_proj; ++j) {
         const int c = proj_cols[j];
         if (c < 0 || c >= table->n_cols || table->cols[c].type < SEL_I32 || table->cols[c].type > SEL_DICT) {
@@ -138,10 +171,9 @@ extern "C" sel_status sel_pushdown_noalloc(void* cuda_stream, const sel_pred* pr
         a.proj_slot[j] = -1;
         for (size_t k = 0; k < prog.slot_col.size(); ++k)
             if (prog.slot_col[k] == c) a.proj_slot[j] = (int32_t)k;
-        proj_bytes += w;
     }
     if ((dev_out_rowids && reinterpret_cast<uintptr_t>(dev_out_rowids) % 8) ||
-        reinterpret_cast<uintptr_t>(dev_out_count) % 8 || (dev_out_error && reinterpret_cast<uintptr_t>(dev_out_error) % 4)) {
+        reinterpret_cast<uintptr_t>(dev_out_count) % 8 || reinterpret_cast<uintptr_t>(dev_out_error) % 4) {
         set_error("%s: misaligned row id, count or error output", who);
         return SEL_ERR_INVALID_ARG;
     }
@@ -157,9 +189,12 @@ extern "C" sel_status sel_pushdown_noalloc(void* cuda_stream, const sel_pred* pr
         set_error("%s: %s", who, cudaGetErrorString(e));
         return SEL_ERR_CUDA;
     }
+    // shared memory holds the program and the predicate columns of one tile
+    // (outputs are not staged); 1 KiB is left for the kernel's static arrays
     a.tile_rows = 1024;
-    const size_t fixed = ((size_t)blob_bytes + 127) / 128 * 128 + 1024 + 16 * (size_t)(n_proj + 1);
-    while (a.tile_rows > (uint32_t)kChunkRows && fixed + (size_t)a.tile_rows * (row_bytes + proj_bytes) > (size_t)max_smem)
+    auto up128 = [](size_t x) { return (x + 127) / 128 * 128; };
+    while (a.tile_rows > (uint32_t)kChunkRows &&
+           up128(blob_bytes) + up128((size_t)a.tile_rows * row_bytes) + 1024 > (size_t)max_smem)
         a.tile_rows -= kChunkRows;
     const int64_t n_tiles = (table->n_rows + a.tile_rows - 1) / a.tile_rows;
     if ((uint64_t)n_tiles > kNaMaxTiles) {
@@ -190,20 +225,19 @@ extern "C" sel_status sel_pushdown_noalloc(void* cuda_stream, const sel_pred* pr
     a.max_rows = max_rows;
     a.status = reinterpret_cast<unsigned long long*>(base + kNaStatusOff);
     a.tile_counter = reinterpret_cast<unsigned int*>(base + kNaMiscOff);
-    a.err = dev_out_error ? reinterpret_cast<unsigned int*>(dev_out_error)
-                          : reinterpret_cast<unsigned int*>(base + kNaMiscOff + 4);
+    a.err = reinterpret_cast<unsigned int*>(dev_out_error);
     a.total = reinterpret_cast<unsigned long long*>(dev_out_count);
     a.skip_publish_tile = -1;
     a.wait_ns = kWaitNs;
-    if (pushdown_layout(a) > (size_t)max_smem) {
+    if (pushdown_layout(a) + 1024 > (size_t)max_smem) {
         set_error("%s: tile does not fit in shared memory", who);
         return SEL_ERR_UNSUPPORTED;
     }
     // the array keeps the previous call's contents: clear what must start at zero
     if ((e = cudaMemsetAsync(base + kNaMiscOff, 0, 256 + (size_t)n_tiles * 8, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(dev_out_count, 0, 8, st)) != cudaSuccess ||
-        (dev_out_error && (e = cudaMemsetAsync(dev_out_error, 0, 4, st)) != cudaSuccess) ||
-        (e = cudaMemcpyAsync(base, t_blob, blob_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+        (e = cudaMemsetAsync(dev_out_error, 0, 4, st)) != cudaSuccess ||
+        (e = upload_blob(base, t_blob, blob_bytes, st)) != cudaSuccess) {
         set_error("%s: %s", who, cudaGetErrorString(e));
         return SEL_ERR_CUDA;
     }
