@@ -416,6 +416,19 @@ sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds,
  * 1 where the exact batched scan answered.  Synchronous. */
 sel_status sel_mlp_estimate(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds, const sel_table* table,
                             int32_t n, float tau, double* est, float* sigma, uint8_t* used_exact);
+/* a9 calibration of tau (the paper has no learned part; reading of the
+ * uncertainty rule): given held-out predicates' sigma (as returned by
+ * sel_mlp_estimate; +inf = no feature form, never accepted), the network's
+ * estimates est = max(0, exp(mu) - 1) and their exact counts, *tau_out = the
+ * largest sigma value t for which the `quantile`-th percentile (linear
+ * interpolation between order statistics, in double) of the q-errors
+ * max(e, c) / min(e, c) (e, c clamped to >= 1) of the predicates with
+ * sigma <= t is at most max_q; 0 when no t qualifies (everything exact).
+ * answered_out (may be NULL) = the fraction of the n predicates accepted at
+ * that tau.  Host only, no GPU work; SEL_ERR_INVALID_ARG on NULL inputs or a
+ * quantile outside [0, 100]. */
+sel_status sel_mlp_choose_tau(const float* sigma, const double* est, const uint64_t* exact, int64_t n,
+                              double max_q, double quantile, float* tau_out, double* answered_out);
 /* Parameters as one FP32 array (W1 256x144, b1 256, W2 256x256, b2, W3
  * 256x256, b3, W4 2x256, b4 2; row-major, [out][in]) of sel_mlp_param_count()
  * floats.  set also clears gradients and Adam state. */

@@ -21,7 +21,13 @@ surrogate computes so that the GPU kernels can be checked against it:
   Adam.  BF16 rounding (round to nearest even) is applied where the GPU
   rounds: the input features, the weights fed to the matrix products, the
   post-ReLU activations and the back-propagated pre-activation gradients
-  that feed the tensor-core products.  Everything else is float64 here.
+  that feed the tensor-core products.  Everything else is float64 here;
+* the gate of the surrogate-gated estimator (the uncertainty rule of the
+  heteroscedastic head): sigma = exp(lv / 2) with lv clamped to [-8, 8]; a
+  predicate without a feature form, or with sigma > tau, is answered by the
+  exact COUNT of §3.1, every other one by max(0, exp(mu) - 1);
+* the choice of tau on a held-out split: the largest tau for which the 95th
+  percentile of the q-error of the estimates it accepts is at most 2.
 """
 from __future__ import annotations
 
@@ -61,7 +67,7 @@ def splitmix64(z: np.ndarray) -> np.ndarray:
 
 
 def sample_indices(seed: int, col: int, m: int, n: int) -> np.ndarray:
-    base = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + np.uint64(((col + 1) << 40) & 0xFFFFFFFFFFFFFFFF))
+    base = np.uint64((seed + ((col + 1) << 40)) & 0xFFFFFFFFFFFFFFFF)
     with np.errstate(over="ignore"):
         z = base + np.arange(m, dtype=np.uint64)
     return (splitmix64(z) % np.uint64(n)).astype(np.int64)
@@ -74,6 +80,14 @@ class CDF:
         self.m = m
         idx = sample_indices(seed, col, m, column.shape[0])
         self.s = np.sort(column[idx], kind="stable")
+
+    @classmethod
+    def from_sample(cls, values) -> "CDF":
+        """A CDF over an explicit sample (hand-worked cases)."""
+        c = cls.__new__(cls)
+        c.s = np.sort(np.asarray(values), kind="stable")
+        c.m = int(c.s.shape[0])
+        return c
 
     def below(self, v) -> int:
         return int(np.searchsorted(self.s, v, side="left"))
@@ -272,3 +286,57 @@ def q_error(est, true) -> np.ndarray:
     e = np.maximum(np.asarray(est, np.float64), 1.0)
     t = np.maximum(np.asarray(true, np.float64), 1.0)
     return np.maximum(e / t, t / e)
+
+
+# ----------------------------------------------------------------------------
+# the gate (reading c15) and the choice of its threshold
+# ----------------------------------------------------------------------------
+
+def gate(mu, lv, ok, tau: float, exact):
+    """The surrogate-gated estimate of each predicate.
+
+    mu, lv: the network's two outputs (lv is clamped to [LV_MIN, LV_MAX]);
+    ok: the predicate has a feature form; exact: its exact COUNT.  A
+    predicate is answered exactly when it has no feature form or when
+    sigma = exp(lv / 2) is not <= tau; otherwise by max(0, exp(mu) - 1).
+    Returns (estimate, sigma, used_exact); sigma is +inf without a feature
+    form."""
+    mu = np.asarray(mu, np.float64)
+    lv = np.clip(np.asarray(lv, np.float64), LV_MIN, LV_MAX)
+    ok = np.asarray(ok, bool)
+    exact = np.asarray(exact, np.float64)
+    n = mu.shape[0]
+    est = np.empty(n, np.float64)
+    sigma = np.empty(n, np.float64)
+    used = np.empty(n, bool)
+    for i in range(n):
+        sigma[i] = math.exp(0.5 * lv[i]) if ok[i] else math.inf
+        used[i] = (not ok[i]) or not (sigma[i] <= tau)
+        est[i] = exact[i] if used[i] else max(0.0, math.expm1(mu[i]))
+    return est, sigma, used
+
+
+def percentile(x, q: float) -> float:
+    """The q-th percentile of x by linear interpolation between order
+    statistics: h = (n - 1) q / 100, x_(floor h) + (h - floor h)(x_(floor h + 1) - x_(floor h))."""
+    s = sorted(float(v) for v in x)
+    h = (len(s) - 1) * (q / 100.0)
+    lo = int(math.floor(h))
+    if lo + 1 >= len(s):
+        return s[-1]
+    return s[lo] + (h - lo) * (s[lo + 1] - s[lo])
+
+
+def choose_tau(sigma, est, exact, max_q: float = 2.0, q: float = 95.0) -> float:
+    """The largest tau, among the held-out sigmas, whose accepted estimates
+    (sigma <= tau) have a q-th percentile q-error of at most max_q; 0.0 (every
+    predicate answered exactly) when no tau qualifies.  Predicates with an
+    infinite sigma (no feature form) are never accepted."""
+    sigma = np.asarray(sigma, np.float64)
+    qe = q_error(est, exact)
+    best = 0.0
+    for t in sorted(set(float(v) for v in sigma if math.isfinite(v))):
+        acc = [float(qe[i]) for i in range(sigma.shape[0]) if sigma[i] <= t]
+        if acc and percentile(acc, q) <= max_q:
+            best = t
+    return best

@@ -126,6 +126,8 @@ def _load():
         "sel_mlp_estimate": (C.c_int, [V, V, P(V), P(sel_table), C.c_int32, C.c_float, P(C.c_double),
                                        P(C.c_float), P(C.c_uint8)]),
         "sel_mlp_param_count": (C.c_int64, []),
+        "sel_mlp_choose_tau": (C.c_int, [P(C.c_float), P(C.c_double), P(C.c_uint64), C.c_int64, C.c_double,
+                                         C.c_double, P(C.c_float), P(C.c_double)]),
         "sel_mlp_get_params": (C.c_int, [V, P(C.c_float), C.c_int64]),
         "sel_mlp_set_params": (C.c_int, [V, V, P(C.c_float), C.c_int64]),
         "sel_mlp_get_grads": (C.c_int, [V, P(C.c_float), C.c_int64]),
@@ -675,6 +677,22 @@ def evaluate_and_push_down(ctx: "Context", relations, min_table_size: int = 0, m
             d["rowids"] = ids[:d["count"]] if ids is not None else None
         res.append(d)
     return res
+
+
+def choose_tau(sigma, est, exact, max_q: float = 2.0, quantile: float = 95.0):
+    """sel_mlp_choose_tau: (tau, answered fraction) chosen on held-out predicates."""
+    sg = np.ascontiguousarray(np.asarray(sigma, np.float32))
+    es = np.ascontiguousarray(np.asarray(est, np.float64))
+    ex = np.ascontiguousarray(np.asarray(exact, np.uint64))
+    n = int(sg.shape[0])
+    if es.shape[0] != n or ex.shape[0] != n:
+        raise ValueError("sigma, est and exact need the same length")
+    tau = C.c_float(0.0)
+    ans = C.c_double(0.0)
+    _check(lib.sel_mlp_choose_tau(sg.ctypes.data_as(C.POINTER(C.c_float)), es.ctypes.data_as(C.POINTER(C.c_double)),
+                                  ex.ctypes.data_as(C.POINTER(C.c_uint64)), n, float(max_q), float(quantile),
+                                  C.byref(tau), C.byref(ans)), "sel_mlp_choose_tau")
+    return float(tau.value), float(ans.value)
 
 
 def join_size_estimate(rows_r: int, rows_s: int, distinct_r: int, distinct_s: int) -> float:

@@ -989,6 +989,63 @@ extern "C" sel_status sel_mlp_estimate(sel_ctx* ctx, sel_mlp* m, const sel_pred*
     return SEL_OK;
 }
 
+// a9 calibration: the largest tau among the held-out sigmas whose accepted
+// estimates (sigma <= tau) keep the `quantile` percentile of the q-error at or
+// below max_q.  The accepted set grows in sigma order; a Fenwick tree over the
+// q-error ranks gives the two order statistics of each percentile in O(log n).
+extern "C" sel_status sel_mlp_choose_tau(const float* sigma, const double* est, const uint64_t* exact, int64_t n,
+                                         double max_q, double quantile, float* tau_out, double* answered_out) {
+    if (!sigma || !est || !exact || n < 0 || !tau_out || !(quantile >= 0.0 && quantile <= 100.0)) {
+        set_error("sel_mlp_choose_tau: bad arguments");
+        return SEL_ERR_INVALID_ARG;
+    }
+    std::vector<double> q((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double e = std::max(est[i], 1.0), t = std::max((double)exact[i], 1.0);
+        q[(size_t)i] = std::max(e / t, t / e);
+    }
+    std::vector<int64_t> by_q((size_t)n), by_sigma;
+    for (int64_t i = 0; i < n; ++i) by_q[(size_t)i] = i;
+    std::sort(by_q.begin(), by_q.end(), [&](int64_t a, int64_t b) { return q[(size_t)a] < q[(size_t)b]; });
+    std::vector<int64_t> rank((size_t)n);
+    for (int64_t r = 0; r < n; ++r) rank[(size_t)by_q[(size_t)r]] = r;
+    for (int64_t i = 0; i < n; ++i)
+        if (std::isfinite(sigma[i])) by_sigma.push_back(i);
+    std::sort(by_sigma.begin(), by_sigma.end(), [&](int64_t a, int64_t b) { return sigma[a] < sigma[b]; });
+    std::vector<int64_t> fen((size_t)n + 1, 0);
+    auto add = [&](int64_t r) {
+        for (int64_t x = r + 1; x <= n; x += x & -x) ++fen[(size_t)x];
+    };
+    int64_t top = 1;
+    while (top * 2 <= n) top *= 2;
+    auto kth = [&](int64_t k) {   // the k-th smallest inserted q-error (0-based)
+        int64_t pos = 0;
+        for (int64_t step = top; step > 0; step >>= 1)
+            if (pos + step <= n && fen[(size_t)(pos + step)] <= k) {
+                pos += step;
+                k -= fen[(size_t)pos];
+            }
+        return q[(size_t)by_q[(size_t)pos]];
+    };
+    float best = 0.f;
+    int64_t best_cnt = 0, cnt = 0;
+    for (size_t j = 0; j < by_sigma.size();) {
+        const float t = sigma[by_sigma[j]];
+        for (; j < by_sigma.size() && sigma[by_sigma[j]] == t; ++j, ++cnt) add(rank[(size_t)by_sigma[j]]);
+        const double h = (double)(cnt - 1) * (quantile / 100.0);
+        const int64_t lo = (int64_t)std::floor(h);
+        const double a = kth(lo);
+        const double p = lo + 1 >= cnt ? kth(cnt - 1) : a + (h - (double)lo) * (kth(lo + 1) - a);
+        if (p <= max_q) {
+            best = t;
+            best_cnt = cnt;
+        }
+    }
+    *tau_out = best;
+    if (answered_out) *answered_out = n > 0 ? (double)best_cnt / (double)n : 0.0;
+    return SEL_OK;
+}
+
 extern "C" int64_t sel_mlp_param_count(void) { return kParams; }
 
 extern "C" sel_status sel_mlp_get_params(const sel_mlp* m, float* host, int64_t n_floats) {

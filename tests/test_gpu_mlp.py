@@ -5,8 +5,8 @@ BF16 like the GPU's); the forward pass, the gradients of the Gaussian NLL and
 the Adam step within the tolerance the arithmetic allows: FP32 accumulation
 in a different order plus BF16 rounding points that may flip by one BF16 ulp,
 so |gpu - oracle| <= 2e-2 * (1 + |oracle|) element-wise for outputs and
-<= 2e-2 * max|oracle| per tensor for gradients.  Every exact fallback of the
-gate equals the exact count."""
+<= 2e-2 * max|oracle| per tensor for gradients.  The gate is compared with the
+oracle's gate, its exact fallbacks with oracle.count."""
 import math
 
 import numpy as np
@@ -14,6 +14,7 @@ import pytest
 import torch
 
 import datagen as dg
+import oracle
 from oracle import mlp as om
 import paper_1806_08384_b300 as sel
 from paper_1806_08384_b300 import baselines
@@ -139,22 +140,75 @@ def test_training_versus_the_independence_estimate(setup):
     assert np.percentile(q_mlp[acc], 95) <= 3.0
 
 
-def test_gate_exact_fallback_and_checkpoint(setup, tmp_path):
+def _distinct_gap_tau(sig):
+    """A threshold halfway between two neighbouring distinct sigmas near the
+    median, with a gap far above float32 rounding, so that no sigma sits on it."""
+    s = np.unique(sig[np.isfinite(sig)])
+    mid = len(s) // 2
+    for k in list(range(mid, len(s) - 1)) + list(range(mid - 1, -1, -1)):
+        if s[k + 1] - s[k] > 1e-4 * s[k + 1]:
+            return float(0.5 * (s[k] + s[k + 1]))
+    raise AssertionError("no gap between sigmas")
+
+
+def test_gate_against_the_oracle_gate(setup, tmp_path):
+    """sel_mlp_estimate against oracle.mlp.gate with exact counts from oracle.count:
+    (1) fed the network outputs the GPU computed on the same features, every
+    decision, sigma and estimate agrees (fallbacks bit-exact, accepted
+    estimates the same expm1 of the same float32 mu); (2) fed the oracle's own
+    features and forward pass with the model's parameters, sigmas and
+    estimates agree within the forward tolerance and every decision agrees
+    outside the band that tolerance allows around tau."""
     t, T, ctx, est, cdfs, dicts, trees = setup
-    preds = [sel.Predicate(T, tr) for tr in trees[:200]] + [sel.Predicate(T, trees[-1])]
-    exact = np.array(sel.count_many(ctx, preds, T), dtype=np.float64)
-    e0, s0, u0 = est.estimate(preds, T, tau=0.0)
-    assert u0.all() and np.array_equal(e0, exact)
-    e1, s1, u1 = est.estimate(preds, T, tau=float("inf"))
-    assert u1[-1] and not u1[:-1].any()             # the last one has no feature form
-    assert e1[-1] == exact[-1]
-    tau = float(np.median(s1[:-1]))
-    e2, s2, u2 = est.estimate(preds, T, tau=tau)
-    assert np.array_equal(e2[u2], exact[u2]) and np.all(s2[:-1][u2[:-1]] > tau)
+    P = om.init_params(13)
+    rng = np.random.default_rng(13)
+    for k in ("b1", "b2", "b3", "b4"):
+        P[k] = (rng.standard_normal(P[k].shape) * 0.05).astype(np.float32)
+    est.set_params(sel.flatten(P))
+    sub = trees[:200] + [trees[-1]]                     # the last one has no feature form
+    preds = [sel.Predicate(T, tr) for tr in sub]
+    ot = oracle.OTable.from_table(t)
+    exact = np.array([oracle.count(ot, tr, threads=8) for tr in sub], dtype=np.uint64)
+    feat, ok = est.featurize(preds)
+    okh = ok.cpu().numpy().astype(bool)
+    assert okh[:-1].all() and not okh[-1]
+    out = est.forward(feat).cpu().numpy().astype(np.float64)
+
+    # (1) the gate's rule on the GPU network's outputs
+    _, sig_all, _ = om.gate(out[:, 0], out[:, 1], okh, math.inf, exact)
+    taus = [0.0, math.inf, _distinct_gap_tau(sig_all)]
+    for tau in taus:
+        we, ws, wu = om.gate(out[:, 0], out[:, 1], okh, tau, exact)
+        e, s, u = est.estimate(preds, T, tau=tau)
+        assert np.array_equal(u.astype(bool), wu), tau
+        assert np.array_equal(e, we), tau
+        fin = np.isfinite(ws)
+        assert np.array_equal(np.isfinite(s), fin)
+        assert np.all(np.abs(s[fin] - ws[fin]) <= 1e-6 * ws[fin]), tau
+    assert 0 < int(np.sum(~om.gate(out[:, 0], out[:, 1], okh, taus[2], exact)[2])) < len(sub) - 1
+
+    # (2) the same against the oracle's features and forward pass
+    X = np.stack([om.featurize(tr, cdfs, dicts)[0] for tr in sub])
+    ref = om.forward(sel.unflatten(est.get_params()), X)
+    tol_lv = 2e-2 * (1 + np.abs(ref["lv"]))
+    tol_mu = 2e-2 * (1 + np.abs(ref["mu"]))
+    tau = taus[2]
+    we, ws, wu = om.gate(ref["mu"], ref["lv"], okh, tau, exact)
+    e, s, u = est.estimate(preds, T, tau=tau)
+    u = u.astype(bool)
+    fin = np.isfinite(ws)
+    assert np.all(np.abs(np.log(s[fin]) - np.log(ws[fin])) <= 0.5 * tol_lv[fin] + 1e-6)
+    clear = ~fin | (np.abs(np.log(ws) - math.log(tau)) > 0.5 * tol_lv + 1e-6)
+    assert clear.sum() >= len(sub) // 2
+    assert np.array_equal(u[clear], wu[clear])
+    both_exact = u & wu
+    assert np.array_equal(e[both_exact], we[both_exact])
+    both_est = ~u & ~wu
+    assert np.all(np.abs(np.log1p(e[both_est]) - np.log1p(we[both_est])) <= tol_mu[both_est])
+
     path = str(tmp_path / "m.bin")
     est.save(path)
     again = sel.Estimator.load(ctx, path)
-    feat, _ = est.featurize(preds)
     assert torch.equal(est.forward(feat), again.forward(feat))
 
 

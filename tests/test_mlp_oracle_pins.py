@@ -7,9 +7,15 @@
   float64 with rounding off);
 * the Gaussian NLL and its gradient at closed-form points;
 * Adam's first step moves each parameter by lr * g / (|g| + eps);
-* CDF features partition the sample: < a, BETWEEN a..b and > b cover it once.
+* CDF features partition the sample: < a, BETWEEN a..b and > b cover it once;
+* the hand-worked features, gate, tau rule and network of tests/mlp_pins.py,
+  and a planted mistake in each part of a copy of the oracle (a dropped
+  complement, a shifted one-hot, a wrong log base, a strict gate, ...) fails
+  at least one of those pins.
 """
 import math
+import os
+import types
 
 import numpy as np
 import pytest
@@ -17,6 +23,7 @@ import torch
 
 import datagen as dg
 from oracle import mlp
+from tests import mlp_pins
 
 
 def test_bf16_rounding_matches_torch():
@@ -109,3 +116,60 @@ def test_dnf_shapes():
     assert mlp.dnf_groups(dg.p_and(a, dg.p_or(b, c))) is None
     f, ok = mlp.featurize(dg.p_or(*[dg.p_and(a, b)] * 4), [None] * 8, [None] * 8)
     assert not ok
+
+
+# ----------------------------------------------------------------------------
+# hand-worked pins (tests/mlp_pins.py) and planted mistakes in copies of the oracle
+# ----------------------------------------------------------------------------
+
+
+
+@pytest.mark.parametrize("pin", mlp_pins.ALL_PINS, ids=lambda p: p.__name__)
+def test_estimator_pin(pin):
+    assert pin(mlp) == []
+
+
+MLP_MUTANTS = {
+    "ne_complement_dropped": ("    if ne:\n        p = 1.0 - p\n", ""),
+    "not_complement_dropped": ("    if neg:\n        p = 1.0 - p\n", ""),
+    "log_base_m": ("/ math.log(2.0 * m)", "/ math.log(1.0 * m)"),
+    "log_floor_1_over_m": ("max(p, 0.5 / m)", "max(p, 1.0 / m)"),
+    "column_onehot_shifted": ("f[o + col] = 1.0", "f[o + col + 1] = 1.0"),
+    "operator_onehot_offset": ("f[o + 8 + op_index(leaf)] = 1.0", "f[o + 9 + op_index(leaf)] = 1.0"),
+    "not_flag_slot": ("f[o + 17] = 1.0", "f[o + 16] = 1.0"),
+    "group_onehot_offset": ("f[o + 20 + gi] = 1.0", "f[o + 21 + gi] = 1.0"),
+    "op_index_in_like_swapped": ('{"between": 6, "in": 7, "like": 8}', '{"between": 6, "in": 8, "like": 7}'),
+    "lt_counts_equal_rows": ('        if op == "<":\n            return 0.0, cdf.frac(cdf.below(v))',
+                             '        if op == "<":\n            return 0.0, cdf.frac(cdf.upto(v))'),
+    "between_hi_exclusive": ("cdf.frac(max(lo, cdf.upto(leaf[3])))", "cdf.frac(max(lo, cdf.below(leaf[3])))"),
+    "in_duplicates_counted": ("vals = sorted(set(leaf[2]))", "vals = sorted(leaf[2])"),
+    "like_prefix_ignored": ("if w.startswith(pre)]", "if w[:1] == pre[:1]]"),
+    "sample_column_offset": ("((col + 1) << 40)", "(col << 40)"),
+    "relu_dropped": ("a = r(np.maximum(z, 0.0).astype(", "a = r(np.asarray(z).astype("),
+    "heads_swapped": ('c["mu"] = out[:, 0]\n    c["lv"] = np.clip(out[:, 1], LV_MIN, LV_MAX)',
+                      'c["mu"] = out[:, 1]\n    c["lv"] = np.clip(out[:, 0], LV_MIN, LV_MAX)'),
+    "bias_dropped": ('z = a @ r(P[f"W{l}"]).T + P[f"b{l}"].astype(np.float64)', 'z = a @ r(P[f"W{l}"]).T'),
+    "gate_sigma_without_half": ("math.exp(0.5 * lv[i])", "math.exp(lv[i])"),
+    "gate_strict_accept": ("not (sigma[i] <= tau)", "not (sigma[i] < tau)"),
+    "gate_exp_not_expm1": ("max(0.0, math.expm1(mu[i]))", "max(0.0, math.exp(mu[i]))"),
+    "gate_no_floor": ("max(0.0, math.expm1(mu[i]))", "math.expm1(mu[i])"),
+    "gate_ignores_feature_form": ("used[i] = (not ok[i]) or not (sigma[i] <= tau)", "used[i] = not (sigma[i] <= tau)"),
+    "gate_no_clamp": ("lv = np.clip(np.asarray(lv, np.float64), LV_MIN, LV_MAX)", "lv = np.asarray(lv, np.float64)"),
+    "tau_median": ("percentile(acc, q) <= max_q", "percentile(acc, 50.0) <= max_q"),
+    "tau_smallest": ("            best = t\n", "            best = t if best == 0.0 else best\n"),
+    "percentile_nearest_lower": ("return s[lo] + (h - lo) * (s[lo + 1] - s[lo])", "return s[lo]"),
+    "q_error_unclamped": ("e = np.maximum(np.asarray(est, np.float64), 1.0)", "e = np.asarray(est, np.float64)"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MLP_MUTANTS))
+def test_estimator_pins_catch_planted_mistake(name):
+    src = open(os.path.join(os.path.dirname(mlp.__file__), "mlp.py")).read()
+    old, new = MLP_MUTANTS[name]
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mod = types.ModuleType(f"mlp_mutant_{name}")
+    mod.__file__ = mlp.__file__
+    with np.errstate(all="ignore"):
+        exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), mod.__dict__)
+        fails = mlp_pins.run_all(mod)
+    assert fails, f"no pin catches mutant {name}"
