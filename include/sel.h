@@ -244,6 +244,18 @@ sel_status sel_batch_plan_info(const sel_batch_plan* plan, int32_t* tile_rows, i
                                int32_t* ctas_per_sm, float* ms);
 /* Count-scan kernel variant chosen by the plan (see sel_ctx_set_scan_variant). */
 sel_status sel_batch_plan_variant(const sel_batch_plan* plan, int32_t* consumer_warps, int32_t* chunks_per_pass);
+/* The kernel the plan runs: 0 = the program interpreter (count.cu), 1 = the
+ * column-bucket kernel (bucket_count.cu): every predicate taken to an OR of at
+ * most 4 AND-groups, each row's bucket per referenced column found once, and
+ * every probe's leaves read from per-bucket group masks.  Both give the same
+ * exact counts; plan creation picks the faster (measured when autotuning,
+ * else the bucket kernel whenever the probes fit it). */
+sel_status sel_batch_plan_kernel(const sel_batch_plan* plan, int32_t* kernel);
+/* Which kernels later batch plans of this context may use: 0 = the faster of
+ * both (default), 1 = the interpreter only, 2 = the bucket kernel only
+ * (plans whose probes do not fit it fail with SEL_ERR_UNSUPPORTED).  Clears
+ * the context's cache of sel_count_batch plans. */
+sel_status sel_ctx_set_batch_kernel(sel_ctx* ctx, int32_t mode);
 void sel_batch_plan_free(sel_batch_plan* plan);
 
 /* Launch configuration override for sel_count / sel_count_async / sel_pushdown
@@ -448,6 +460,15 @@ sel_status sel_mlp_load(sel_ctx* ctx, const char* path, sel_mlp** out);
  * nonzero if a bounded wait inside the kernel gave up. */
 sel_status sel_debug_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int32_t N, int32_t K,
                                float* C, int32_t k_splits, uint32_t* dev_err);
+
+/* Test hook for the column-bucket form of a batch (host only, no GPU): the
+ * exact counts of preds[0..n) over `table`, whose column pointers are HOST
+ * memory here, evaluated on the CPU from the same bucket tables the GPU
+ * kernel reads (counts: host, n entries; n_blocks, may be NULL: blocks of 64
+ * probes the form used).  SEL_ERR_UNSUPPORTED (message in sel_last_error)
+ * when the probes do not fit the form. */
+sel_status sel_debug_bucket_count_host(const sel_pred* const* preds, int32_t n, const sel_table* table,
+                                       uint64_t* counts, int32_t* n_blocks);
 
 #ifdef __cplusplus
 }

@@ -106,6 +106,9 @@ def _load():
         "sel_batch_plan_info": (C.c_int, [V, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_float)]),
         "sel_batch_plan_variant": (C.c_int, [V, P(C.c_int32), P(C.c_int32)]),
         "sel_batch_plan_free": (None, [V]),
+        "sel_batch_plan_kernel": (C.c_int, [V, P(C.c_int32)]),
+        "sel_ctx_set_batch_kernel": (C.c_int, [V, C.c_int32]),
+        "sel_debug_bucket_count_host": (C.c_int, [P(V), C.c_int32, P(sel_table), P(C.c_uint64), P(C.c_int32)]),
         "sel_ctx_set_scan_shape": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32]),
         "sel_ctx_set_scan_variant": (C.c_int, [V, C.c_int32, C.c_int32]),
         "sel_ctx_launch_count": (C.c_uint64, [V]),
@@ -343,6 +346,10 @@ class Context:
     def set_scan_variant(self, consumer_warps=0, chunks_per_pass=0):
         _check(lib.sel_ctx_set_scan_variant(self.h, consumer_warps, chunks_per_pass), "sel_ctx_set_scan_variant")
 
+    def set_batch_kernel(self, mode: int):
+        """0: the faster of both kernels, 1: interpreter only, 2: bucket kernel only."""
+        _check(lib.sel_ctx_set_batch_kernel(self.h, int(mode)), "sel_ctx_set_batch_kernel")
+
     def debug_pushdown_fault(self, skip_tile: int, wait_ns: int = 0):
         _check(lib.sel_ctx_debug_pushdown_fault(self.h, skip_tile, wait_ns), "sel_ctx_debug_pushdown_fault")
 
@@ -486,8 +493,11 @@ class BatchPlan:
                "sel_batch_plan_info")
         w, g = C.c_int32(), C.c_int32()
         _check(lib.sel_batch_plan_variant(self.h, C.byref(w), C.byref(g)), "sel_batch_plan_variant")
+        k = C.c_int32()
+        _check(lib.sel_batch_plan_kernel(self.h, C.byref(k)), "sel_batch_plan_kernel")
         return {"tile_rows": tr.value, "stages": st.value, "ctas_per_sm": cp.value, "ms": ms.value,
-                "consumer_warps": w.value, "chunks_per_pass": g.value}
+                "consumer_warps": w.value, "chunks_per_pass": g.value,
+                "kernel": ("interpreter", "bucket")[k.value]}
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -677,6 +687,18 @@ def evaluate_and_push_down(ctx: "Context", relations, min_table_size: int = 0, m
             d["rowids"] = ids[:d["count"]] if ids is not None else None
         res.append(d)
     return res
+
+
+def debug_bucket_count_host(preds: Sequence[Predicate], table):
+    """sel_debug_bucket_count_host: (counts, blocks) of the column-bucket form
+    evaluated on the CPU; ``table`` holds CPU tensors."""
+    table = Table.of(table)
+    n = len(preds)
+    pa = (C.c_void_p * n)(*[p.h.value for p in preds])
+    out = (C.c_uint64 * n)()
+    nb = C.c_int32()
+    _check(lib.sel_debug_bucket_count_host(pa, n, table.ref(), out, C.byref(nb)), "sel_debug_bucket_count_host")
+    return [int(x) for x in out], int(nb.value)
 
 
 def choose_tau(sigma, est, exact, max_q: float = 2.0, quantile: float = 95.0):

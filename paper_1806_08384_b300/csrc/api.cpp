@@ -13,6 +13,7 @@
 #include <tuple>
 #include <vector>
 
+#include "bucket.h"
 #include "internal.h"
 
 namespace sel {
@@ -75,6 +76,8 @@ struct sel_ctx {
     int max_smem = 0;         // opt-in shared memory per block
     int max_smem_scan = 0;    // dynamic shared memory available to the scan kernel
     int max_smem_pdp = 0;     // dynamic shared memory available to the persistent push-down
+    int max_smem_bucket = 0;  // dynamic shared memory available to the bucket count kernel
+    int batch_kernel = 0;     // batch plans: 0 autotuned choice, 1 interpreter only, 2 bucket kernel only
     DevBuf counts;            // sel_count / batch staging
     DevBuf err;               // 4 bytes: error flag of the last launches
     DevBuf pd_scratch;        // push-down: tile status | tile counter | total
@@ -103,6 +106,10 @@ struct sel_batch_plan {
     float ms = 0.f;
     cudaGraphExec_t graph = nullptr;
     int launches_per_run = 0;
+    // the column-bucket form of the same probes (bucket.h), when they fit it
+    int kernel = 0;                    // the kernel the plan runs: 0 interpreter, 1 bucket
+    void* d_bk_blob = nullptr;
+    uint32_t bk_blob_bytes = 0, bk_gb_bytes = 0, bk_n_out = 0;
 };
 
 namespace sel {
@@ -279,6 +286,97 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
     return SEL_OK;
 }
 
+// The bucket kernel's launch arguments for a plan's tables (one launch: at
+// most kMaxTables tables): the largest tile (multiple of 256 rows, at most the
+// requested one) whose stages fit next to the counters, the bucket blob and
+// the per-warp bucket-index buffers; the library's choice also keeps about 4
+// tiles per CTA on small tables.  *smem: the dynamic shared memory needed.
+static sel_status resolve_bucket(sel_ctx* ctx, const sel_batch_plan* p, const std::vector<TableArg>& tables,
+                                 const Shape& sh_in, ScanArgs* args, size_t* smem, Shape* used) {
+    Shape sh = sh_in;
+    if (!bucket_variant_ok(sh.warps) || sh.stages < 1 || tables.size() > (size_t)kMaxTables) {
+        set_error("bucket scan: unsupported launch shape");
+        return SEL_ERR_UNSUPPORTED;
+    }
+    ScanArgs& a = *args;
+    std::memset(&a, 0, sizeof(a));
+    a.blob = static_cast<const uint8_t*>(p->d_bk_blob);
+    a.blob_bytes = p->bk_blob_bytes;
+    a.n_progs = p->bk_n_out;
+    a.stages = (uint32_t)sh.stages;
+    a.err = static_cast<unsigned int*>(ctx->err.p);
+    a.n_tables = (uint32_t)tables.size();
+    uint32_t max_rb = 0;
+    int64_t rows = 0;
+    for (auto& t : tables) {
+        max_rb = std::max(max_rb, t.row_bytes);
+        rows += t.n_rows;
+    }
+    const size_t fixed = bucket_layout(a, sh.warps, p->bk_gb_bytes);
+    if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem_bucket) {
+        set_error("bucket scan: %zu bytes of tables and counters leave no room for %d stages", fixed, sh.stages);
+        return SEL_ERR_UNSUPPORTED;
+    }
+    if (max_rb > 0) {
+        const size_t per_stage = ((size_t)ctx->max_smem_bucket - fixed) / (size_t)sh.stages;
+        const int fit = (int)(per_stage / max_rb) / kChunkRows * kChunkRows;
+        if (fit < kChunkRows) {
+            set_error("bucket scan: %d stages of 256 rows x %u bytes do not fit in shared memory", sh.stages, max_rb);
+            return SEL_ERR_UNSUPPORTED;
+        }
+        sh.tile_rows = std::min(sh.tile_rows, fit);
+    }
+    if (sh.auto_tile) {
+        const int64_t want = 4ll * ctx->n_sm * std::max(1, sh.ctas_per_sm);
+        const int64_t cap = rows / want / kChunkRows * kChunkRows;
+        if (cap < sh.tile_rows) sh.tile_rows = (int)std::max<int64_t>(kChunkRows, cap);
+        sh.auto_tile = false;
+    }
+    a.tile_rows = (uint32_t)sh.tile_rows;
+    int64_t tiles = 0;
+    for (size_t i = 0; i < tables.size(); ++i) {
+        TableArg ta = tables[i];
+        ta.n_tiles = (ta.n_rows + sh.tile_rows - 1) / sh.tile_rows;
+        ta.tile_begin = tiles;
+        tiles += ta.n_tiles;
+        uint32_t off = 0;
+        for (uint32_t j = 0; j < ta.n_slots; ++j) {
+            ta.slot_off[j] = off;
+            off += (uint32_t)sh.tile_rows * ta.width[j];
+        }
+        a.t[i] = ta;
+    }
+    a.total_tiles = tiles;
+    a.stage_bytes = ((uint32_t)sh.tile_rows * max_rb + 127u) / 128u * 128u;
+    *smem = bucket_layout(a, sh.warps, p->bk_gb_bytes);
+    if (*smem > (size_t)ctx->max_smem_bucket) {
+        set_error("bucket scan: %zu bytes of shared memory needed", *smem);
+        return SEL_ERR_UNSUPPORTED;
+    }
+    if (used) *used = sh;
+    return SEL_OK;
+}
+
+static sel_status run_bucket(sel_ctx* ctx, const sel_batch_plan* p, const Shape& sh_in, unsigned long long* d_counts,
+                             int* n_launches) {
+    ScanArgs a;
+    size_t smem = 0;
+    Shape sh;
+    sel_status s = resolve_bucket(ctx, p, p->tables, sh_in, &a, &smem, &sh);
+    if (s != SEL_OK) return s;
+    a.counts = d_counts;
+    int launches = 0;
+    if (a.total_tiles > 0) {
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.total_tiles, (int64_t)ctx->n_sm * sh.ctas_per_sm));
+        cudaError_t e = launch_bucket_count(a, (int)grid, smem, ctx->stream, sh.warps);
+        if (e != cudaSuccess) return cuda_fail("bucket scan launch", e);
+        ++launches;
+        ctx->launches++;
+    }
+    if (n_launches) *n_launches = launches;
+    return SEL_OK;
+}
+
 static Shape single_shape(sel_ctx* ctx, uint32_t row_bytes) {
     Shape s;
     // measured on the 300M-row fact table: 3 stages that fill shared memory
@@ -338,6 +436,7 @@ extern "C" sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out) {
              cudaDeviceGetAttribute(&c->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     SEL_CUDA("scan smem attribute", scan_kernel_max_smem(c->max_smem, &c->max_smem_scan));
     SEL_CUDA("push-down smem attribute", pushdown_persistent_max_smem(c->max_smem, &c->max_smem_pdp));
+    SEL_CUDA("bucket smem attribute", bucket_kernel_max_smem(c->max_smem, &c->max_smem_bucket));
     sel_status s = c->err.ensure(256, "error flag");
     if (s != SEL_OK) return s;
     SEL_CUDA("cudaMemset", cudaMemset(c->err.p, 0, 256));
@@ -842,7 +941,15 @@ static std::string table_key(const sel_table* t) {
     return k;
 }
 
-static sel_status plan_time(sel_batch_plan* p, const Shape& sh, int reps, float* ms) {
+// One launch of the plan's probes on the given kernel (0 interpreter, 1 bucket).
+static sel_status plan_launch(sel_batch_plan* p, int kernel, const Shape& sh, int* n_launches) {
+    unsigned long long* d_counts = static_cast<unsigned long long*>(p->d_counts);
+    if (kernel == 1) return run_bucket(p->ctx, p, sh, d_counts, n_launches);
+    return run_scan(p->ctx, static_cast<const uint8_t*>(p->d_blob), p->blob_bytes, p->instr_off, p->pool_off,
+                    p->n_progs, p->tables, d_counts, sh, n_launches);
+}
+
+static sel_status plan_time(sel_batch_plan* p, int kernel, const Shape& sh, int reps, float* ms) {
     sel_ctx* ctx = p->ctx;
     cudaEvent_t e0, e1;
     SEL_CUDA("cudaEventCreate", cudaEventCreate(&e0));
@@ -852,8 +959,7 @@ static sel_status plan_time(sel_batch_plan* p, const Shape& sh, int reps, float*
     for (int r = 0; r <= reps && s == SEL_OK; ++r) {
         cudaEventRecord(e0, ctx->stream);
         cudaMemsetAsync(p->d_counts, 0, (size_t)p->n * 8, ctx->stream);
-        s = run_scan(ctx, static_cast<const uint8_t*>(p->d_blob), p->blob_bytes, p->instr_off, p->pool_off,
-                     p->n_progs, p->tables, static_cast<unsigned long long*>(p->d_counts), sh, nullptr);
+        s = plan_launch(p, kernel, sh, nullptr);
         cudaEventRecord(e1, ctx->stream);
         cudaError_t e = cudaEventSynchronize(e1);
         if (e != cudaSuccess) s = cuda_fail("autotune", e);
@@ -881,8 +987,7 @@ static sel_status plan_capture(sel_batch_plan* p) {
     int nl = 0;
     if (s == SEL_OK) {
         cudaMemsetAsync(p->d_counts, 0, (size_t)p->n * 8, cs);
-        s = run_scan(ctx, static_cast<const uint8_t*>(p->d_blob), p->blob_bytes, p->instr_off, p->pool_off,
-                     p->n_progs, p->tables, static_cast<unsigned long long*>(p->d_counts), p->shape, &nl);
+        s = plan_launch(p, p->kernel, p->shape, &nl);
         e = cudaStreamEndCapture(cs, &g);
         if (s == SEL_OK && e != cudaSuccess) s = cuda_fail("cudaStreamEndCapture", e);
     }
@@ -933,6 +1038,7 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     std::vector<const Program*> progs;
     std::vector<std::vector<int32_t>> maps;
     std::vector<uint32_t> outs;
+    std::vector<BkTableIn> bk_in(gtab.size());
     for (size_t g = 0; g < gtab.size(); ++g) {
         std::vector<int32_t> cols;
         for (int32_t i = 0; i < n; ++i)
@@ -955,8 +1061,12 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
             progs.push_back(&preds[i]->prog);
             maps.push_back(m);
             outs.push_back((uint32_t)i);
+            bk_in[g].progs.push_back(&preds[i]->prog);
+            bk_in[g].slot_maps.push_back(m);
+            bk_in[g].outs.push_back((uint32_t)i);
         }
         ta.prog_end = (uint32_t)progs.size();
+        for (uint32_t j = 0; j < ta.n_slots; ++j) bk_in[g].slot_width.push_back(ta.width[j]);
         p->tables.push_back(ta);
     }
     p->n_progs = (uint32_t)progs.size();
@@ -968,19 +1078,81 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_counts, (size_t)n * 8));
     uint32_t max_rb = 0;
     for (auto& t : p->tables) max_rb = std::max(max_rb, t.row_bytes);
+    // the column-bucket form, when the probes fit it (bucket.h)
+    bool bucket_ok = false;
+    if (ctx->batch_kernel != 1) {
+        BucketPlan bp;
+        std::string why;
+        const sel_status bs = build_bucket_plan(bk_in, &bp, &why);
+        if (bs == SEL_OK) {
+            BkHeader hdr;
+            std::memcpy(&hdr, bp.blob.data(), sizeof(hdr));
+            p->bk_blob_bytes = (uint32_t)bp.blob.size();
+            p->bk_n_out = bp.n_out;
+            p->bk_gb_bytes = hdr.gb_slots * 8u * 32u * 2u;
+            SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_bk_blob, bp.blob.size()));
+            SEL_CUDA("cudaMemcpy", cudaMemcpy(p->d_bk_blob, bp.blob.data(), bp.blob.size(), cudaMemcpyHostToDevice));
+            bucket_ok = true;
+        } else if (ctx->batch_kernel == 2) {
+            set_error("%s: %s", who, why.c_str());
+            return bs;
+        }
+    }
     // default shape, then the autotuner's candidates (stage size, stages, CTAs
     // per SM, consumer warps, chunks per instruction pass)
     // (stage_kb 0: the largest tile whose stages fit in shared memory); the
     // default shape is the single-probe count's, with the context's overrides
     Shape best = single_shape(ctx, max_rb);
+    int best_kernel = 0;
+    Shape bucket_default;   // 8 consumer warps, 3 stages that fill shared memory, or the context's overrides
+    bucket_default.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 3;
+    bucket_default.ctas_per_sm = 1;
+    bucket_default.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : kMaxTileRows;
+    bucket_default.auto_tile = ctx->shape.tile_rows <= 0;
+    bucket_default.warps = bucket_variant_ok(ctx->shape.warps) ? ctx->shape.warps : 8;
+    bucket_default.group = 1;
+    if (bucket_ok) {   // tables too large for shared memory next to the stages: the interpreter
+        ScanArgs a;
+        size_t smem = 0;
+        const sel_status rs = resolve_bucket(ctx, p.get(), p->tables, bucket_default, &a, &smem, nullptr);
+        if (rs == SEL_OK) {
+            best = bucket_default;
+            best_kernel = 1;
+        } else if (ctx->batch_kernel == 2) {
+            return rs;
+        } else {
+            bucket_ok = false;
+        }
+    }
     float best_ms = 0.f;
-    if (autotune) {
+    if (autotune && bucket_ok) {
+        struct BCand { int stage_kb, stages, warps; };
+        const BCand bc[] = {{0, 3, 8}, {0, 2, 8}, {0, 4, 8}, {48, 3, 8}, {32, 4, 8}, {0, 3, 16}, {32, 3, 16}};
+        best_ms = 1e30f;
+        for (const BCand& c : bc) {
+            Shape sh = bucket_default;
+            sh.stages = c.stages;
+            sh.tile_rows = c.stage_kb > 0 ? default_tile_rows(max_rb, c.stage_kb * 1024) : kMaxTileRows;
+            sh.warps = c.warps;
+            float ms = 0;
+            sel_status st = plan_time(p.get(), 1, sh, 2, &ms);
+            if (st == SEL_ERR_UNSUPPORTED) continue;
+            if (st != SEL_OK) return st;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = sh;
+                best_kernel = 1;
+            }
+        }
+    }
+    if (autotune && ctx->batch_kernel != 2) {
         struct Cand { int stage_kb, stages, ctas, warps, group; };
         const Cand cands[] = {{0, 3, 1, 16, 2},  {64, 3, 1, 16, 2}, {48, 4, 1, 16, 2}, {96, 2, 1, 16, 2},
                               {64, 3, 1, 16, 1}, {48, 4, 1, 16, 1}, {32, 3, 2, 8, 2},  {24, 4, 2, 8, 2},
                               {32, 3, 2, 8, 1},  {24, 4, 2, 8, 1},  {16, 4, 3, 8, 1},  {64, 3, 1, 8, 4},
                               {48, 4, 1, 8, 4}};
-        best_ms = 1e30f;
+        if (!bucket_ok) best_ms = 1e30f;
+        bool first = true;
         for (const Cand& c : cands) {
             Shape sh;
             sh.stages = c.stages;
@@ -990,16 +1162,27 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
             sh.warps = c.warps;
             sh.group = c.group;
             float ms = 0;
-            sel_status s = plan_time(p.get(), sh, 2, &ms);
+            sel_status s = plan_time(p.get(), 0, sh, first && bucket_ok ? 0 : 2, &ms);
             if (s == SEL_ERR_UNSUPPORTED) continue;
             if (s != SEL_OK) return s;
+            // the interpreter's other shapes are tried only when its default
+            // comes within 25 % of the bucket kernel's best
+            if (first && bucket_ok && ms > 1.25f * best_ms) break;
+            first = false;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = sh;
+                best_kernel = 0;
             }
         }
     }
-    {   // the shape the plan's launches use (reported by sel_batch_plan_info)
+    p->kernel = best_kernel;
+    if (best_kernel == 1) {   // the shape the plan's launches use (reported by sel_batch_plan_info)
+        ScanArgs a;
+        size_t smem = 0;
+        const sel_status rs = resolve_bucket(ctx, p.get(), p->tables, best, &a, &smem, &p->shape);
+        if (rs != SEL_OK) return rs;
+    } else {   // the shape the plan's launches use (reported by sel_batch_plan_info)
         const sel_status rs = resolve_shape(ctx, p->blob_bytes, p->n_progs, p->tables, best, &p->shape);
         if (rs != SEL_OK) return rs;
     }
@@ -1063,9 +1246,30 @@ extern "C" sel_status sel_batch_plan_variant(const sel_batch_plan* p, int32_t* c
     return SEL_OK;
 }
 
+extern "C" sel_status sel_batch_plan_kernel(const sel_batch_plan* p, int32_t* kernel) {
+    if (!p || !kernel) {
+        set_error("sel_batch_plan_kernel: bad arguments");
+        return SEL_ERR_INVALID_ARG;
+    }
+    *kernel = p->kernel;
+    return SEL_OK;
+}
+
+extern "C" sel_status sel_ctx_set_batch_kernel(sel_ctx* c, int32_t mode) {
+    if (!c || mode < 0 || mode > 2) {
+        set_error("sel_ctx_set_batch_kernel: mode must be 0, 1 or 2");
+        return SEL_ERR_INVALID_ARG;
+    }
+    c->batch_kernel = mode;
+    for (auto& kv : c->plans) sel_batch_plan_free(kv.second);   // cached plans were made under the old mode
+    c->plans.clear();
+    return SEL_OK;
+}
+
 extern "C" void sel_batch_plan_free(sel_batch_plan* p) {
     if (!p) return;
     if (p->graph) cudaGraphExecDestroy(p->graph);
+    if (p->d_bk_blob) cudaFree(p->d_bk_blob);
     if (p->d_blob) cudaFree(p->d_blob);
     if (p->d_counts) cudaFree(p->d_counts);
     delete p;

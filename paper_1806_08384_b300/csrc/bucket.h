@@ -1,0 +1,112 @@
+// bucket.h -- the column-bucket form of a batch of count probes, shared by
+// the host plan builder (bucket_plan.cpp) and the batched count kernel
+// (bucket_count.cu).
+//
+// Every leaf of a compiled program tests one column value against a value
+// set that is a union of intervals in the raw bit order of the column (an
+// int32 range is one cyclic interval of uint32, a float32 range at most two
+// intervals of its bit patterns, a set of codes a union of points).  For one
+// table of a batch, the starts and ends of all those intervals on a column
+// cut the column's raw domain into buckets; inside a bucket every leaf on
+// that column has one value.  A row then needs one bucket index per column
+// (a binary search over the sorted boundaries, or a linear count when there
+// are at most kBkLinear of them), and every leaf of every program follows
+// from those indices.
+//
+// Programs are taken to disjunctive normal form (OR of AND-groups of
+// possibly negated leaves, at most kBkGroups groups each).  The programs of a
+// table are cut into blocks of at most 64; in a block, program k owns the
+// 4-bit field k % 8 of group word k / 8, one bit per group.  For a block and
+// a column, the table gm[bucket][word] holds, for every group bit, whether
+// the group's leaves on that column hold in that bucket (1 when the group has
+// no leaf there).  A row's group bits are the AND over the block's columns of
+// those words (starting from the block's init mask, which clears unused
+// bits); a program holds on the row when any bit of its field is set.  The
+// per-field ORs are summed over the lane's rows and the warp (16-bit fields
+// of a warp reduction) into per-CTA counters.
+//
+// Several blocks on one table share the column's global bucket search; a
+// block whose leaves distinguish fewer buckets reads its gm table through a
+// remap of global to local bucket indices (uint16).
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sel.h"
+#include "kernels.h"
+
+namespace sel {
+
+constexpr int kBkGroups = 4;         // groups per program (one 4-bit field)
+constexpr int kBkProgsPerWord = 8;   // 8 fields of 4 bits
+constexpr int kBkMaxWords = 8;       // group words per block
+constexpr int kBkBlockProgs = kBkProgsPerWord * kBkMaxWords;   // 64 programs per block
+constexpr int kBkLinear = 8;         // at most this many boundaries: a linear count instead of a search
+constexpr uint32_t kBkIdentity = 0xFFFFFFFFu;   // remap_off: global bucket = local bucket
+
+// Search data of one referenced column of a table (16 bytes).
+struct BkSlot {
+    uint32_t bnd_off;   // byte offset of the sorted boundaries (uint32 or uint64 by the slot width),
+                        // padded with all-ones values to 2^steps - 1 entries when searched
+    uint32_t k;         // number of real boundaries; buckets 0..k
+    uint32_t half;      // binary search: 2^(steps - 1) (0 when k == 0); unused when linear
+    uint32_t linear;    // 1: bucket = number of boundaries <= x, counted over all k
+};
+
+// One block of at most 64 programs of a table.
+struct BkBlock {
+    uint32_t n_words;               // group words in use (1..8)
+    uint32_t stride;                // words per gm row: 1, 2, 4 or 8
+    uint32_t n_progs;               // programs in the block
+    uint32_t out_off;               // byte offset of the uint32 output indices of its programs
+    uint32_t n_used;                // columns the block reads
+    uint32_t pad[3];
+    uint32_t init[kBkMaxWords];     // group bits in use, per word
+    uint32_t used[kMaxSlots];       // slot of each column the block reads
+    uint32_t remap_off[kMaxSlots];  // per used column: uint16 global -> local bucket table, or kBkIdentity
+    uint32_t gm_off[kMaxSlots];     // per used column: gm table [local bucket][stride] uint32
+};
+
+struct BkTable {
+    uint32_t n_slots, n_blocks, block_off, max_buckets;   // block_off: byte offset of BkBlock[n_blocks]
+    BkSlot slot[kMaxSlots];
+};
+
+// Blob header; everything else is addressed by byte offsets from the blob start.
+struct BkHeader {
+    uint32_t n_tables;
+    uint32_t n_out;       // per-CTA counters (one per probe of the launch)
+    uint32_t gb_slots;    // >0: the kernel keeps global bucket indices of this many slots per warp in shared memory
+    uint32_t pad;
+    BkTable t[kMaxTables];
+};
+
+// The host side of a bucket plan: one blob for one launch (at most kMaxTables tables).
+struct BucketPlan {
+    std::vector<uint8_t> blob;   // BkHeader | boundaries | output indices | remaps | gm tables | BkBlock arrays
+    uint32_t n_out = 0;
+};
+
+struct Program;
+
+// One table of a batch: its referenced columns (slots) and the programs run on it.
+struct BkTableIn {
+    std::vector<uint32_t> slot_width;              // bytes per value of each slot (4 or 8)
+    std::vector<const Program*> progs;
+    std::vector<std::vector<int32_t>> slot_maps;   // per program: its slot -> the table's slot
+    std::vector<uint32_t> outs;                    // per program: index of its count
+};
+
+// Builds the blob; SEL_ERR_UNSUPPORTED (reason in *why) when the batch does
+// not fit the bucket form.
+sel_status build_bucket_plan(const std::vector<BkTableIn>& tables, BucketPlan* out, std::string* why);
+
+// Evaluates a plan on the host over host column data (cols[table][slot],
+// widths[table][slot]); adds each probe's count to counts[out].
+void bucket_eval_host(const BucketPlan& plan, const std::vector<std::vector<const uint8_t*>>& cols,
+                      const std::vector<std::vector<uint32_t>>& widths, const std::vector<int64_t>& n_rows,
+                      uint64_t* counts);
+
+}  // namespace sel

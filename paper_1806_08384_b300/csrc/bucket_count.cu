@@ -1,0 +1,322 @@
+// bucket_count.cu -- batched filtered COUNT over the column-bucket form of
+// the probes (layout in bucket.h): many selectivity probes of one query
+// optimisation (§3.1's COUNT per relation, batched) share one pass over every
+// referenced column, and every probe's predicate follows from one bucket
+// index per column and row.
+//
+// Warp roles and the tile pipeline are those of the interpreter's count scan
+// (count.cu): a producer warp fills `stages` shared-memory stages with column
+// tiles by bulk copies, W consumer warps take the tile's 256-row chunks in
+// rotation and release each stage as they finish.  A lane owns 8 rows of a
+// chunk (the same row mapping as the interpreter).  For each chunk a consumer
+// warp
+//   1. finds each row's bucket on every column the table's probes read (a
+//      branch-free binary search over the sorted boundaries in shared memory,
+//      or a linear count for a few boundaries); with several blocks of probes
+//      on the table the indices go to a per-warp shared buffer and are reused
+//      by every block;
+//   2. per block, ANDs the gm words of the row's buckets into the row's group
+//      words (8 rows x up to 8 words in registers);
+//   3. ORs each program's 4 group bits into the low bit of its field, sums the
+//      8 rows' fields (each field stays <= 8), reduces 16-bit fields over the
+//      warp and adds each program's chunk count to a per-CTA counter.
+// At the end each CTA adds its counters to the launch's counts.
+#include <algorithm>
+
+#include "bucket.h"
+#include "kernels.h"
+#include "scan.cuh"
+
+namespace sel {
+
+namespace {
+
+// Bucket index of each of the lane's 8 values on one column.
+template <typename T>
+__device__ __forceinline__ void bucket8(const BkSlot& sl, const T* __restrict__ bnd, const T (&v)[8],
+                                        uint32_t (&idx)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) idx[i] = 0;
+    if (sl.linear) {
+        for (uint32_t j = 0; j < sl.k; ++j) {
+            const T b = bnd[j];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) idx[i] += v[i] >= b ? 1u : 0u;
+        }
+        return;
+    }
+    for (uint32_t h = sl.half; h; h >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t j = idx[i] + h;
+            if (v[i] >= bnd[j - 1]) idx[i] = j;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) idx[i] = min(idx[i], sl.k);
+}
+
+// Bucket indices of the lane's 8 rows of the chunk at c0 on slot s.
+__device__ __forceinline__ void slot_buckets(const uint8_t* blob, const BkSlot& sl, uint32_t width, uint32_t col_addr,
+                                             uint32_t c0, uint32_t lane, uint32_t (&idx)[8]) {
+    if (width == 8) {
+        uint64_t v[8];
+        load8x64(col_addr, c0, lane, v);
+        bucket8<uint64_t>(sl, reinterpret_cast<const uint64_t*>(blob + sl.bnd_off), v, idx);
+    } else {
+        uint32_t v[8];
+        load8x32(col_addr, c0, lane, v);
+        bucket8<uint32_t>(sl, reinterpret_cast<const uint32_t*>(blob + sl.bnd_off), v, idx);
+    }
+}
+
+// One block of probes on the lane's 8 rows (vm: the rows that exist).  NW:
+// the block's gm row stride in words.  gbuf: the warp's bucket indices of
+// every slot (null: search here).
+template <int NW>
+__device__ __forceinline__ void eval_block(const uint8_t* blob, const BkTable& bt, const BkBlock& bk,
+                                           const TableArg& T, const uint32_t* s_off, uint32_t st_addr, uint32_t c0,
+                                           uint32_t lane, uint32_t vm, const uint16_t* gbuf,
+                                           unsigned long long* cnt) {
+    uint32_t R[8][NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t init = bk.init[w];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) R[i][w] = ((vm >> i) & 1u) ? init : 0u;
+    }
+    const uint32_t n_used = bk.n_used;
+    for (uint32_t u = 0; u < n_used; ++u) {
+        const uint32_t s = bk.used[u];
+        uint32_t b[8];
+        if (gbuf) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) b[i] = gbuf[(s * 8u + i) * 32u + lane];
+        } else {
+            slot_buckets(blob, bt.slot[s], T.width[s], st_addr + s_off[s], c0, lane, b);
+        }
+        const uint32_t ro = bk.remap_off[u];
+        if (ro != kBkIdentity) {
+            const uint16_t* rm = reinterpret_cast<const uint16_t*>(blob + ro);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) b[i] = rm[b[i]];
+        }
+        const uint32_t* gm = reinterpret_cast<const uint32_t*>(blob + bk.gm_off[u]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t* row = gm + b[i] * NW;
+            if (NW == 1) {
+                R[i][0] &= row[0];
+            } else if (NW == 2) {
+                const uint2 x = *reinterpret_cast<const uint2*>(row);
+                R[i][0] &= x.x;
+                R[i][NW > 1 ? 1 : 0] &= x.y;
+            } else {
+#pragma unroll
+                for (int q = 0; q < NW / 4; ++q) {
+                    const uint4 x = *reinterpret_cast<const uint4*>(row + 4 * q);
+                    R[i][4 * q + 0] &= x.x;
+                    R[i][4 * q + 1] &= x.y;
+                    R[i][4 * q + 2] &= x.z;
+                    R[i][4 * q + 3] &= x.w;
+                }
+            }
+        }
+    }
+    // per program: OR of its field's group bits, summed over rows and the warp
+    const uint32_t* outs = reinterpret_cast<const uint32_t*>(blob + bk.out_off);
+    const uint32_t n_words = bk.n_words, n_progs = bk.n_progs;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if ((uint32_t)w >= n_words) break;
+        uint32_t N = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            uint32_t t = R[i][w] | (R[i][w] >> 1);
+            t |= t >> 2;
+            N += t & 0x11111111u;   // field k's OR in bit 4k; a field's sum over 8 rows is <= 8
+        }
+        const uint32_t f0 = __reduce_add_sync(0xFFFFFFFFu, N & 0x000F000Fu);           // fields 0 and 4
+        const uint32_t f1 = __reduce_add_sync(0xFFFFFFFFu, (N >> 4) & 0x000F000Fu);    // 1 and 5
+        const uint32_t f2 = __reduce_add_sync(0xFFFFFFFFu, (N >> 8) & 0x000F000Fu);    // 2 and 6
+        const uint32_t f3 = __reduce_add_sync(0xFFFFFFFFu, (N >> 12) & 0x000F000Fu);   // 3 and 7
+        const uint32_t j = lane & 7u;
+        const uint32_t pair = (j & 3u) == 0 ? f0 : (j & 3u) == 1 ? f1 : (j & 3u) == 2 ? f2 : f3;
+        const uint32_t c = (pair >> (16u * (j >> 2))) & 0xFFFFu;
+        const uint32_t k = 8u * (uint32_t)w + j;
+        if (lane < 8 && k < n_progs && c) atomicAdd(&cnt[outs[k]], static_cast<unsigned long long>(c));
+    }
+}
+
+template <int W>
+__device__ __forceinline__ void consume_buckets(const ScanArgs& a, const uint8_t* blob, uint64_t* full, uint64_t* empty,
+                                                unsigned long long* cnt, uint8_t* stages, uint16_t* gbuf_all,
+                                                const uint32_t (&s_off)[kMaxTables][kMaxSlots], uint32_t* s_fail,
+                                                uint32_t warp, uint32_t lane) {
+    const BkHeader* hdr = reinterpret_cast<const BkHeader*>(blob);
+    const int64_t NB = gridDim.x;
+    const uint32_t S = a.stages;
+    uint16_t* gbuf = gbuf_all + (size_t)warp * hdr->gb_slots * 8u * 32u;
+    uint32_t rot = 0;
+    uint32_t s = 0, parity = 0;
+    for (int64_t k = 0;; ++k) {
+        const int64_t g = blockIdx.x + k * NB;
+        if (g >= a.total_tiles) break;
+        const int ti = find_table(a, g);
+        const TableArg& T = a.t[ti];
+        const BkTable& bt = hdr->t[ti];
+        const BkBlock* blocks = reinterpret_cast<const BkBlock*>(blob + bt.block_off);
+        const uint32_t valid = tile_valid(a, T, g);
+        const uint32_t n_chunks = (valid + kChunkRows - 1) / kChunkRows;
+        const uint32_t first = (warp + W - rot % W) % W;
+        const bool okw = __all_sync(0xFFFFFFFFu, mbar_wait_bounded(&full[s], parity));
+        if (!okw) {
+            if (lane == 0) {
+                atomicOr(a.err, 1u);
+                atomicOr(s_fail, 1u);
+                mbar_wait_bounded(&full[s], parity);
+            }
+            break;
+        }
+        if (*reinterpret_cast<volatile uint32_t*>(s_fail)) break;
+        const uint32_t st_addr = smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes);
+        const uint32_t n_blocks = bt.n_blocks;
+        for (uint32_t ch = first; ch < n_chunks; ch += W) {
+            const uint32_t c0 = ch * kChunkRows;
+            const uint32_t vm = (c0 + kChunkRows <= valid) ? 0xFFu : valid_mask(c0, lane, valid);
+            const uint16_t* gb = nullptr;
+            if (n_blocks > 1) {
+                for (uint32_t sl = 0; sl < bt.n_slots; ++sl) {
+                    uint32_t b[8];
+                    slot_buckets(blob, bt.slot[sl], T.width[sl], st_addr + s_off[ti][sl], c0, lane, b);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) gbuf[(sl * 8u + i) * 32u + lane] = (uint16_t)b[i];
+                }
+                gb = gbuf;
+            }
+            for (uint32_t bi = 0; bi < n_blocks; ++bi) {
+                const BkBlock& bk = blocks[bi];
+                switch (bk.stride) {
+                case 1: eval_block<1>(blob, bt, bk, T, s_off[ti], st_addr, c0, lane, vm, gb, cnt); break;
+                case 2: eval_block<2>(blob, bt, bk, T, s_off[ti], st_addr, c0, lane, vm, gb, cnt); break;
+                case 4: eval_block<4>(blob, bt, bk, T, s_off[ti], st_addr, c0, lane, vm, gb, cnt); break;
+                default: eval_block<8>(blob, bt, bk, T, s_off[ti], st_addr, c0, lane, vm, gb, cnt); break;
+                }
+            }
+        }
+        rot += n_chunks;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        if (++s == S) {
+            s = 0;
+            parity ^= 1u;
+        }
+    }
+}
+
+}  // namespace
+
+template <int W>
+__global__ void __launch_bounds__((W + 1) * 32, 1) bucket_count_kernel(const __grid_constant__ ScanArgs a) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ uint32_t s_off[kMaxTables][kMaxSlots];
+    __shared__ uint32_t s_fail;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t S = a.stages;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + S;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem + a.cnt_off);
+    uint8_t* stages = smem + a.stage_off;
+
+    if (tid == 0) {
+        for (uint32_t s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W);
+        }
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    for (uint32_t i = tid; i < kMaxTables * kMaxSlots; i += blockDim.x)
+        s_off[i / kMaxSlots][i % kMaxSlots] = a.t[i / kMaxSlots].slot_off[i % kMaxSlots];
+    for (uint32_t p = tid; p < a.n_progs; p += blockDim.x) cnt[p] = 0ull;
+    {
+        uint4* dst = reinterpret_cast<uint4*>(smem + a.prog_off);
+        const uint4* src = reinterpret_cast<const uint4*>(a.blob);
+        for (uint32_t i = tid; i < a.blob_bytes / 16u; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const int64_t NB = gridDim.x;
+
+    if (warp == W) {
+        const uint64_t pol = policy_evict_first();
+        uint32_t s = 0, phase = 0;
+        for (int64_t k = 0;; ++k) {
+            const int64_t g = blockIdx.x + k * NB;
+            if (g >= a.total_tiles) break;
+            if (k >= S) {
+                const bool ok = mbar_wait_bounded(&empty[s], phase ^ 1u);
+                if (!__all_sync(0xFFFFFFFFu, ok)) {
+                    if (lane == 0) {
+                        atomicOr(a.err, 1u);
+                        atomicOr(&s_fail, 1u);
+                    }
+                    break;
+                }
+            }
+            produce_tile(a, g, s, stages, full, pol, lane);
+            if (++s == S) {
+                s = 0;
+                phase ^= 1u;
+            }
+        }
+    } else {
+        consume_buckets<W>(a, smem + a.prog_off, full, empty, cnt, stages,
+                           reinterpret_cast<uint16_t*>(smem + a.aux_off), s_off, &s_fail, warp, lane);
+    }
+    __syncthreads();
+    if (s_fail) return;
+    for (uint32_t p = tid; p < a.n_progs; p += blockDim.x)
+        if (cnt[p]) atomicAdd(&a.counts[p], cnt[p]);
+}
+
+static inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+size_t bucket_layout(ScanArgs& a, int warps, uint32_t gb_bytes_per_warp) {
+    a.prog_in_smem = 1;
+    a.cnt_off = align_up(16u * a.stages, 16u);
+    a.prog_off = align_up(a.cnt_off + 8u * a.n_progs, 16u);
+    a.aux_off = align_up(a.prog_off + align_up(a.blob_bytes, 16u), 16u);
+    a.stage_off = align_up(a.aux_off + (uint32_t)warps * gb_bytes_per_warp, 128u);
+    return static_cast<size_t>(a.stage_off) + static_cast<size_t>(a.stages) * a.stage_bytes;
+}
+
+bool bucket_variant_ok(int warps) { return warps == 8 || warps == 16; }
+
+template <int W>
+static cudaError_t bucket_smem_limit(int optin, int* dyn_max) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, bucket_count_kernel<W>);
+    if (e != cudaSuccess) return e;
+    const int lim = optin - static_cast<int>(fa.sharedSizeBytes);
+    *dyn_max = *dyn_max < 0 ? lim : std::min(*dyn_max, lim);
+    return cudaFuncSetAttribute(bucket_count_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+cudaError_t bucket_kernel_max_smem(int optin, int* dyn_max) {
+    *dyn_max = -1;
+    cudaError_t e = bucket_smem_limit<8>(optin, dyn_max);
+    if (e == cudaSuccess) e = bucket_smem_limit<16>(optin, dyn_max);
+    return e;
+}
+
+cudaError_t launch_bucket_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps) {
+    if (warps == 8)
+        bucket_count_kernel<8><<<grid, 9 * 32, smem, st>>>(a);
+    else if (warps == 16)
+        bucket_count_kernel<16><<<grid, 17 * 32, smem, st>>>(a);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+}  // namespace sel

@@ -23,43 +23,6 @@
 
 namespace sel {
 
-__device__ __forceinline__ int find_table(const ScanArgs& a, int64_t g) {
-    int t = 0;
-    while (t + 1 < static_cast<int>(a.n_tables) && g >= a.t[t + 1].tile_begin) ++t;
-    return t;
-}
-
-__device__ __forceinline__ uint32_t tile_valid(const ScanArgs& a, const TableArg& T, int64_t g) {
-    const int64_t r0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows);
-    const int64_t left = T.n_rows - r0;
-    return static_cast<uint32_t>(left < static_cast<int64_t>(a.tile_rows) ? left : a.tile_rows);
-}
-
-// Producer warp: fills stage s with tile g (all 32 lanes call this).
-__device__ __forceinline__ void produce_tile(const ScanArgs& a, int64_t g, uint32_t s, uint8_t* stages,
-                                             uint64_t* full, uint64_t pol, uint32_t lane) {
-    const TableArg& T = a.t[find_table(a, g)];
-    const int64_t r0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows);
-    const uint32_t valid = tile_valid(a, T, g);
-    uint8_t* st = stages + static_cast<size_t>(s) * a.stage_bytes;
-    if (T.tma && valid == a.tile_rows && T.row_bytes > 0) {
-        if (lane == 0) {
-            mbar_arrive_expect_tx(&full[s], a.tile_rows * T.row_bytes);
-            for (uint32_t j = 0; j < T.n_slots; ++j)
-                bulk_g2s(st + T.slot_off[j], T.col[j] + r0 * T.width[j], a.tile_rows * T.width[j], &full[s], pol);
-        }
-    } else {
-        for (uint32_t j = 0; j < T.n_slots; ++j) {
-            const uint32_t words = valid * T.width[j] / 4u;
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(T.col[j] + r0 * T.width[j]);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(st + T.slot_off[j]);
-            for (uint32_t i = lane; i < words; i += 32) dst[i] = src[i];
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[s]);   // release: the copies above are visible to the waiters
-    }
-}
-
 // Consumer warps: evaluate every tile's chunk groups for all programs of the
 // tile's table.  blob is the program blob (shared or global memory); the
 // kernel calls this with a pointer the compiler can trace to shared memory

@@ -37,6 +37,7 @@ struct ScanArgs {
     uint32_t n_progs, instr_off, pool_off, blob_bytes;
     uint32_t tile_rows, stages, stage_bytes, prog_in_smem;
     uint32_t cnt_off, prog_off, stage_off, n_tables;
+    uint32_t aux_off, aux_pad;       // bucket kernel: per-warp bucket-index buffers (0 bytes otherwise)
     int64_t total_tiles;
     unsigned long long* counts;      // n_progs, zeroed before the launch
     unsigned int* err;               // bit 0: a bounded wait timed out
@@ -50,6 +51,14 @@ cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStre
 // Sets every scan variant's dynamic shared-memory limit to the opt-in maximum
 // minus its static shared memory; *dyn_max receives the smallest of them.
 cudaError_t scan_kernel_max_smem(int optin, int* dyn_max);
+
+// Batched count over the column-bucket form of the probes (bucket.h): a.blob
+// is the bucket blob (staged in shared memory), a.n_progs its counter count.
+// gb_bytes_per_warp: shared bytes of one warp's bucket-index buffer.
+size_t bucket_layout(ScanArgs& a, int warps, uint32_t gb_bytes_per_warp);
+bool bucket_variant_ok(int warps);
+cudaError_t launch_bucket_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps);
+cudaError_t bucket_kernel_max_smem(int optin, int* dyn_max);
 
 // ---------------------------------------------------------------------------
 // push-down (stable compaction with decoupled look-back)
