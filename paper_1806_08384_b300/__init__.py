@@ -636,8 +636,10 @@ def flatten(params: dict) -> np.ndarray:
     return np.concatenate([np.asarray(params[name], np.float32).ravel() for name, _ in PARAM_LAYOUT])
 
 
-def count_many(ctx: "Context", preds: Sequence[Predicate], table, chunk: int = 2048) -> List[int]:
-    """Exact counts of many predicates over one table, in batched launches of `chunk` probes."""
+def count_many(ctx: "Context", preds: Sequence[Predicate], table, chunk: int = 128) -> List[int]:
+    """Exact counts of many predicates over one table, in batched launches of
+    `chunk` probes (128: the bucket kernel's tables still leave room for
+    deep pipeline stages)."""
     T = Table.of(table)
     out = []
     for i in range(0, len(preds), chunk):

@@ -294,7 +294,7 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
 static sel_status resolve_bucket(sel_ctx* ctx, const sel_batch_plan* p, const std::vector<TableArg>& tables,
                                  const Shape& sh_in, ScanArgs* args, size_t* smem, Shape* used) {
     Shape sh = sh_in;
-    if (!bucket_variant_ok(sh.warps) || sh.stages < 1 || tables.size() > (size_t)kMaxTables) {
+    if (!bucket_variant_ok(sh.warps, sh.group) || sh.stages < 1 || tables.size() > (size_t)kMaxTables) {
         set_error("bucket scan: unsupported launch shape");
         return SEL_ERR_UNSUPPORTED;
     }
@@ -312,7 +312,8 @@ static sel_status resolve_bucket(sel_ctx* ctx, const sel_batch_plan* p, const st
         max_rb = std::max(max_rb, t.row_bytes);
         rows += t.n_rows;
     }
-    const size_t fixed = bucket_layout(a, sh.warps, p->bk_gb_bytes);
+    const uint32_t gb_bytes = p->bk_gb_bytes * (uint32_t)sh.group;   // bucket indices of a warp's chunk group
+    const size_t fixed = bucket_layout(a, sh.warps, gb_bytes);
     if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem_bucket) {
         set_error("bucket scan: %zu bytes of tables and counters leave no room for %d stages", fixed, sh.stages);
         return SEL_ERR_UNSUPPORTED;
@@ -348,7 +349,7 @@ static sel_status resolve_bucket(sel_ctx* ctx, const sel_batch_plan* p, const st
     }
     a.total_tiles = tiles;
     a.stage_bytes = ((uint32_t)sh.tile_rows * max_rb + 127u) / 128u * 128u;
-    *smem = bucket_layout(a, sh.warps, p->bk_gb_bytes);
+    *smem = bucket_layout(a, sh.warps, gb_bytes);
     if (*smem > (size_t)ctx->max_smem_bucket) {
         set_error("bucket scan: %zu bytes of shared memory needed", *smem);
         return SEL_ERR_UNSUPPORTED;
@@ -368,7 +369,7 @@ static sel_status run_bucket(sel_ctx* ctx, const sel_batch_plan* p, const Shape&
     int launches = 0;
     if (a.total_tiles > 0) {
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(a.total_tiles, (int64_t)ctx->n_sm * sh.ctas_per_sm));
-        cudaError_t e = launch_bucket_count(a, (int)grid, smem, ctx->stream, sh.warps);
+        cudaError_t e = launch_bucket_count(a, (int)grid, smem, ctx->stream, sh.warps, sh.group);
         if (e != cudaSuccess) return cuda_fail("bucket scan launch", e);
         ++launches;
         ctx->launches++;
@@ -1104,17 +1105,32 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     // default shape is the single-probe count's, with the context's overrides
     Shape best = single_shape(ctx, max_rb);
     int best_kernel = 0;
-    Shape bucket_default;   // 8 consumer warps, 3 stages that fill shared memory, or the context's overrides
+    Shape bucket_default;   // 16 consumer warps, 3 stages that fill shared memory, or the context's overrides
     bucket_default.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 3;
     bucket_default.ctas_per_sm = 1;
     bucket_default.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : kMaxTileRows;
     bucket_default.auto_tile = ctx->shape.tile_rows <= 0;
-    bucket_default.warps = bucket_variant_ok(ctx->shape.warps) ? ctx->shape.warps : 8;
+    bucket_default.warps = 16;
     bucket_default.group = 1;
-    if (bucket_ok) {   // tables too large for shared memory next to the stages: the interpreter
-        ScanArgs a;
-        size_t smem = 0;
-        const sel_status rs = resolve_bucket(ctx, p.get(), p->tables, bucket_default, &a, &smem, nullptr);
+    if (bucket_variant_ok(ctx->shape.warps, ctx->shape.group > 0 ? ctx->shape.group : 1)) {
+        bucket_default.warps = ctx->shape.warps;
+        bucket_default.group = ctx->shape.group > 0 ? ctx->shape.group : 1;
+    }
+    if (bucket_ok) {   // the first shape that fits (tables too large for any: the interpreter)
+        const int fallback[][3] = {{16, 1, 3}, {8, 1, 3}, {8, 1, 2}};   // warps, chunks per pass, stages
+        sel_status rs = SEL_ERR_UNSUPPORTED;
+        for (int c = -1; c < 3 && rs != SEL_OK; ++c) {
+            Shape sh = bucket_default;
+            if (c >= 0) {
+                sh.warps = fallback[c][0];
+                sh.group = fallback[c][1];
+                sh.stages = fallback[c][2];
+            }
+            ScanArgs a;
+            size_t smem = 0;
+            rs = resolve_bucket(ctx, p.get(), p->tables, sh, &a, &smem, nullptr);
+            if (rs == SEL_OK) bucket_default = sh;
+        }
         if (rs == SEL_OK) {
             best = bucket_default;
             best_kernel = 1;
@@ -1126,14 +1142,16 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     }
     float best_ms = 0.f;
     if (autotune && bucket_ok) {
-        struct BCand { int stage_kb, stages, warps; };
-        const BCand bc[] = {{0, 3, 8}, {0, 2, 8}, {0, 4, 8}, {48, 3, 8}, {32, 4, 8}, {0, 3, 16}, {32, 3, 16}};
+        struct BCand { int stage_kb, stages, warps, group; };
+        const BCand bc[] = {{0, 3, 16, 1}, {0, 3, 16, 2}, {0, 3, 8, 2}, {0, 2, 16, 1}, {0, 4, 16, 2},
+                            {32, 4, 16, 1}, {0, 3, 8, 1}, {0, 2, 8, 1}};
         best_ms = 1e30f;
         for (const BCand& c : bc) {
             Shape sh = bucket_default;
             sh.stages = c.stages;
             sh.tile_rows = c.stage_kb > 0 ? default_tile_rows(max_rb, c.stage_kb * 1024) : kMaxTileRows;
             sh.warps = c.warps;
+            sh.group = c.group;
             float ms = 0;
             sel_status st = plan_time(p.get(), 1, sh, 2, &ms);
             if (st == SEL_ERR_UNSUPPORTED) continue;

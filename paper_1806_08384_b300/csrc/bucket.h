@@ -9,9 +9,10 @@
 // table of a batch, the starts and ends of all those intervals on a column
 // cut the column's raw domain into buckets; inside a bucket every leaf on
 // that column has one value.  A row then needs one bucket index per column
-// (a binary search over the sorted boundaries, or a linear count when there
-// are at most kBkLinear of them), and every leaf of every program follows
-// from those indices.
+// (a cell table indexed by the value's high bits followed by at most 3
+// compares, a binary search over the sorted boundaries, or a linear count
+// when there are few of them), and every leaf of every program follows from
+// those indices.
 //
 // Programs are taken to disjunctive normal form (OR of AND-groups of
 // possibly negated leaves, at most kBkGroups groups each).  The programs of a
@@ -43,26 +44,44 @@ constexpr int kBkGroups = 4;         // groups per program (one 4-bit field)
 constexpr int kBkProgsPerWord = 8;   // 8 fields of 4 bits
 constexpr int kBkMaxWords = 8;       // group words per block
 constexpr int kBkBlockProgs = kBkProgsPerWord * kBkMaxWords;   // 64 programs per block
-constexpr int kBkLinear = 8;         // at most this many boundaries: a linear count instead of a search
+constexpr int kBkLinear = 8;         // at most this many boundaries: a linear count can replace a search
+constexpr int kBkMaxCells = 2048;    // cells of a BK_CELLS column
+constexpr int kBkMaxOcc = 3;         // boundaries per cell for BK_CELLS
 constexpr uint32_t kBkIdentity = 0xFFFFFFFFu;   // remap_off: global bucket = local bucket
 
-// Search data of one referenced column of a table (16 bytes).
-struct BkSlot {
-    uint32_t bnd_off;   // byte offset of the sorted boundaries (uint32 or uint64 by the slot width),
-                        // padded with all-ones values to 2^steps - 1 entries when searched
-    uint32_t k;         // number of real boundaries; buckets 0..k
-    uint32_t half;      // binary search: 2^(steps - 1) (0 when k == 0); unused when linear
-    uint32_t linear;    // 1: bucket = number of boundaries <= x, counted over all k
+// How a row's bucket on one column is found (BkSlot.mode).
+enum BkMode : uint32_t {
+    BK_LINEAR = 0,   // count the k boundaries <= x (k <= kBkLinear)
+    BK_BINARY = 1,   // branch-free binary search over 2^steps - 1 padded boundaries
+    BK_CELLS = 2,    // cell c = (x - lo) >> shift gives the buckets before the cell; at most occ
+                     // boundaries inside one cell are then compared with x
 };
 
+// Search data of one referenced column of a table (48 bytes).
+struct BkSlot {
+    uint32_t bnd_off;   // byte offset of the sorted boundaries (uint32 or uint64 by the slot width),
+                        // padded with all-ones values (to 2^steps - 1 entries when searched, by occ
+                        // entries for cells)
+    uint32_t k;         // number of real boundaries; buckets 0..k
+    uint32_t half;      // BK_BINARY: 2^(steps - 1)
+    uint32_t mode;      // BkMode
+    uint32_t cells_off; // BK_CELLS: byte offset of n_cells uint16 counts of boundaries before each cell
+    uint32_t n_cells;
+    uint32_t shift;
+    uint32_t occ;       // largest number of boundaries in one cell
+    uint64_t lo;        // BK_CELLS: the smallest boundary
+    uint64_t pad;
+};
 // One block of at most 64 programs of a table.
 struct BkBlock {
     uint32_t n_words;               // group words in use (1..8)
-    uint32_t stride;                // words per gm row: 1, 2, 4 or 8
+    uint32_t nw;                    // words read per gm row: 1, 2, 4 or 8
     uint32_t n_progs;               // programs in the block
     uint32_t out_off;               // byte offset of the uint32 output indices of its programs
     uint32_t n_used;                // columns the block reads
-    uint32_t pad[3];
+    uint32_t stride;                // words between gm rows: nw, or 12 for 8 (48-byte rows start on
+                                    // all 8 16-byte bank groups, so random rows conflict less)
+    uint32_t pad[2];
     uint32_t init[kBkMaxWords];     // group bits in use, per word
     uint32_t used[kMaxSlots];       // slot of each column the block reads
     uint32_t remap_off[kMaxSlots];  // per used column: uint16 global -> local bucket table, or kBkIdentity

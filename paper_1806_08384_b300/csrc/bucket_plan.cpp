@@ -400,29 +400,74 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
                 L.member[j] = m ? 1 : 0;
             }
         }
-        // search data
+        // search data: a linear count for up to 4 boundaries, a direct table
+        // when every cell is one value, cells when at most kBkMaxOcc
+        // boundaries share a cell, else a linear count (up to kBkLinear) or a
+        // binary search
         for (uint32_t s = 0; s < bt.n_slots; ++s) {
             const uint32_t w = T.slot_width[s];
+            const std::vector<uint64_t>& B = bnd[s];
             BkSlot& sl = bt.slot[s];
-            sl.k = (uint32_t)bnd[s].size();
-            sl.linear = sl.k <= (uint32_t)kBkLinear ? 1u : 0u;
+            sl.k = (uint32_t)B.size();
             size_t n_entries = sl.k;
-            if (!sl.linear) {
-                uint32_t steps = 0;
-                while (((size_t)1 << steps) < (size_t)sl.k + 1) ++steps;
-                sl.half = 1u << (steps - 1);
-                n_entries = ((size_t)1 << steps) - 1;
+            std::vector<uint16_t> cells;
+            if (sl.k <= 4) {   // 2 instructions per boundary and row (measured faster than cells up to 4)
+                sl.mode = BK_LINEAR;
+            } else {
+                const uint64_t span = B.back() - B.front();
+                uint32_t shift = 0;
+                while ((span >> shift) >= (uint64_t)kBkMaxCells) ++shift;
+                const uint32_t n_cells = (uint32_t)(span >> shift) + 1;
+                std::vector<uint32_t> occ(n_cells, 0);
+                for (uint64_t b : B) ++occ[(b - B.front()) >> shift];
+                const uint32_t mx = *std::max_element(occ.begin(), occ.end());
+                if (shift == 0) {
+                    // every cell is one value: the table holds that value's bucket, no compares
+                    sl.mode = BK_CELLS;
+                    sl.lo = B.front();
+                    sl.shift = 0;
+                    sl.n_cells = n_cells;
+                    sl.occ = 0;
+                    cells.resize(n_cells);
+                    uint32_t upto = 0;
+                    for (uint32_t c = 0; c < n_cells; ++c) {
+                        upto += occ[c];
+                        cells[c] = (uint16_t)upto;
+                    }
+                } else if (mx <= (uint32_t)kBkMaxOcc) {
+                    sl.mode = BK_CELLS;
+                    sl.lo = B.front();
+                    sl.shift = shift;
+                    sl.n_cells = n_cells;
+                    sl.occ = mx;
+                    cells.resize(n_cells);
+                    uint32_t before = 0;
+                    for (uint32_t c = 0; c < n_cells; ++c) {
+                        cells[c] = (uint16_t)before;
+                        before += occ[c];
+                    }
+                    n_entries = (size_t)sl.k + mx;
+                } else if (sl.k <= (uint32_t)kBkLinear) {
+                    sl.mode = BK_LINEAR;
+                } else {
+                    sl.mode = BK_BINARY;
+                    uint32_t steps = 0;
+                    while (((size_t)1 << steps) < (size_t)sl.k + 1) ++steps;
+                    sl.half = 1u << (steps - 1);
+                    n_entries = ((size_t)1 << steps) - 1;
+                }
             }
             std::vector<uint8_t> raw(std::max<size_t>(n_entries, 1) * w, 0xFF);
-            for (size_t j = 0; j < bnd[s].size(); ++j) {
+            for (size_t j = 0; j < B.size(); ++j) {
                 if (w == 8)
-                    std::memcpy(raw.data() + 8 * j, &bnd[s][j], 8);
+                    std::memcpy(raw.data() + 8 * j, &B[j], 8);
                 else {
-                    const uint32_t v = (uint32_t)bnd[s][j];
+                    const uint32_t v = (uint32_t)B[j];
                     std::memcpy(raw.data() + 4 * j, &v, 4);
                 }
             }
             sl.bnd_off = (uint32_t)append(blob, raw.data(), raw.size());
+            if (!cells.empty()) sl.cells_off = (uint32_t)append(blob, cells.data(), cells.size() * 2);
             bt.max_buckets = std::max(bt.max_buckets, sl.k + 1);
         }
         // blocks
@@ -436,7 +481,8 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
             const size_t p0 = (size_t)bi * kBkBlockProgs, p1 = std::min(np, p0 + kBkBlockProgs);
             bk.n_progs = (uint32_t)(p1 - p0);
             bk.n_words = (bk.n_progs + kBkProgsPerWord - 1) / kBkProgsPerWord;
-            bk.stride = bk.n_words <= 1 ? 1 : bk.n_words <= 2 ? 2 : bk.n_words <= 4 ? 4 : 8;
+            bk.nw = bk.n_words <= 1 ? 1 : bk.n_words <= 2 ? 2 : bk.n_words <= 4 ? 4 : 8;
+            bk.stride = bk.nw == 8 ? 12 : bk.nw;
             std::vector<uint32_t> outs(bk.n_progs);
             for (size_t k = 0; k < bk.n_progs; ++k) {
                 outs[k] = T.outs[p0 + k];
@@ -517,9 +563,17 @@ uint32_t host_bucket(const std::vector<uint8_t>& blob, const BkSlot& sl, uint32_
         return rd<uint32_t>(blob, sl.bnd_off + 4 * (size_t)j);
     };
     uint32_t idx = 0;
-    if (sl.linear) {
+    if (sl.mode == BK_LINEAR) {
         for (uint32_t j = 0; j < sl.k; ++j) idx += x >= bnd(j) ? 1u : 0u;
         return idx;
+    }
+    if (sl.mode == BK_CELLS) {
+        if (x < sl.lo) return 0;
+        const uint64_t c = std::min<uint64_t>((x - sl.lo) >> sl.shift, sl.n_cells - 1);
+        const uint32_t base = rd<uint16_t>(blob, sl.cells_off + 2 * (size_t)c);
+        idx = base;
+        for (uint32_t t = 0; t < sl.occ; ++t) idx += x >= bnd(base + t) ? 1u : 0u;
+        return std::min(idx, sl.k);
     }
     for (uint32_t h = sl.half; h; h >>= 1)
         if (x >= bnd(idx + h - 1)) idx += h;

@@ -54,10 +54,11 @@ cudaError_t scan_kernel_max_smem(int optin, int* dyn_max);
 
 // Batched count over the column-bucket form of the probes (bucket.h): a.blob
 // is the bucket blob (staged in shared memory), a.n_progs its counter count.
-// gb_bytes_per_warp: shared bytes of one warp's bucket-index buffer.
+// gb_bytes_per_warp: shared bytes of one warp's bucket-index buffer.  Variants:
+// 8 or 16 consumer warps, 1 or 2 chunks per pass.
 size_t bucket_layout(ScanArgs& a, int warps, uint32_t gb_bytes_per_warp);
-bool bucket_variant_ok(int warps);
-cudaError_t launch_bucket_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps);
+bool bucket_variant_ok(int warps, int group);
+cudaError_t launch_bucket_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group);
 cudaError_t bucket_kernel_max_smem(int optin, int* dyn_max);
 
 // ---------------------------------------------------------------------------

@@ -155,3 +155,29 @@ def test_programs_beyond_four_groups_are_refused():
         _host_counts([sel.Predicate(T, wide)], T)
     assert e.value.status == sel.SEL_ERR_UNSUPPORTED
     assert "groups" in str(e.value)
+
+
+def test_spread_boundaries_and_extreme_values():
+    """Many ranges spread over the whole int32 and float32 domains (the cell
+    search: a cell table over the boundaries' span, at most 3 boundaries per
+    cell) with data at and around every boundary and at the type's ends."""
+    rng = np.random.default_rng(21)
+    lo = rng.integers(-2 ** 31, 2 ** 31 - 2 ** 24, 60)
+    hi = lo + rng.integers(0, 2 ** 24, 60)
+    flo = np.sort(rng.normal(0, 3, (60, 2)).astype(np.float32), axis=1)
+    edge_i = np.concatenate([lo, hi, lo - 1, hi + 1, [-2 ** 31, -1, 0, 1, 2 ** 31 - 1]]).clip(-2 ** 31, 2 ** 31 - 1)
+    ivals = np.concatenate([edge_i, rng.integers(-2 ** 31, 2 ** 31, 4000)]).astype(np.int32)
+    edge_f = np.concatenate([flo.ravel(), np.nextafter(flo.ravel(), np.float32(np.inf)),
+                             np.nextafter(flo.ravel(), np.float32(-np.inf)),
+                             np.array([0.0, -0.0, np.inf, -np.inf, np.nan], np.float32)])
+    fvals = np.concatenate([edge_f, rng.normal(0, 3, ivals.shape[0] - edge_f.shape[0])]).astype(np.float32)
+    specs = [dg.ColumnSpec("i", "i32", "uniform", 0, 4), dg.ColumnSpec("f", "f32", "uniform", 0.0, 1.0)]
+    t = dg.Table("spread", [dg.Column(specs[0], torch.from_numpy(ivals), None),
+                            dg.Column(specs[1], torch.from_numpy(fvals), None)])
+    ot, T = oracle.OTable.from_table(t), sel.Table(t.columns)
+    trees = [p_between(0, int(a), int(b)) for a, b in zip(lo, hi)]
+    trees += [p_between(1, float(a), float(b)) for a, b in flo]
+    trees += [p_or(p_between(0, int(lo[k]), int(hi[k])), p_not(p_between(1, float(flo[k][0]), float(flo[k][1]))))
+              for k in range(10)]
+    got, _ = _host_counts([sel.Predicate(T, tr) for tr in trees], T)
+    assert got == [oracle.count(ot, tr) for tr in trees]

@@ -42,8 +42,12 @@ def test_random_trees_tiny(dev, n):
     rng = np.random.default_rng(500 + n)
     fit = _fits(sel.Table(t.columns), [dg.random_tree(t, rng, depth=3) for _ in range(150)])
     preds = [sel.Predicate(T, tr) for tr in fit]
-    ctx = _bucket_ctx()
-    assert _run(ctx, preds, [T] * len(preds)) == [oracle.count(ot, tr) for tr in fit]
+    want = [oracle.count(ot, tr) for tr in fit]
+    for variant in ((16, 1), (8, 2)):
+        ctx = _bucket_ctx()
+        ctx.set_scan_variant(*variant)
+        assert _run(ctx, preds, [T] * len(preds)) == want
+        assert _run(ctx, preds[:40], [T] * 40) == want[:40]    # one block (no bucket buffer)
 
 
 def test_edge_values(dev):
@@ -61,28 +65,31 @@ def medium():
     return t, oracle.OTable.from_table(t), sel.Table(t.columns)
 
 
-@pytest.mark.parametrize("shape", [(256, 2, 8), (768, 3, 8), (2048, 4, 16), (0, 0, 0), (0, 2, 16), (16384, 3, 8)])
+@pytest.mark.parametrize("shape", [(256, 2, 8, 1), (768, 3, 8, 2), (2048, 4, 16, 1), (0, 0, 0, 0), (0, 2, 16, 2),
+                                   (16384, 3, 8, 1), (1280, 3, 16, 2), (256, 3, 8, 2)])
 def test_config2_shapes(medium, shape):
-    """Ragged last tile (n = 300,001), tiles with fewer chunks than warps, every ring depth."""
+    """Ragged last tile (n = 300,001), tiles with fewer chunks than warps, every
+    ring depth, one or two chunks per pass (an odd chunk count leaves the last
+    group with one chunk)."""
     t, ot, T = medium
     ctx = _bucket_ctx()
-    tile, stages, warps = shape
+    tile, stages, warps, group = shape
     ctx.set_scan_shape(tile, stages, 0)
     if warps:
-        ctx.set_scan_variant(warps, 1)
+        ctx.set_scan_variant(warps, group)
     trees = [dg.config2_predicate(s, seed=k) for s in dg.CONFIG2_TARGETS for k in range(3)]
     preds = [sel.Predicate(T, tr) for tr in trees]
     assert _run(ctx, preds, [T] * len(preds)) == [oracle.count(ot, tr, threads=THREADS) for tr in trees]
 
 
-@pytest.mark.parametrize("warps", [8, 16])
-def test_several_blocks_on_one_table(dev, warps):
+@pytest.mark.parametrize("variant", [(8, 1), (16, 1), (8, 2), (16, 2)])
+def test_several_blocks_on_one_table(dev, variant):
     """256 probes (4 blocks of 64) and 300 random estimator-workload probes (5 blocks)."""
     t = dg.config5_table(n=1_000_003, device=dev)
     ot = oracle.OTable.from_table(t)
     T = sel.Table(t.columns)
     ctx = _bucket_ctx()
-    ctx.set_scan_variant(warps, 1)
+    ctx.set_scan_variant(*variant)
     trees = dg.config5_predicates(256, seed=4)
     preds = [sel.Predicate(T, tr) for tr in trees]
     assert _run(ctx, preds, [T] * len(preds)) == [oracle.count(ot, tr, threads=THREADS) for tr in trees]
