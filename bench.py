@@ -1,24 +1,31 @@
 #!/usr/bin/env python3
-"""Benchmark: exact selectivity computation and selection push-down on the
-300M-row, 8-column synthetic fact table (the table of configs 2 and 4).
+"""Benchmark: exact selectivity computation and selection push-down.
 
-One step is one optimiser pass of the method over that table (Ch3; Algorithm 1
-Execute for one relation, with every probe of the pass):
-  a1  compile the probe predicates (OR of 3 ANDs mixing BETWEEN, 5-value IN and
-      prefix LIKE; selectivities 1e-4 .. 0.5);
-  a5  their exact counts in one batched scan (persistent kernel, CUDA graph,
-      autotuned shape) -- a2 is the same kernel with one program;
+Headline workload (the largest single-GPU configuration): the 1.2B-row,
+6-column synthetic table of config 5 (24 B/row, 28.8 GB resident in HBM) with
+its 256 seeded probe predicates (OR of 1-3 ANDs of 1-3 clauses; selectivities
+log-spaced in [1e-6, 0.9]).  One step is one optimiser pass of the method over
+that table (Ch3; Algorithm 1 Execute for the relation, with every probe):
+  a1  compile the 256 probe predicates;
+  a5  their exact counts in one batched scan (the column-bucket kernel, one
+      graph launch, autotuned shape) -- a2 is the single-probe count;
   a3  maxSize = floor(n * 0.05): probes above it are not pushed down;
-  a4  push-down (fused count + stable compaction) of 4 projected columns for
+  a4  push-down (fused count + stable compaction) of 3 projected columns for
       every probe at or under maxSize;
-  a6-a9  the learned estimator on the same table: features and the tensor-core
-      forward pass of 4096 held-out probes, the uncertainty gate, and one
-      training minibatch (the model is trained before the timed region on
-      exact counts from the count kernel; the gate's exact fallback is the a5
-      scan, timed separately as exact_ms_per_estimate).
+  a6-a9  the learned estimator on config 4's table (config 2's 300M-row
+      table): features and the tensor-core forward pass of 4096 held-out
+      probes, the uncertainty gate, and one training minibatch (the model is
+      trained before the timed region on exact counts from the count kernel,
+      tau is chosen on a validation split; the gate's exact fallback is the
+      batched scan, timed separately as exact_ms_per_estimate).
 value = algorithmic bytes of all scans of a step / device time of the step.
 
+Other configurations are reported beside it: config 2's probes (batched vs
+one launch per probe, single counts, push-downs at every selectivity),
+config 3's star schema, config 1's latency.
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       python bench.py --estimator-curve     (config 4's learning curve: 20k / 200k / 2M pairs)
 """
 from __future__ import annotations
 
@@ -43,6 +50,8 @@ import datagen as dg  # noqa: E402
 METRIC = "exact-count scan GB/s (% HBM peak), ms/estimate; surrogate p95 q-error"
 MAX_SELECTIVITY = 0.05          # PUSH_DOWN_MAX_SELECTIVITY of Algorithm 1 (ratio form)
 WIDTH = {"i32": 4, "i64": 8, "f32": 4, "date": 4, "dict": 4}
+CFG5_ROWS = 1_200_000_000
+CFG2_ROWS = 300_000_000
 
 
 def load_peaks():
@@ -148,10 +157,6 @@ class ClockSampler:
 # the workload
 # ----------------------------------------------------------------------------
 
-def probe_trees(seed=0):
-    return [dg.config2_predicate(s, seed=seed) for s in dg.CONFIG2_TARGETS]
-
-
 def algorithmic_bytes(types, n, trees, counts, accepted, proj):
     """Bytes a step must move at least: each predicate column of the batched
     scan once, and for each push-down its predicate columns, the projected
@@ -169,13 +174,16 @@ def algorithmic_bytes(types, n, trees, counts, accepted, proj):
 
 
 class Workload:
+    """Config 5: 1.2B rows x 6 columns, 256 probes, push-down of 3 columns."""
+
     def __init__(self, n_rows: int, device, seed_offset: int = 0):
-        self.table = dg.gen_table("cfg2" if seed_offset == 0 else f"cfg2_r{seed_offset}", dg.config2_specs(),
-                                  n_rows, device, cfg_label="cfg2" if seed_offset == 0 else None)
+        label = "cfg5" if seed_offset == 0 else f"cfg5_r{seed_offset}"
+        self.table = dg.gen_table(label, dg.config5_specs(), n_rows, device,
+                                  cfg_label="cfg5" if seed_offset == 0 else None)
         self.n = n_rows
         self.types = [c.type for c in self.table.columns]
-        self.trees = probe_trees()
-        self.proj = [self.table.index(c) for c in dg.CONFIG2_PROJECTION]
+        self.trees = dg.config5_predicates()
+        self.proj = [self.table.index(c) for c in dg.CONFIG5_PROJECTION]
         self.max_rows = int(math.floor(n_rows * MAX_SELECTIVITY))
 
 
@@ -195,8 +203,10 @@ class OurStep:
         self.host_out = None
         # the batch plan (autotuned, graph-captured) is created and cached by the first call
         preds = [sel.Predicate(self.T, t) for t in w.trees]
+        t0 = time.perf_counter()
         self.ctx.count_batch_async(preds, [self.T] * len(preds), self.counts_dev)
         self.ctx.synchronize()
+        self.plan_s = time.perf_counter() - t0
 
     def run(self, record=False, e2e=False):
         w, sel, ctx = self.w, self.sel, self.ctx
@@ -239,65 +249,95 @@ def q_error(est, true):
     return np.maximum(e / t, t / e)
 
 
-class Surrogate:
-    """a6-a9 on the same table: the learned estimator, trained before the timed
-    region on exact counts from the count kernel (a5), then inside every timed
-    step: featurize + forward of a batch of probes, the gate decision, and one
-    training minibatch.  The gate's exact fallback is the batched scan of a5;
-    its cost per estimate is timed separately."""
+def estimator_workload(n, seed_label="bench_estimator"):
+    rng = np.random.default_rng(dg.mix_seed(seed_label))
+    specs = dg.config2_specs()
+    return [dg.random_dnf_predicate(specs, rng) for _ in range(n)]
 
-    def __init__(self, step: "OurStep", n_train=20_000, n_eval=4096, sample_rows=4096):
-        sel, T, ctx = step.sel, step.T, step.ctx
-        self.sel, self.T, self.ctx = sel, T, ctx
-        rng = np.random.default_rng(dg.mix_seed("bench_estimator"))
-        specs = dg.config2_specs()
-        trees = [dg.random_dnf_predicate(specs, rng) for _ in range(n_train + n_eval)]
+
+def train_and_gate(sel, ctx, T, preds, counts, n_train, n_val, n_test, sample_rows=4096):
+    """Config 4: train on n_train labelled probes, choose tau on the next
+    n_val (the largest tau whose accepted estimates keep the 95th-percentile
+    q-error <= 2), score the n_test after them."""
+    model = sel.Estimator(ctx, T, sample_rows=sample_rows, seed=dg.MASTER_SEED)
+    epochs = max(4, min(40, 800_000 // max(1, n_train)))
+    cfg = sel.train_cfg(epochs=epochs, batch=256, lr=1e-3, seed=1)
+    t0 = time.perf_counter()
+    loss = model.train(preds[:n_train], counts[:n_train], cfg)
+    train_s = time.perf_counter() - t0
+
+    def outputs(lo, hi):
+        pl = sel.PredicateList(preds[lo:hi])
+        feat, ok = model.featurize(pl)
+        out = model.forward(feat).cpu().numpy().astype(np.float64)
+        okm = ok.cpu().numpy().astype(bool)
+        est = np.maximum(np.expm1(out[:, 0]), 0.0)
+        sig = np.where(okm, np.exp(0.5 * np.clip(out[:, 1], -8, 8)), np.inf)
+        return pl, feat, okm, est, sig
+    _, _, okv, est_v, sig_v = outputs(n_train, n_train + n_val)
+    tau, answered_val = sel.choose_tau(sig_v, est_v, counts[n_train:n_train + n_val])
+    pl, feat, okt, est_t, sig_t = outputs(n_train + n_val, n_train + n_val + n_test)
+    exact_t = counts[n_train + n_val:n_train + n_val + n_test]
+    q = q_error(est_t, exact_t)
+    acc = okt & (sig_t <= tau)
+    from paper_1806_08384_b300 import baselines
+    ind = baselines.independence_selectivity(feat.float().cpu().numpy()) * T.n_rows
+    qi = q_error(ind, exact_t)
+    gated = np.where(acc, est_t, exact_t.astype(np.float64))
+    qg = q_error(gated, exact_t)
+    quality = {
+        "n_train": n_train, "n_val": n_val, "n_test": n_test, "epochs": epochs,
+        "train_seconds": round(train_s, 2), "final_train_loss": round(loss, 4),
+        "q_error_p50": round(float(np.median(q[okt])), 3), "q_error_p95": round(float(np.percentile(q[okt], 95)), 3),
+        "tau": round(float(tau), 4), "tau_rule": "largest tau with 95th-percentile q-error <= 2 on the validation split",
+        "answered_fraction_validation": round(answered_val, 3),
+        "gated_answered_fraction": round(float(acc.mean()), 3),
+        "gated_accepted_q_error_p50": round(float(np.median(q[acc])), 3) if acc.any() else None,
+        "gated_accepted_q_error_p95": round(float(np.percentile(q[acc], 95)), 3) if acc.any() else None,
+        "gated_all_q_error_p95": round(float(np.percentile(qg, 95)), 3),
+        "independence_q_error_p50": round(float(np.median(qi[okt])), 3),
+        "independence_q_error_p95": round(float(np.percentile(qi[okt], 95)), 3)}
+    return model, tau, pl, quality, okt
+
+
+class Surrogate:
+    """a6-a9 on config 4's table: the learned estimator, trained before the
+    timed region on exact counts from the count kernel (a5), tau chosen on a
+    validation split; inside every timed step: featurize + forward of the
+    held-out test probes, the gate decision, and one training minibatch.  The
+    gate's exact fallback is the batched scan; its cost per estimate is timed
+    separately."""
+
+    def __init__(self, sel, ctx, table, n_train=200_000, n_val=20_000, n_test=4096, sample_rows=4096):
+        self.sel, self.ctx = sel, ctx
+        T = sel.Table(table.columns)
+        self.T = T
+        trees = estimator_workload(n_train + n_val + n_test)
         preds = [sel.Predicate(T, t) for t in trees]
         t0 = time.perf_counter()
         counts = np.array(sel.count_many(ctx, preds, T), dtype=np.uint64)
         self.label_s = time.perf_counter() - t0
-        self.model = sel.Estimator(ctx, T, sample_rows=sample_rows, seed=dg.MASTER_SEED)
-        self.cfg = sel.train_cfg(epochs=40, batch=256, lr=1e-3, seed=1)
-        t0 = time.perf_counter()
-        self.final_loss = self.model.train(preds[:n_train], counts[:n_train], self.cfg)
-        self.train_s = time.perf_counter() - t0
-        self.n_train = n_train
-        self.eval_preds, self.eval_counts = sel.PredicateList(preds[n_train:]), counts[n_train:]
-        feat, ok = self.model.featurize(self.eval_preds)
-        out = self.model.forward(feat).cpu().numpy()
-        okm = ok.cpu().numpy().astype(bool)
-        sig = np.exp(0.5 * np.clip(out[:, 1], -8, 8))
-        self.tau = float(np.median(sig[okm]))
-        acc = okm & (sig <= self.tau)
-        q = q_error(np.expm1(out[:, 0]), self.eval_counts)
-        from paper_1806_08384_b300 import baselines
-        ind = baselines.independence_selectivity(feat.float().cpu().numpy()) * T.n_rows
-        qi = q_error(ind, self.eval_counts)
-        self.traditional = self.traditional_baselines(step, trees[n_train:], okm)
-        self.quality = {
-            "q_error_p50": round(float(np.median(q[okm])), 3), "q_error_p95": round(float(np.percentile(q[okm], 95)), 3),
-            "gated_tau": round(self.tau, 4), "gated_answered_fraction": round(float(acc.mean()), 3),
-            "gated_q_error_p50": round(float(np.median(q[acc])), 3),
-            "gated_q_error_p95": round(float(np.percentile(q[acc], 95)), 3),
-            "independence_q_error_p50": round(float(np.median(qi[okm])), 3),
-            "independence_q_error_p95": round(float(np.percentile(qi[okm], 95)), 3)}
-        # the step's training minibatch: the first 256 labelled probes
+        self.n_labels = len(preds)
+        self.model, self.tau, self.eval_preds, self.quality, okt = train_and_gate(
+            sel, ctx, T, preds, counts, n_train, n_val, n_test, sample_rows)
+        self.eval_counts = counts[n_train + n_val:]
+        self.traditional = self.traditional_baselines(table, trees[n_train + n_val:], okt)
         self.train_feat, _ = self.model.featurize(preds[:256])
         self.train_y = torch.from_numpy(np.log1p(counts[:256].astype(np.float64)).astype(np.float32)).cuda()
         self.step_cfg = sel.train_cfg(batch=256, lr=1e-4, apply_update=1)
-        # exact fallback cost: one batched scan of 256 of the held-out probes
-        self.exact_plan = sel.BatchPlan(ctx, self.eval_preds[:256], [T] * 256, autotune=False)
+        # exact fallback cost: one batched scan of 128 of the held-out probes
+        self.exact_plan = sel.BatchPlan(ctx, self.eval_preds[:128], [T] * 128, autotune=False)
         self.events = []
         self.accepted = 0
 
-    def traditional_baselines(self, step, eval_trees, okm, sample_rows=65_536):
+    def traditional_baselines(self, table, eval_trees, okm, sample_rows=65_536):
         """Ch2's estimators on the same held-out probes: the textbook heuristics
         (1/V, 1/3) with exact distinct counts, equi-depth histograms (64 buckets)
         built from a row sample, and the sampling estimator (the library's count
         on that sample, scaled by |R| / |R'|)."""
         from paper_1806_08384_b300 import baselines
-        sel, T, w = self.sel, self.T, step.w
-        cols = w.table.columns
+        sel, T = self.sel, self.T
+        cols = table.columns
         n = T.n_rows
         distinct = [int(torch.unique(c.data).numel()) for c in cols]
         dicts = [c.dictionary for c in cols]
@@ -364,42 +404,160 @@ class Surrogate:
         exact_ms = e0.elapsed_time(e1) / reps
         n = len(self.eval_preds)
         return dict(self.quality, **self.traditional, **{
-            "workload": f"{n} held-out OR-of-AND probes (<= 6 leaves) on the same table; trained on "
-                        f"{self.n_train} probes labelled by the count kernel",
-            "label_seconds": round(self.label_s, 2), "train_seconds": round(self.train_s, 2),
-            "final_train_loss": round(self.final_loss, 4),
+            "workload": f"config 4: {n} held-out OR-of-AND probes (<= 6 leaves) on config 2's 300M-row table; "
+                        f"trained on {self.quality['n_train']} probes labelled by the count kernel, tau chosen on "
+                        f"{self.quality['n_val']} validation probes",
+            "label_seconds": round(self.label_s, 2), "labels": self.n_labels,
+            "ms_per_label": round(self.label_s * 1e3 / self.n_labels, 4),
             "ms_per_batch_featurize_forward": round(statistics.mean(inf), 3),
             "ms_featurize": round(statistics.mean(fz), 3), "ms_forward": round(statistics.mean(fw), 3),
             "ms_per_estimate": round(statistics.mean(inf) / n, 6),
-            "exact_ms_per_estimate": round(exact_ms / 256, 4),
+            "exact_ms_per_estimate": round(exact_ms / 128, 4),
             "train_step_ms": round(statistics.mean(trn), 3),
             "answered_without_scan_per_step": self.accepted})
 
 
-def time_separate_vs_batched(step: OurStep, reps=5):
-    """The same probes as one batched launch vs one launch per probe."""
-    sel, w = step.sel, step.w
-    preds = [sel.Predicate(step.T, t) for t in w.trees]
-    outs = torch.zeros(len(preds), dtype=torch.int64, device=step.counts_dev.device)
-    res = {}
-    for mode in ("batched", "separate"):
-        for r in range(reps + 1):
-            if r == 1:
-                torch.cuda.synchronize()
-                t0 = torch.cuda.Event(enable_timing=True)
-                t0.record()
-            if mode == "batched":
-                step.ctx.count_batch_async(preds, [step.T] * len(preds), outs)
-            else:
-                for i, p in enumerate(preds):
-                    step.ctx.count_async(p, step.T, outs[i:i + 1])
-        t1 = torch.cuda.Event(enable_timing=True)
-        t1.record()
+# ----------------------------------------------------------------------------
+# config 2: batched vs separate, single counts, push-downs at every selectivity
+# ----------------------------------------------------------------------------
+
+def config2_measurements(sel, table, peak: float, reps=5):
+    """Config 2's five probes (OR of 3 ANDs; s = 1e-4 .. 0.5) on the 300M-row
+    table: one batched launch (the bucket kernel and the interpreter) vs one
+    launch per probe; each probe's count alone; and each probe's push-down of
+    4 columns with maxSize = n (every selection materialised, up to 150M rows),
+    with its algorithmic bytes (predicate columns read, projected values of
+    the selected rows read, rows + row ids written) and GB/s."""
+    T = sel.Table(table.columns)
+    trees = [dg.config2_predicate(s) for s in dg.CONFIG2_TARGETS]
+    preds = [sel.Predicate(T, t) for t in trees]
+    types = [c.type for c in table.columns]
+    n = T.n_rows
+    dev = table.columns[0].data.device
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, r=reps):
+        for _ in range(2):
+            fn()
         torch.cuda.synchronize()
-        res[mode + "_ms"] = t0.elapsed_time(t1) / reps
-    res["speedup"] = res["separate_ms"] / res["batched_ms"]
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(r):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / r
+    outs = torch.zeros(len(preds), dtype=torch.int64, device=dev)
+    res = {}
+    union = sorted({c for t in trees for c in dg.tree_columns(t)})
+    shared = sum(WIDTH[types[c]] for c in union) * n
+    for kernel, mode in (("bucket", 0), ("interpreter", 1)):
+        ctx = sel.Context()
+        ctx.set_batch_kernel(mode)
+        plan = sel.BatchPlan(ctx, preds, [T] * len(preds), autotune=True)
+        ms = timed(lambda: plan.run(outs))
+        res[f"batched_{kernel}_ms"] = round(ms, 4)
+        res[f"batched_{kernel}_frac"] = round(shared / ms / 1e6 / peak, 4)
+        res[f"batched_{kernel}_pick"] = plan.info()
+        counts = outs.cpu().tolist()
+    ctx = sel.Context()
+    res["separate_ms"] = round(timed(lambda: [ctx.count_async(p, T, outs[i:i + 1]) for i, p in enumerate(preds)]), 4)
+    res["speedup"] = round(res["separate_ms"] / min(res["batched_bucket_ms"], res["batched_interpreter_ms"]), 3)
+    res["batched_shared_pass_bytes"] = shared
+    single = []
+    one = torch.zeros(1, dtype=torch.int64, device=dev)
+    for t, p in zip(trees, preds):
+        nb = sum(WIDTH[types[c]] for c in dg.tree_columns(t)) * n
+        ms = timed(lambda: ctx.count_async(p, T, one))
+        single.append({"bytes": nb, "ms": round(ms, 4), "gbs": round(nb / ms / 1e6, 1),
+                       "frac": round(nb / ms / 1e6 / peak, 4)})
+    res["count_single"] = single
+    res["count_single_frac_mean"] = round(statistics.mean(x["frac"] for x in single), 4)
+    proj = [table.index(c) for c in dg.CONFIG2_PROJECTION]
+    mr = max(counts)
+    cols_out = [torch.empty(mr, dtype=table.columns[c].data.dtype, device=dev) for c in proj]
+    ids = torch.empty(mr, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    pds = []
+    for s, t, p, c in zip(dg.CONFIG2_TARGETS, trees, preds, counts):
+        ms = timed(lambda: ctx.pushdown_async(p, T, proj, mr, cols_out, ids, cnt), 3)
+        assert int(cnt.item()) == c
+        _, (b,) = algorithmic_bytes(types, n, [t], [c], [0], proj)
+        written = c * (sum(WIDTH[types[k]] for k in proj) + 8)
+        pds.append({"target_s": s, "count": c, "ms": round(ms, 3), "bytes": int(b), "written_bytes": int(written),
+                    "gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4)})
+    res["pushdown"] = pds
+    del cols_out, ids
+    res["distinct_and_join"] = distinct_and_join(sel, ctx, T, table, preds[2])
+    res["workload"] = ("config2: 300M rows x 8 cols (2 i32 U, i64 Zipf1.1, f32 U, f32 LogN, date, dict-25, "
+                       "dict-10k); 5 probes OR of 3 ANDs, s = 1e-4 .. 0.5; push-down of k0, k2, f0, d")
     return res
 
+
+def distinct_and_join(sel, ctx, T, table, pred, reps=3):
+    """f3: V(R, k2) and V(sigma_P(R), k2) of the int64 key (exact, GPU hash set)
+    and the join-size estimate of sigma_P(R) with R on that key."""
+    k = table.index("k2")
+    out = {}
+    for name, p in (("all_rows", None), ("selected_rows", pred)):
+        ctx.count_distinct(T, k, p)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            d, r = ctx.count_distinct(T, k, p)
+        out[name] = {"distinct": d, "rows": r, "ms": round((time.perf_counter() - t0) * 1e3 / reps, 3)}
+    a, b_ = out["selected_rows"], out["all_rows"]
+    out["join_size_estimate"] = round(sel.join_size_estimate(a["rows"], b_["rows"], a["distinct"], b_["distinct"]), 1)
+    out["note"] = "host-timed synchronous calls; with a predicate the time includes the push-down of k2"
+    return out
+
+
+def config5_extras(step: "OurStep", peak: float, reps=3):
+    """On the headline table: three single-probe counts and the push-down of
+    the s = 0.9 probe (about 1.08B rows written; its own maxSize = n)."""
+    sel, w, ctx, T = step.sel, step.w, step.ctx, step.T
+    counts = step.counts_dev.tolist()
+    dev = step.counts_dev.device
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, r):
+        fn()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        for _ in range(r):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / r
+    targets = np.logspace(-6, np.log10(0.9), len(w.trees))
+    res = {"count_single": []}
+    one = torch.zeros(1, dtype=torch.int64, device=dev)
+    for i in (0, len(w.trees) // 2, len(w.trees) - 1):
+        p = sel.Predicate(T, w.trees[i])
+        ms = timed(lambda: ctx.count_async(p, T, one), reps)
+        assert int(one.item()) == counts[i]
+        b = sum(WIDTH[w.types[c]] for c in dg.tree_columns(w.trees[i])) * w.n
+        res["count_single"].append({"target_s": float(f"{targets[i]:.3g}"), "count": counts[i], "ms": round(ms, 3),
+                                    "gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4)})
+    i = len(w.trees) - 1
+    p = sel.Predicate(T, w.trees[i])
+    c = counts[i]
+    cols_out = [torch.empty(c, dtype=w.table.columns[k].data.dtype, device=dev) for k in w.proj]
+    ids = torch.empty(c, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ms = timed(lambda: ctx.pushdown_async(p, T, w.proj, c, cols_out, ids, cnt), 2)
+    assert int(cnt.item()) == c
+    _, (b,) = algorithmic_bytes(w.types, w.n, [w.trees[i]], [c], [0], w.proj)
+    res["pushdown_s09"] = {"target_s": 0.9, "count": c, "ms": round(ms, 3), "bytes": int(b),
+                           "gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4)}
+    del cols_out, ids
+    torch.cuda.empty_cache()
+    return res
+
+
+# ----------------------------------------------------------------------------
+# config 3 and config 1
+# ----------------------------------------------------------------------------
 
 def star_batch(sel, peak: float, device, reps=5):
     """a5 on the star schema: 64 probes over a 480M-row fact table and four
@@ -528,121 +686,6 @@ def config1_latency(sel, device, reps=200):
     return res
 
 
-def config5_batch(sel, peak, device, reps=3):
-    """Config 5: 256 probes (s log-spaced in [1e-6, 0.9], OR of 1-3 ANDs) over
-    a 1.2B-row table of 24 B/row (28.8 GB): the exact batched count as one
-    autotuned plan (ms per estimate), single-probe counts, and the push-down of
-    3 columns for the probes at s = 1e-4 and 1e-2."""
-    tab = dg.config5_table(device=device)
-    T = sel.Table(tab.columns)
-    trees = dg.config5_predicates()
-    preds = [sel.Predicate(T, tr) for tr in trees]
-    ctx = sel.Context()
-    t0 = time.perf_counter()
-    plan = sel.BatchPlan(ctx, preds, [T] * len(preds))
-    plan_s = time.perf_counter() - t0
-    out = torch.zeros(len(preds), dtype=torch.int64, device=device)
-    ev = lambda: torch.cuda.Event(enable_timing=True)
-
-    def timed(fn, r):
-        fn()
-        torch.cuda.synchronize()
-        a, b = ev(), ev()
-        a.record()
-        for _ in range(r):
-            fn()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / r
-    n = tab.n_rows
-    width = lambda cols: sum(tab.columns[c].spec.width for c in set(cols))
-    union = sorted({c for tr in trees for c in dg.tree_columns(tr)})
-    batch_ms = timed(lambda: plan.run(out), reps)
-    counts = out.cpu().tolist()
-    res = {"batched_ms": round(batch_ms, 3), "ms_per_estimate_batched": round(batch_ms / len(preds), 4),
-           "shared_pass_bytes": width(union) * n,
-           "batched_gbs_shared_pass": round(width(union) * n / batch_ms / 1e6, 1),
-           "rows_per_s_per_probe": round(n * len(preds) / batch_ms * 1e3, 1),
-           "autotune_pick": plan.info(), "plan_create_s": round(plan_s, 2)}
-    targets = np.logspace(-6, np.log10(0.9), len(trees))
-    singles = []
-    for i in (0, len(trees) // 2, len(trees) - 1):
-        one = torch.zeros(1, dtype=torch.int64, device=device)
-        ms = timed(lambda: ctx.count_async(preds[i], T, one), reps)
-        assert int(one.item()) == counts[i]
-        b = width(dg.tree_columns(trees[i])) * n
-        singles.append({"target_s": float(f"{targets[i]:.3g}"), "count": counts[i], "ms": round(ms, 3),
-                        "gbs": round(b / ms / 1e6, 1), "frac": round(b / ms / 1e6 / peak, 4)})
-    res["count_single"] = singles
-    proj = [tab.index(c) for c in dg.CONFIG5_PROJECTION]
-    pds = []
-    for s in (1e-4, 1e-2):
-        i = int(np.argmin(np.abs(np.log(targets) - np.log(s))))
-        mr = max(1, counts[i])
-        cols_out = [torch.empty(mr, dtype=tab.columns[c].data.dtype, device=device) for c in proj]
-        ids = torch.empty(mr, dtype=torch.int64, device=device)
-        cnt = torch.zeros(1, dtype=torch.int64, device=device)
-        ms = timed(lambda: ctx.pushdown_async(preds[i], T, proj, mr, cols_out, ids, cnt), reps)
-        assert int(cnt.item()) == counts[i]
-        pc = set(dg.tree_columns(trees[i]))
-        b = width(pc) * n + counts[i] * (sum(tab.columns[c].spec.width for c in proj if c not in pc)
-                                         + sum(tab.columns[c].spec.width for c in proj) + 8)
-        pds.append({"target_s": s, "count": counts[i], "ms": round(ms, 3), "gbs": round(b / ms / 1e6, 1),
-                    "frac": round(b / ms / 1e6 / peak, 4)})
-        del cols_out, ids
-    res["pushdown"] = pds
-    res["workload"] = ("config5: 1.2B rows x 6 cols (i32 U/Zipf1.1/U, f32 N/U, dict-1000 Zipf), 24 B/row; "
-                       "256 probes s log-spaced in [1e-6, 0.9]; push-down of u0, z1, g1")
-    del plan, preds, T, tab
-    torch.cuda.empty_cache()
-    return res
-
-
-def distinct_and_join(step: OurStep, reps=3):
-    """f3: V(R, k2) and V(sigma_P(R), k2) of the int64 key (exact, GPU hash set)
-    and the join-size estimate of sigma_P(R) with R on that key."""
-    sel, w = step.sel, step.w
-    k = w.table.index("k2")
-    p = sel.Predicate(step.T, w.trees[2])   # the s = 1e-2 probe
-    out = {}
-    for name, pred in (("all_rows", None), ("selected_rows", p)):
-        step.ctx.count_distinct(step.T, k, pred)
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            d, r = step.ctx.count_distinct(step.T, k, pred)
-        out[name] = {"distinct": d, "rows": r, "ms": round((time.perf_counter() - t0) * 1e3 / reps, 3)}
-    a, b_ = out["selected_rows"], out["all_rows"]
-    out["join_size_estimate"] = round(sel.join_size_estimate(a["rows"], b_["rows"], a["distinct"], b_["distinct"]), 1)
-    out["note"] = "host-timed synchronous calls; with a predicate the time includes the push-down of k2"
-    return out
-
-
-def count_single(step: OurStep, peak: float, reps=5):
-    """a2 alone: each probe's exact count as its own launch (sel_count_async,
-    the library's default shape), GB/s of its referenced columns."""
-    sel, w = step.sel, step.w
-    out = torch.zeros(1, dtype=torch.int64, device=step.counts_dev.device)
-    res = []
-    for tree in w.trees:
-        p = sel.Predicate(step.T, tree)
-        nb = sum(WIDTH[w.types[c]] for c in dg.tree_columns(tree)) * w.n
-        for _ in range(2):
-            step.ctx.count_async(p, step.T, out)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        torch.cuda.nvtx.range_push("a2_count_single")
-        for _ in range(reps):
-            step.ctx.count_async(p, step.T, out)
-        torch.cuda.nvtx.range_pop()
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / reps
-        res.append({"bytes": nb, "ms": round(ms, 4), "gbs": round(nb / ms / 1e6, 1), "frac": round(nb / ms / 1e6 / peak, 4)})
-    fr = [r["frac"] for r in res]
-    return {"kernel": "scan_count_kernel", "per_probe": res, "frac_min": min(fr), "frac_mean": round(statistics.mean(fr), 4),
-            "note": "one launch per probe on the context's stream, inputs larger than L2; frac of measured HBM"}
-
 
 # ----------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and --impl reference)
@@ -662,7 +705,7 @@ def oracle_sample(table, trees, target_s: float, threads: int):
     """A prefix of the table sized so that one oracle step takes about target_s."""
     import oracle
     n = table.n_rows
-    m0 = min(n, 1_000_000)
+    m0 = min(n, 200_000)
     ot = oracle.OTable([c.data[:m0].cpu().numpy() for c in table.columns], [c.type for c in table.columns],
                        [c.dictionary for c in table.columns])
     t0 = time.perf_counter()
@@ -684,46 +727,54 @@ def cpu_rate(ot, types, trees, proj, threads, reps=1):
 
 
 # ----------------------------------------------------------------------------
-# traffic from the committed ncu summary (null if the kernel changed since)
+# traffic and instruction counts from the committed ncu summaries
+# (null if the kernel changed since)
 # ----------------------------------------------------------------------------
 
-def kernel_source_hash(name):
+KERNEL_SOURCES = {
+    "bucket_count_kernel": ("scan.cuh", "program.h", "kernels.h", "bucket.h", "bucket_count.cu"),
+    "scan_count_kernel": ("scan.cuh", "program.h", "kernels.h", "count.cu"),
+    "pushdown_persistent_kernel": ("scan.cuh", "program.h", "kernels.h", "lookback.cuh", "pushdown.cu"),
+}
+
+
+def kernel_source_hash(kernel):
     import hashlib
     h = hashlib.sha256()
-    for f in ("scan.cuh", "program.h", "kernels.h", "lookback.cuh", name):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_1806_08384_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, source: str, algorithmic_bytes: float):
-    """DRAM bytes of one launch: the DRAM-to-algorithmic byte ratio measured by
-    ncu on a smaller case of the same kernel (profiles/traffic.json) times this
-    launch's algorithmic bytes; None when the kernel source changed since."""
+def _traffic_entry(kernel):
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
-        d = json.load(f)
-    e = d.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash(source):
+        e = json.load(f).get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
-    return int(e["traffic_per_algorithmic_byte"] * algorithmic_bytes)
+    return e
 
 
-def issue_roofline(kernel: str, source: str, n_rows: int, launch_ms: float, sm_mhz: float):
-    """The count scan's instruction-issue roofline, for launches bound by the
-    interpreter rather than by HBM.  Achieved: the warp instructions per row
-    that ncu measured on a smaller case of the same kernel and program set
+def traffic_for(kernel: str, algorithmic_bytes: float):
+    """DRAM bytes of one launch: the DRAM-to-algorithmic byte ratio measured by
+    ncu on a smaller case of the same kernel (profiles/traffic.json) times this
+    launch's algorithmic bytes; None when the kernel source changed since."""
+    e = _traffic_entry(kernel)
+    return int(e["traffic_per_algorithmic_byte"] * algorithmic_bytes) if e else None
+
+
+def issue_roofline(kernel: str, n_rows: int, launch_ms: float, sm_mhz: float):
+    """A count scan's instruction-issue roofline, for launches bound by the
+    instruction stream rather than by HBM.  Achieved: the warp instructions per
+    row that ncu measured on a smaller case of the same kernel and probe set
     (profiles/traffic.json) times this launch's rows, over the launch time.
     Peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x the SM
     clock.  None when the kernel source changed since the capture."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(p) or launch_ms <= 0:
-        return None
-    with open(p) as f:
-        e = json.load(f).get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash(source) or "warp_instructions_per_row" not in e:
+    e = _traffic_entry(kernel)
+    if not e or "warp_instructions_per_row" not in e or launch_ms <= 0:
         return None
     achieved = e["warp_instructions_per_row"] * n_rows / (launch_ms / 1e3) / 1e9
     peak = 148 * 4 * sm_mhz / 1e3
@@ -738,16 +789,18 @@ def issue_roofline(kernel: str, source: str, n_rows: int, launch_ms: float, sm_m
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--rows", type=int, default=300_000_000)
+    ap.add_argument("--rows", type=int, default=CFG5_ROWS, help="rows of the headline (config 5) table")
+    ap.add_argument("--cfg2-rows", type=int, default=CFG2_ROWS, help="rows of the config 2 / 4 table")
+    ap.add_argument("--train", type=int, default=200_000, help="labelled training probes of the estimator")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--no-star", action="store_true", help="skip the star-schema batch measurement")
-    ap.add_argument("--no-cfg1", action="store_true", help="skip the 1M-row latency measurement")
-    ap.add_argument("--no-cfg5", action="store_true", help="skip the 1.2B-row, 256-probe measurement")
+    ap.add_argument("--no-extras", action="store_true", help="skip the config 1/2/3 and extra config 5 measurements")
+    ap.add_argument("--estimator-curve", action="store_true",
+                    help="config 4's learning curve (20k / 200k / 2M labelled pairs); prints its own JSON")
     ap.add_argument("--clock-interval-ms", type=float, default=50.0, help="NVML clock sampling interval")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -767,12 +820,21 @@ def main():
     import paper_1806_08384_b300 as sel
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.estimator_curve:
+        estimator_curve(sel, dev, args)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     w = Workload(args.rows, dev, seed_offset=rank)
     step = OurStep(w, sel)
-    sur = Surrogate(step) if not args.no_surrogate else None
+    sur = None
+    cfg2_table = None
+    if not args.no_surrogate or (rank == 0 and not args.no_extras):
+        cfg2_table = dg.gen_table("cfg2", dg.config2_specs(), args.cfg2_rows, dev)
+    if not args.no_surrogate:
+        n_val = max(2_000, args.train // 10)
+        sur = Surrogate(sel, sel.Context(), cfg2_table, n_train=args.train, n_val=n_val)
     for _ in range(args.warmup):
         step.run()
         if sur:
@@ -786,7 +848,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    launches0 = step.ctx.launches
+    launches0 = step.ctx.launches + (sur.ctx.launches if sur else 0)
     clocks.start()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -800,7 +862,7 @@ def main():
     t1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    launches = step.ctx.launches - launches0
+    launches = step.ctx.launches + (sur.ctx.launches if sur else 0) - launches0
     elapsed_ms, value = replica_throughput(t0.elapsed_time(t1), step_bytes, args.steps, world, dev)
 
     # per-kernel durations inside the timed region
@@ -810,11 +872,13 @@ def main():
     count_ms = statistics.mean(dur["count"])
     pd_ms = statistics.mean(dur["pushdown"]) if dur["pushdown"] else 0.0
     peak, peak_kind = load_peaks()
+    count_kernel = "bucket_count_kernel"
     kernels = {
-        "count": {"name": "scan_count_kernel", "ms": count_ms, "bytes": b_batch, "launches": len(dur["count"]),
-                  "total_ms": sum(dur["count"]), "source": "count.cu"},
-        "pushdown": {"name": "pushdown_persistent_kernel", "ms": pd_ms, "bytes": (sum(b_pds) / len(b_pds)) if b_pds else 0,
-                     "launches": len(dur["pushdown"]), "total_ms": sum(dur["pushdown"]), "source": "pushdown.cu"},
+        "count": {"name": count_kernel, "ms": count_ms, "bytes": b_batch, "launches": len(dur["count"]),
+                  "total_ms": sum(dur["count"])},
+        "pushdown": {"name": "pushdown_persistent_kernel", "ms": pd_ms,
+                     "bytes": (sum(b_pds) / len(b_pds)) if b_pds else 0,
+                     "launches": len(dur["pushdown"]), "total_ms": sum(dur["pushdown"])},
     }
 
     def roof(k):
@@ -822,38 +886,34 @@ def main():
         ach = kk["bytes"] / (kk["ms"] / 1e3) / 1e9 if kk["ms"] > 0 else 0.0
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4), "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic_for(kk["name"], kk["source"], kk["bytes"]), "kernel": kk["name"],
+                "traffic": traffic_for(kk["name"], kk["bytes"]), "kernel": kk["name"],
                 "algorithmic_bytes_per_launch": int(kk["bytes"]), "avg_launch_ms": round(kk["ms"], 4),
-                "launches_timed": kk["launches"]}
+                "launches_timed": kk["launches"], "total_ms_timed": round(kk["total_ms"], 3)}
     dominant = max(kernels, key=lambda k: kernels[k]["total_ms"])
     other = "count" if dominant == "pushdown" else "pushdown"
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64/f32 compares, u64 counts",
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32 compares, u64 counts",
         "data": "synthetic, seeded (datagen; shapes of the paper's fact tables), resident in HBM",
         "config": workload_config(w.n, len(w.trees), len(accepted), world),
-        "ms_per_estimate": round(elapsed_ms / args.steps / len(w.trees), 4),
+        "ms_per_estimate": round(count_ms / len(w.trees), 4),
+        "ms_per_estimate_note": "the batched count's device time over its 256 probes",
         "roofline": roof(dominant),
         "roofline_other": roof(other),
-        "roofline_issue": issue_roofline("scan_count_kernel", "count.cu", w.n, count_ms,
-                                         float((clk or {}).get("sm_max_mhz") or 2032.0)),
+        "roofline_issue": issue_roofline(count_kernel, w.n, count_ms, float((clk or {}).get("sm_max_mhz") or 2032.0)),
         "gpu_launches": int(launches),
         "clocks": clk,
+        "batch_plan_create_s": round(step.plan_s, 2),
     }
     if sur:
         out["surrogate"] = sur.summary()
-    if rank == 0:
-        out["batched_vs_separate"] = time_separate_vs_batched(step)
-        out["count_single"] = count_single(step, peak)
-        out["distinct_and_join"] = distinct_and_join(step)
-        if not args.no_star:
-            out["star_batch"] = star_batch(sel, peak, dev)
-        if not args.no_cfg1:
-            out["config1_latency"] = config1_latency(sel, dev)
-        if not args.no_cfg5:
-            out["config5_batch"] = config5_batch(sel, peak, dev)
+    if rank == 0 and not args.no_extras:
+        out["config5_extras"] = config5_extras(step, peak)
+        out["config2"] = config2_measurements(sel, cfg2_table, peak)
+        out["star_batch"] = star_batch(sel, peak, dev)
+        out["config1_latency"] = config1_latency(sel, dev)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(step, args, step_bytes)
     if rank == 0 and not args.no_cpu:
@@ -861,23 +921,51 @@ def main():
         gbs, secs = cpu_rate(ot, w.types, w.trees, w.proj, threads)
         out["cpu_baseline"] = {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
                                "sample": f"first {ot.n_rows} rows of the same table, the same step "
-                                         f"(5 counts + push-down row ids), {secs:.1f} s"}
+                                         f"({len(w.trees)} counts + push-down row ids), {secs:.1f} s"}
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
 
 
+def estimator_curve(sel, dev, args):
+    """Config 4 at its stated size: 2.2M probes labelled once by the count
+    kernel on config 2's 300M-row table; networks trained from scratch on the
+    first 20k, 200k and 2M, tau chosen on the same 100k validation probes,
+    all scored on the same 100k test probes."""
+    table = dg.gen_table("cfg2", dg.config2_specs(), args.cfg2_rows, dev)
+    T = sel.Table(table.columns)
+    ctx = sel.Context()
+    n_train, n_val, n_test = 2_000_000, 100_000, 100_000
+    trees = estimator_workload(n_train + n_val + n_test, "bench_estimator_curve")
+    preds = [sel.Predicate(T, t) for t in trees]
+    t0 = time.perf_counter()
+    counts = np.array(sel.count_many(ctx, preds, T), dtype=np.uint64)
+    label_s = time.perf_counter() - t0
+    val = slice(n_train, n_train + n_val)
+    curve = []
+    for m in (20_000, 200_000, 2_000_000):
+        sub_p = preds[:m] + preds[val] + preds[n_train + n_val:]
+        sub_c = np.concatenate([counts[:m], counts[val], counts[n_train + n_val:]])
+        _, _, _, quality, _ = train_and_gate(sel, ctx, T, sub_p, sub_c, m, n_val, n_test)
+        curve.append(quality)
+        print(json.dumps({"n_train": m, **quality}), flush=True)
+    print(json.dumps({"estimator_curve": curve, "labels": len(preds), "label_seconds": round(label_s, 1),
+                      "ms_per_label": round(label_s * 1e3 / len(preds), 4),
+                      "workload": "config 4: random OR-of-AND probes (<= 6 leaves, <= 3 groups) on config 2's "
+                                  f"{args.cfg2_rows}-row table, labels from the count kernel"}))
+
+
 def run_e2e(step: OurStep, args, step_bytes):
     """The same step through the C ABI with the table in pinned HOST memory:
-    every step copies the 8 columns host->device and the results back."""
+    every step copies the columns host->device and the results back."""
     w = step.w
     host_cols = [torch.empty_like(c.data, device="cpu").pin_memory() for c in w.table.columns]
     for h, c in zip(host_cols, w.table.columns):
         h.copy_(c.data)
     step.host_out = [torch.empty(o.numel(), dtype=o.dtype).pin_memory() for o in step.out_cols + [step.out_ids]]
     h2d = sum(h.numel() * h.element_size() for h in host_cols)
-    k = max(1, min(args.steps, 5))
+    k = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -890,6 +978,8 @@ def run_e2e(step: OurStep, args, step_bytes):
     t1.record()
     torch.cuda.synchronize()
     ms = t0.elapsed_time(t1) / k
+    del host_cols
+    step.host_out = None
     return {"value": round(step_bytes / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": k}
 
@@ -908,13 +998,12 @@ def replica_throughput(elapsed_ms: float, step_bytes: int, steps: int, world: in
 
 def workload_config(n: int, probes: int, pushed: int, world: int = 1) -> dict:
     """The bench's config object (both arms)."""
-    return {"workload": f"config2 fact table: {n} rows x 8 cols (2 i32 U, i64 Zipf1.1, f32 U, f32 LogN, "
-                        f"date, dict-25, dict-10k), {probes} probes OR-of-3-ANDs "
-                        f"s={list(dg.CONFIG2_TARGETS)}, push-down of {list(dg.CONFIG2_PROJECTION)} "
-                        f"when count <= floor(n*{MAX_SELECTIVITY})",
-            "n_rows": n, "table_bytes": n * 36, "probes": probes, "pushed_down": pushed,
+    return {"workload": f"config5 table: {n} rows x 6 cols (3 i32 U/Zipf1.1/U, 2 f32 N/U, dict-1000 Zipf), "
+                        f"24 B/row; {probes} probes OR of 1-3 ANDs, s log-spaced in [1e-6, 0.9]; push-down of "
+                        f"{list(dg.CONFIG5_PROJECTION)} when count <= floor(n*{MAX_SELECTIVITY})",
+            "n_rows": n, "table_bytes": n * 24, "probes": probes, "pushed_down": pushed,
             "max_rows": int(math.floor(n * MAX_SELECTIVITY)),
-            "l2": "inputs larger than L2 (table 10.8 GB vs 126 MB L2), no flush needed",
+            "l2": "inputs larger than L2 (table 28.8 GB vs 126 MB L2), no flush needed",
             "parallelism": f"replicas{world}" if world > 1 else "single"}
 
 
@@ -922,10 +1011,10 @@ def run_reference(args, threads):
     """The oracle as it stands, on the host cores, on a bounded sample per step."""
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     n = args.rows
-    w_tab = dg.gen_table("cfg2", dg.config2_specs(), n if dev == "cuda" else min(n, 20_000_000), dev)
-    trees = probe_trees()
+    w_tab = dg.gen_table("cfg5", dg.config5_specs(), min(n, 50_000_000), dev)
+    trees = dg.config5_predicates()
     types = [c.type for c in w_tab.columns]
-    proj = [w_tab.index(c) for c in dg.CONFIG2_PROJECTION]
+    proj = [w_tab.index(c) for c in dg.CONFIG5_PROJECTION]
     per_step = max(1.0, 150.0 / max(1, args.steps + args.warmup))
     ot = oracle_sample(w_tab, trees, per_step, threads)
     del w_tab
@@ -937,10 +1026,11 @@ def run_reference(args, threads):
     dt = (time.perf_counter() - t0) / args.steps
     b, pds = algorithmic_bytes(types, ot.n_rows, trees, counts, accepted, proj)
     gbs = (b + sum(pds)) / dt / 1e9
-    sample = f"first {ot.n_rows} of {n} rows of the config 2 table per step, 5 counts + push-down row ids"
+    sample = (f"first {ot.n_rows} of {n} rows of the config 5 table per step, {len(trees)} counts + push-down "
+              f"row ids")
     out = {"impl": "reference", "metric": METRIC, "value": round(gbs, 3), "unit": "GB/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "i32/i64/f32 compares, u64 counts",
+           "scaling": "weak", "vs_baseline": None, "dtype": "i32/f32 compares, u64 counts",
            "data": "synthetic, seeded (datagen)",
            "config": workload_config(n, len(trees), len(accepted), args.gpus),
            "cpu_baseline": {"value": round(gbs, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
