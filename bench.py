@@ -341,10 +341,7 @@ class Surrogate:
         n = T.n_rows
         distinct = [int(torch.unique(c.data).numel()) for c in cols]
         dicts = [c.dictionary for c in cols]
-        g = torch.Generator(device=cols[0].data.device)
-        g.manual_seed(dg.mix_seed("bench_row_sample"))
-        rows = torch.randint(0, n, (sample_rows,), generator=g, device=cols[0].data.device)
-        sample = [dg.Column(c.spec, c.data[rows].contiguous(), c.dictionary) for c in cols]
+        sample = baselines.row_sample(cols, sample_rows, dg.mix_seed("bench_row_sample"))
         hists = [baselines.EquiDepthHistogram.build(c.data.cpu().numpy(), n, buckets=64) for c in sample]
         TS = sel.Table(sample)
         sp = [sel.Predicate(TS, t) for t in eval_trees]
@@ -600,20 +597,27 @@ def star_batch(sel, peak: float, device, reps=5):
         res[mode + "_ms"] = round(a.elapsed_time(b) / reps, 4)
         res[mode + "_counts"] = out.cpu().tolist()
     assert res["batched_counts"] == res["separate_counts"]
+    counts = res["batched_counts"]
     del res["batched_counts"], res["separate_counts"]
-    # f3 / f4 on the star: the exact COUNT of sigma(fact) join sigma(dim) on fact.a1 = dim.key
-    # next to the join-size estimate from exact selectivities and distinct counts
+    # f3 / f4 on the star: the exact COUNT of sigma(fact) join sigma(dim) on a fact column whose
+    # domain is the dimension key's (a1: 1000 Zipf values for the 2k-row dimension, a2: uniform
+    # below 1M for the 200k- and 2.4M-row ones) next to the join-size estimate from exact
+    # selectivities and distinct counts; the fact probe with the most rows under 10 % of the
+    # fact table, each dimension's probe with the most rows
     joins = []
-    fact_p = preds[0]
-    for k in (1, 2, 3):
-        dim_i = next(i for i, (ti, _) in enumerate(probes) if ti == k)
+    fact_idx = [i for i, (ti, _) in enumerate(probes) if ti == 0]
+    fact_i = max((i for i in fact_idx if counts[i] <= 0.1 * tabs[0].n_rows), key=lambda i: counts[i])
+    fact_p = preds[fact_i]
+    for k, fk in ((1, tabs[0].index("a1")), (2, tabs[0].index("a2")), (3, tabs[0].index("a2"))):
+        dim_i = max((i for i, (ti, _) in enumerate(probes) if ti == k), key=lambda i: counts[i])
         t0 = time.perf_counter()
-        exact, nr, ns = ctx.join_count(T[0], 1, fact_p, T[k], 0, preds[dim_i])
+        exact, nr, ns = ctx.join_count(T[0], fk, fact_p, T[k], 0, preds[dim_i])
         join_ms = (time.perf_counter() - t0) * 1e3
-        vr, _ = ctx.count_distinct(T[0], 1, fact_p)
+        vr, _ = ctx.count_distinct(T[0], fk, fact_p)
         vs, _ = ctx.count_distinct(T[k], 0, preds[dim_i])
         est = sel.join_size_estimate(nr, ns, vr, vs)
-        joins.append({"dimension_rows": tabs[k].n_rows, "fact_selected": nr, "dim_selected": ns,
+        joins.append({"dimension_rows": tabs[k].n_rows, "fact_column": tabs[0].columns[fk].name,
+                      "fact_selected": nr, "dim_selected": ns, "fact_distinct": vr, "dim_distinct": vs,
                       "join_count": exact, "join_count_ms": round(join_ms, 3), "estimate": round(est, 1),
                       "estimate_q_error": round(max(est, 1.0, exact) / max(min(est, exact), 1.0), 3)})
     info = plan.info()
@@ -801,6 +805,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the config 1/2/3 and extra config 5 measurements")
     ap.add_argument("--estimator-curve", action="store_true",
                     help="config 4's learning curve (20k / 200k / 2M labelled pairs); prints its own JSON")
+    ap.add_argument("--kernel-case", choices=["batch-cfg5", "batch-cfg2", "pushdown-cfg5"],
+                    help="run one kernel case twice (for an ncu capture) and exit: the batched count of config 5's "
+                         "256 probes or of config 2's 5 probes, or the push-down of the config 5 probe nearest "
+                         "selectivity --case-s, over a --rows-row table")
+    ap.add_argument("--case-s", type=float, default=1e-3)
     ap.add_argument("--clock-interval-ms", type=float, default=50.0, help="NVML clock sampling interval")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
@@ -822,6 +831,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.estimator_curve:
         estimator_curve(sel, dev, args)
+        return
+    if args.kernel_case:
+        kernel_case(sel, dev, args)
         return
     if world > 1:
         import torch.distributed as dist
@@ -926,6 +938,42 @@ def main():
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
+
+
+def kernel_case(sel, dev, args):
+    """One kernel case launched twice (the profiles' captures take the second)."""
+    if args.kernel_case == "batch-cfg2":
+        t = dg.gen_table("cfg2", dg.config2_specs(), args.rows, dev)
+        trees = [dg.config2_predicate(s) for s in dg.CONFIG2_TARGETS]
+    else:
+        t = dg.gen_table("cfg5", dg.config5_specs(), args.rows, dev)
+        trees = dg.config5_predicates()
+    T = sel.Table(t.columns)
+    ctx = sel.Context()
+    if args.kernel_case.startswith("batch"):
+        preds = [sel.Predicate(T, tr) for tr in trees]
+        ctx.set_batch_kernel(2)
+        plan = sel.BatchPlan(ctx, preds, [T] * len(preds), autotune=False)
+        out = torch.zeros(len(preds), dtype=torch.int64, device=dev)
+        for _ in range(2):
+            plan.run(out)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.kernel_case, "rows": args.rows, "plan": plan.info(),
+                          "counts": out[:8].tolist()}))
+        return
+    targets = np.logspace(-6, np.log10(0.9), len(trees))
+    i = int(np.argmin(np.abs(np.log(targets) - np.log(args.case_s))))
+    proj = [t.index(c) for c in dg.CONFIG5_PROJECTION]
+    mr = int(math.floor(args.rows * MAX_SELECTIVITY))
+    outs = [torch.empty(mr, dtype=t.columns[c].data.dtype, device=dev) for c in proj]
+    ids = torch.empty(mr, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    p = sel.Predicate(T, trees[i])
+    for _ in range(2):
+        ctx.pushdown_async(p, T, proj, mr, outs, ids, cnt)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.kernel_case, "rows": args.rows, "probe": i, "count": int(cnt.item()),
+                      "predicate_columns": len(dg.tree_columns(trees[i]))}))
 
 
 def estimator_curve(sel, dev, args):

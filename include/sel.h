@@ -236,7 +236,10 @@ sel_status sel_ctx_synchronize(sel_ctx* ctx);
 sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
                                  int32_t n, int32_t autotune, sel_batch_plan** out);
 /* Runs the plan: counts to dev_out_counts (device, n u64, enqueue only) when
- * it is not NULL, else to host_out_counts (synchronous). */
+ * it is not NULL, else to host_out_counts (synchronous).  With a device
+ * buffer the replayed graph's kernel writes the counts straight into it: the
+ * first run with a buffer captures that graph (the plan keeps the graphs of
+ * its last 4 buffers), later runs are one graph launch. */
 sel_status sel_batch_plan_run(sel_batch_plan* plan, uint64_t* dev_out_counts, uint64_t* host_out_counts);
 /* Launch shape chosen by the plan and its measured time per launch (ms, 0 if
  * not autotuned). */
@@ -282,7 +285,7 @@ uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
 
 /* Test hook for the bounded waits of the push-down look-back: look-back unit
  * skip_tile (a super-tile of the default kernel -- the largest multiple of
- * its tile up to 16384 rows --, a tile of the one-CTA-per-tile kernel; -1:
+ * its tile up to 32768 rows --, a tile of the one-CTA-per-tile kernel; -1:
  * none) never publishes its prefix, and a waiting tile gives up after
  * wait_ns nanoseconds (0: the default of 2 s), so that later sel_pushdown
  * calls on this context return SEL_ERR_TIMEOUT instead of waiting forever.
@@ -460,6 +463,15 @@ sel_status sel_mlp_load(sel_ctx* ctx, const char* path, sel_mlp** out);
  * nonzero if a bounded wait inside the kernel gave up. */
 sel_status sel_debug_gemm_bf16(void* cuda_stream, const void* A, const void* B, int32_t M, int32_t N, int32_t K,
                                float* C, int32_t k_splits, uint32_t* dev_err);
+
+/* Test hook for allocation failures (failure injection on the host; no GPU
+ * fault): the nth device or pinned-host allocation the library makes from
+ * now on (1 = the next one; process-wide, every context and thread) fails as
+ * if the device were out of memory, without allocating; the entry point that
+ * made it returns SEL_ERR_OOM and frees what it had allocated, and the
+ * context stays usable.  0 disarms; negative: SEL_ERR_INVALID_ARG.  The hook
+ * fires once. */
+sel_status sel_debug_fail_allocation(int64_t nth);
 
 /* Test hook for the column-bucket form of a batch (host only, no GPU): the
  * exact counts of preds[0..n) over `table`, whose column pointers are HOST

@@ -107,6 +107,7 @@ def _load():
         "sel_batch_plan_variant": (C.c_int, [V, P(C.c_int32), P(C.c_int32)]),
         "sel_batch_plan_free": (None, [V]),
         "sel_batch_plan_kernel": (C.c_int, [V, P(C.c_int32)]),
+        "sel_debug_fail_allocation": (C.c_int, [C.c_int64]),
         "sel_ctx_set_batch_kernel": (C.c_int, [V, C.c_int32]),
         "sel_debug_bucket_count_host": (C.c_int, [P(V), C.c_int32, P(sel_table), P(C.c_uint64), P(C.c_int32)]),
         "sel_ctx_set_scan_shape": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32]),
@@ -689,6 +690,11 @@ def evaluate_and_push_down(ctx: "Context", relations, min_table_size: int = 0, m
             d["rowids"] = ids[:d["count"]] if ids is not None else None
         res.append(d)
     return res
+
+
+def debug_fail_allocation(nth: int):
+    """sel_debug_fail_allocation: the nth library allocation from now on fails (0 disarms)."""
+    _check(lib.sel_debug_fail_allocation(int(nth)), "sel_debug_fail_allocation")
 
 
 def debug_bucket_count_host(preds: Sequence[Predicate], table):

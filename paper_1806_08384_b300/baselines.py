@@ -185,6 +185,27 @@ def histogram_selectivity(tree, hists: list, dicts=None) -> float:
     raise ValueError(k)
 
 
+def row_sample(columns, sample_rows: int, seed: int):
+    """R': sample_rows rows of the table drawn uniformly with replacement
+    (a seeded torch generator on the columns' device); returns columns
+    (``.type``, ``.data``, ``.dictionary``) holding the sampled rows, whose
+    selection the library's count kernel then counts."""
+    import torch
+    dev = columns[0].data.device
+    n = int(columns[0].data.numel())
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    rows = torch.randint(0, n, (sample_rows,), generator=g, device=dev)
+    return [SampledColumn(c.type, c.data[rows].contiguous(), c.dictionary) for c in columns]
+
+
+class SampledColumn:
+    """A sampled column: type name, data tensor and dictionary (or None)."""
+
+    def __init__(self, type_name: str, data, dictionary):
+        self.type, self.data, self.dictionary = type_name, data, dictionary
+
+
 def sampling_estimate(sample_count: int, sample_rows: int, n_rows: int) -> float:
     """|sigma(R)| = |sigma(R')| * |R| / |R'| (Ch2), R' a random row sample."""
     return float(sample_count) * float(n_rows) / float(max(1, sample_rows))

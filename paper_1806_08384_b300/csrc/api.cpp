@@ -29,6 +29,34 @@ void set_error(const char* fmt, ...) {
     g_err = buf;
 }
 
+// Allocation failure injection: the n-th allocation from the arming call on
+// (process-wide, every context and thread) fails; 0 = disarmed.
+static std::atomic<int64_t> g_fail_alloc{0};
+
+static bool injected_failure() {
+    int64_t v = g_fail_alloc.load();
+    while (v > 0) {
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t host_alloc(void** p, size_t bytes) {
+    if (injected_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+
 static sel_status cuda_fail(const char* where, cudaError_t e) {
     set_error("%s: %s", where, cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? SEL_ERR_OOM : SEL_ERR_CUDA;
@@ -49,7 +77,7 @@ struct DevBuf {
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
-        cudaError_t e = cudaMalloc(&p, std::max<size_t>(bytes, 256));
+        cudaError_t e = dev_alloc(&p, std::max<size_t>(bytes, 256));
         if (e != cudaSuccess) return cuda_fail(what, e);
         cap = std::max<size_t>(bytes, 256);
         return SEL_OK;
@@ -110,6 +138,15 @@ struct sel_batch_plan {
     int kernel = 0;                    // the kernel the plan runs: 0 interpreter, 1 bucket
     void* d_bk_blob = nullptr;
     uint32_t bk_blob_bytes = 0, bk_gb_bytes = 0, bk_n_out = 0;
+    // graphs that write the counts to a caller's device buffer, by buffer
+    std::vector<std::pair<void*, cudaGraphExec_t>> out_graphs;
+    ~sel_batch_plan() {
+        if (graph) cudaGraphExecDestroy(graph);
+        for (auto& kv : out_graphs) cudaGraphExecDestroy(kv.second);
+        if (d_bk_blob) cudaFree(d_bk_blob);
+        if (d_blob) cudaFree(d_blob);
+        if (d_counts) cudaFree(d_counts);
+    }
 };
 
 namespace sel {
@@ -119,7 +156,7 @@ static sel_status ensure_host(sel_ctx* c, size_t n) {
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     c->h_pinned = nullptr;
     c->h_cap = 0;
-    SEL_CUDA("cudaMallocHost", cudaMallocHost(reinterpret_cast<void**>(&c->h_pinned), n * 8 + 64));
+    SEL_CUDA("cudaMallocHost", host_alloc(reinterpret_cast<void**>(&c->h_pinned), n * 8 + 64));
     c->h_cap = n;
     return SEL_OK;
 }
@@ -443,7 +480,7 @@ extern "C" sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out) {
     SEL_CUDA("cudaMemset", cudaMemset(c->err.p, 0, 256));
     s = ensure_host(c.get(), 64);
     if (s != SEL_OK) return s;
-    SEL_CUDA("cudaMallocHost", cudaMallocHost(reinterpret_cast<void**>(&c->h_err), 64));
+    SEL_CUDA("cudaMallocHost", host_alloc(reinterpret_cast<void**>(&c->h_err), 64));
     *out = c.release();
     return SEL_OK;
 }
@@ -480,6 +517,15 @@ extern "C" sel_status sel_ctx_set_scan_variant(sel_ctx* c, int32_t consumer_warp
 }
 
 extern "C" uint64_t sel_ctx_launch_count(const sel_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" sel_status sel_debug_fail_allocation(int64_t nth) {
+    if (nth < 0) {
+        set_error("sel_debug_fail_allocation: nth must be >= 0");
+        return SEL_ERR_INVALID_ARG;
+    }
+    g_fail_alloc.store(nth);
+    return SEL_OK;
+}
 
 namespace sel {
 cudaStream_t ctx_stream(sel_ctx* c) { return c->stream; }
@@ -607,7 +653,7 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     a.row_bytes = ta.row_bytes;
     a.tma = ta.tma;
     // The persistent kernel: super-tiles (the largest multiple of the sub-tile
-    // up to 16384 rows) streamed in sub-tiles through shared-memory stages.
+    // up to 32768 rows) streamed in sub-tiles through shared-memory stages.
     // Variant: the context's scan variant, else 16 consumer warps x 2 chunks
     // per pass.  Sub-tile and stages: the requested ones, else the count
     // scan's rule: 3 stages (2 if 3 do not fit) of the largest sub-tile, in
@@ -943,8 +989,9 @@ static std::string table_key(const sel_table* t) {
 }
 
 // One launch of the plan's probes on the given kernel (0 interpreter, 1 bucket).
-static sel_status plan_launch(sel_batch_plan* p, int kernel, const Shape& sh, int* n_launches) {
-    unsigned long long* d_counts = static_cast<unsigned long long*>(p->d_counts);
+static sel_status plan_launch(sel_batch_plan* p, int kernel, const Shape& sh, int* n_launches,
+                              void* counts = nullptr) {
+    unsigned long long* d_counts = static_cast<unsigned long long*>(counts ? counts : p->d_counts);
     if (kernel == 1) return run_bucket(p->ctx, p, sh, d_counts, n_launches);
     return run_scan(p->ctx, static_cast<const uint8_t*>(p->d_blob), p->blob_bytes, p->instr_off, p->pool_off,
                     p->n_progs, p->tables, d_counts, sh, n_launches);
@@ -974,7 +1021,10 @@ static sel_status plan_time(sel_batch_plan* p, int kernel, const Shape& sh, int 
     return s;
 }
 
-static sel_status plan_capture(sel_batch_plan* p) {
+// Captures the plan's launch (zeroing the counts, then the kernel) into a
+// graph whose kernel writes the counts to `counts` (the plan's own buffer, or
+// a caller's device buffer of n u64).
+static sel_status plan_capture(sel_batch_plan* p, void* counts, cudaGraphExec_t* out) {
     sel_ctx* ctx = p->ctx;
     cudaStream_t cs;
     SEL_CUDA("cudaStreamCreate", cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -987,15 +1037,15 @@ static sel_status plan_capture(sel_batch_plan* p) {
     if (e != cudaSuccess) s = cuda_fail("cudaStreamBeginCapture", e);
     int nl = 0;
     if (s == SEL_OK) {
-        cudaMemsetAsync(p->d_counts, 0, (size_t)p->n * 8, cs);
-        s = plan_launch(p, p->kernel, p->shape, &nl);
+        cudaMemsetAsync(counts, 0, (size_t)p->n * 8, cs);
+        s = plan_launch(p, p->kernel, p->shape, &nl, counts);
         e = cudaStreamEndCapture(cs, &g);
         if (s == SEL_OK && e != cudaSuccess) s = cuda_fail("cudaStreamEndCapture", e);
     }
     ctx->stream = saved;
     ctx->launches = saved_launches;
     if (s == SEL_OK) {
-        e = cudaGraphInstantiate(&p->graph, g, 0);
+        e = cudaGraphInstantiate(out, g, 0);
         if (e != cudaSuccess) s = cuda_fail("cudaGraphInstantiate", e);
     }
     if (g) cudaGraphDestroy(g);
@@ -1074,9 +1124,9 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     std::vector<uint8_t> blob;
     build_blob(progs, maps, blob, p->instr_off, p->pool_off, outs);
     p->blob_bytes = (uint32_t)blob.size();
-    SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_blob, blob.size()));
+    SEL_CUDA("cudaMalloc", dev_alloc(&p->d_blob, blob.size()));
     SEL_CUDA("cudaMemcpy", cudaMemcpy(p->d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
-    SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_counts, (size_t)n * 8));
+    SEL_CUDA("cudaMalloc", dev_alloc(&p->d_counts, (size_t)n * 8));
     uint32_t max_rb = 0;
     for (auto& t : p->tables) max_rb = std::max(max_rb, t.row_bytes);
     // the column-bucket form, when the probes fit it (bucket.h)
@@ -1091,7 +1141,7 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
             p->bk_blob_bytes = (uint32_t)bp.blob.size();
             p->bk_n_out = bp.n_out;
             p->bk_gb_bytes = hdr.gb_slots * 8u * 32u * 2u;
-            SEL_CUDA("cudaMalloc", cudaMalloc(&p->d_bk_blob, bp.blob.size()));
+            SEL_CUDA("cudaMalloc", dev_alloc(&p->d_bk_blob, bp.blob.size()));
             SEL_CUDA("cudaMemcpy", cudaMemcpy(p->d_bk_blob, bp.blob.data(), bp.blob.size(), cudaMemcpyHostToDevice));
             bucket_ok = true;
         } else if (ctx->batch_kernel == 2) {
@@ -1205,7 +1255,7 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
         if (rs != SEL_OK) return rs;
     }
     p->ms = best_ms;
-    sel_status s = plan_capture(p.get());
+    sel_status s = plan_capture(p.get(), p->d_counts, &p->graph);
     if (s != SEL_OK) return s;
     *out = p.release();
     return SEL_OK;
@@ -1217,15 +1267,29 @@ extern "C" sel_status sel_batch_plan_run(sel_batch_plan* p, uint64_t* dev_out_co
         return SEL_ERR_INVALID_ARG;
     }
     sel_ctx* ctx = p->ctx;
-    if (!dev_out_counts) SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(ctx->err.p, 0, 4, ctx->stream));
+    if (dev_out_counts) {
+        // a graph whose kernel writes straight into the caller's buffer,
+        // captured on the first run with that buffer (a few are kept)
+        cudaGraphExec_t g = nullptr;
+        for (auto& kv : p->out_graphs)
+            if (kv.first == dev_out_counts) g = kv.second;
+        if (!g) {
+            if (p->out_graphs.size() >= 4) {
+                cudaGraphExecDestroy(p->out_graphs.front().second);
+                p->out_graphs.erase(p->out_graphs.begin());
+            }
+            sel_status s = plan_capture(p, dev_out_counts, &g);
+            if (s != SEL_OK) return s;
+            p->out_graphs.emplace_back(dev_out_counts, g);
+        }
+        SEL_CUDA("cudaGraphLaunch", cudaGraphLaunch(g, ctx->stream));
+        ctx->launches += (uint64_t)p->launches_per_run;
+        return SEL_OK;
+    }
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(ctx->err.p, 0, 4, ctx->stream));
     SEL_CUDA("cudaGraphLaunch", cudaGraphLaunch(p->graph, ctx->stream));
     ctx->launches += (uint64_t)p->launches_per_run;
     const size_t bytes = (size_t)p->n * 8;
-    if (dev_out_counts) {
-        SEL_CUDA("cudaMemcpyAsync",
-                 cudaMemcpyAsync(dev_out_counts, p->d_counts, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-        return SEL_OK;
-    }
     sel_status s = ensure_host(ctx, (size_t)p->n);
     if (s != SEL_OK) return s;
     SEL_CUDA("cudaMemcpyAsync", cudaMemcpyAsync(ctx->h_pinned, p->d_counts, bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1284,14 +1348,7 @@ extern "C" sel_status sel_ctx_set_batch_kernel(sel_ctx* c, int32_t mode) {
     return SEL_OK;
 }
 
-extern "C" void sel_batch_plan_free(sel_batch_plan* p) {
-    if (!p) return;
-    if (p->graph) cudaGraphExecDestroy(p->graph);
-    if (p->d_bk_blob) cudaFree(p->d_bk_blob);
-    if (p->d_blob) cudaFree(p->d_blob);
-    if (p->d_counts) cudaFree(p->d_counts);
-    delete p;
-}
+extern "C" void sel_batch_plan_free(sel_batch_plan* p) { delete p; }
 
 static sel_status batch_cached(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
                                int32_t n, uint64_t* dev_out, uint64_t* host_out) {

@@ -828,7 +828,7 @@ sel_status pred_upload(const sel_pred* cp) {
     for (int i = 0; i < kMaxSlots; ++i) ident[i] = i;
     build_blob({&p->prog}, {ident}, blob, p->instr_off, p->pool_off);
     void* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, blob.size());
+    cudaError_t e = dev_alloc(&d, blob.size());
     if (e != cudaSuccess) {
         set_error("predicate upload: cudaMalloc: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? SEL_ERR_OOM : SEL_ERR_CUDA;

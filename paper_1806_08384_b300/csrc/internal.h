@@ -17,6 +17,12 @@ namespace sel {
 
 void set_error(const char* fmt, ...);
 
+// Every device and pinned host allocation of the library goes through these
+// two; sel_debug_fail_allocation can make the n-th one fail with
+// cudaErrorMemoryAllocation (reported as SEL_ERR_OOM) without allocating.
+cudaError_t dev_alloc(void** p, size_t bytes);
+cudaError_t host_alloc(void** p, size_t bytes);
+
 // A comparison leaf of the normalised tree, kept for featurisation.
 struct Clause {
     int32_t col;

@@ -108,8 +108,8 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
 // sub-tiles of tile_rows rows stream through `stages` shared-memory stages and
 // the look-back unit (n_tiles, status words) is a super-tile of super_rows
 // rows: the largest multiple of tile_rows that is at most kPdpMaxChunks chunks
-// (16384 rows).
-constexpr int kPdpMaxChunks = 64;
+// (32768 rows).
+constexpr int kPdpMaxChunks = 128;
 bool pushdown_persistent_ok(int warps, int chunks_per_pass);
 // tile_rows: a multiple of chunks_per_pass chunks, at most kPdpMaxChunks chunks.
 bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass);

@@ -376,7 +376,7 @@ namespace {
 template <typename T>
 sel_status dalloc(sel_mlp* m, T** p, size_t count, const char* what) {
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 256));
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&q), std::max<size_t>(count * sizeof(T), 256));
     if (e != cudaSuccess) {
         set_error("%s: cudaMalloc: %s", what, cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? SEL_ERR_OOM : SEL_ERR_CUDA;
@@ -660,8 +660,8 @@ sel_status stage_reserve(sel_mlp* m, size_t bytes) {
     if (m->d_stage) cudaFree(m->d_stage);
     m->h_stage = m->d_stage = nullptr;
     m->stage_cap = 0;
-    MLP_TRY(cuda_ok(cudaMallocHost(reinterpret_cast<void**>(&m->h_stage), cap), "featurize staging"));
-    MLP_TRY(cuda_ok(cudaMalloc(reinterpret_cast<void**>(&m->d_stage), cap), "featurize staging"));
+    MLP_TRY(cuda_ok(host_alloc(reinterpret_cast<void**>(&m->h_stage), cap), "featurize staging"));
+    MLP_TRY(cuda_ok(dev_alloc(reinterpret_cast<void**>(&m->d_stage), cap), "featurize staging"));
     m->stage_cap = cap;
     return SEL_OK;
 }
@@ -784,8 +784,8 @@ extern "C" sel_status sel_mlp_create(sel_ctx* ctx, const sel_table* table, int32
     std::vector<const uint8_t*> ptrs;
     for (int32_t c = 0; c < m->n_cols; ++c) ptrs.push_back(static_cast<const uint8_t*>(table->cols[c].data));
     DeviceVec dptr, dty;
-    MLP_TRY(cuda_ok(cudaMalloc(&dptr.p, ptrs.size() * 8), "sel_mlp_create"));
-    MLP_TRY(cuda_ok(cudaMalloc(&dty.p, ptrs.size() * 4), "sel_mlp_create"));
+    MLP_TRY(cuda_ok(dev_alloc(&dptr.p, ptrs.size() * 8), "sel_mlp_create"));
+    MLP_TRY(cuda_ok(dev_alloc(&dty.p, ptrs.size() * 4), "sel_mlp_create"));
     MLP_TRY(cuda_ok(cudaMemcpyAsync(dptr.p, ptrs.data(), ptrs.size() * 8, cudaMemcpyHostToDevice, st), "sel_mlp_create"));
     MLP_TRY(cuda_ok(cudaMemcpyAsync(dty.p, m->types.data(), ptrs.size() * 4, cudaMemcpyHostToDevice, st),
                     "sel_mlp_create"));
@@ -874,7 +874,7 @@ extern "C" sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* co
     }
     cudaStream_t st = ctx_stream(ctx);
     DeviceVec feat, y, idx, xb, yb;
-    MLP_TRY(cuda_ok(cudaMalloc(&feat.p, (size_t)n * kFeat * 2), "sel_mlp_train"));
+    MLP_TRY(cuda_ok(dev_alloc(&feat.p, (size_t)n * kFeat * 2), "sel_mlp_train"));
     std::vector<uint8_t> ok_all;
     ok_all.reserve((size_t)n);
     for (int64_t b0 = 0; b0 < n; b0 += 65536) {
@@ -893,11 +893,11 @@ extern "C" sel_status sel_mlp_train(sel_ctx* ctx, sel_mlp* m, const sel_pred* co
         set_error("sel_mlp_train: %zu featurizable predicates, fewer than one batch", usable.size());
         return SEL_ERR_INVALID_ARG;
     }
-    MLP_TRY(cuda_ok(cudaMalloc(&y.p, (size_t)n * 4), "sel_mlp_train"));
+    MLP_TRY(cuda_ok(dev_alloc(&y.p, (size_t)n * 4), "sel_mlp_train"));
     MLP_TRY(cuda_ok(cudaMemcpyAsync(y.p, yh.data(), (size_t)n * 4, cudaMemcpyHostToDevice, st), "sel_mlp_train"));
-    MLP_TRY(cuda_ok(cudaMalloc(&idx.p, usable.size() * 4), "sel_mlp_train"));
-    MLP_TRY(cuda_ok(cudaMalloc(&xb.p, (size_t)cfg->batch * kFeat * 2), "sel_mlp_train"));
-    MLP_TRY(cuda_ok(cudaMalloc(&yb.p, (size_t)cfg->batch * 4), "sel_mlp_train"));
+    MLP_TRY(cuda_ok(dev_alloc(&idx.p, usable.size() * 4), "sel_mlp_train"));
+    MLP_TRY(cuda_ok(dev_alloc(&xb.p, (size_t)cfg->batch * kFeat * 2), "sel_mlp_train"));
+    MLP_TRY(cuda_ok(dev_alloc(&yb.p, (size_t)cfg->batch * 4), "sel_mlp_train"));
     if (m->step == 0) {
         // start the head at the targets' mean and log-variance (an untrained model)
         double s1 = 0.0, s2 = 0.0;
@@ -949,7 +949,7 @@ extern "C" sel_status sel_mlp_estimate(sel_ctx* ctx, sel_mlp* m, const sel_pred*
     }
     cudaStream_t st = ctx_stream(ctx);
     DeviceVec feat;
-    MLP_TRY(cuda_ok(cudaMalloc(&feat.p, (size_t)n * kFeat * 2), "sel_mlp_estimate"));
+    MLP_TRY(cuda_ok(dev_alloc(&feat.p, (size_t)n * kFeat * 2), "sel_mlp_estimate"));
     std::vector<uint8_t> ok;
     MLP_TRY(featurize(m, st, preds, n, static_cast<__nv_bfloat16*>(feat.p), &ok, nullptr));
     MLP_TRY(forward(m, static_cast<const __nv_bfloat16*>(feat.p), n, false, st));

@@ -210,7 +210,7 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 // Persistent push-down over super-tiles (the default path).
 //
 // The look-back unit is a super-tile: the largest multiple of the sub-tile
-// (tile_rows rows) that is at most 16384 rows.  A CTA streams a super-tile
+// (tile_rows rows) that is at most 32768 rows.  A CTA streams a super-tile
 // through its shared-memory stages a sub-tile at a time and keeps only the row
 // masks (1 bit per row, in row order) and the per-chunk counts of it, in one
 // of three super-tile buffers.
@@ -222,18 +222,21 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 //                   from sub-tile to sub-tile), store masks and chunk counts
 //                   into the super-tile's buffer and free the stage at once
 //                   (empty[s]); after their part of super-tile j (evald[b])
-//                   they write the selected rows of super-tile j-1, reading
-//                   the projected values of those rows from global memory,
-//                   and release that buffer (freeb[b]);
+//                   they go on with j+1 (once buffer b of j+1 is free);
 //   look-back warp  sums super-tile j's chunk counts, publishes its aggregate,
 //                   finds its exclusive prefix by decoupled look-back,
 //                   publishes the inclusive prefix and the chunk prefixes
-//                   (done[b]) while the consumers already stream j+1.
+//                   (done[b]) while the consumers already stream j+1;
+//   writer warps    (kPdWriters) write the selected rows of each looked-back
+//                   super-tile, reading the projected values of those rows
+//                   from global memory, and release its buffer (freeb[b]).
 // The write step ranks the super-tile's selected rows in row order and hands
-// out batches of 32 consecutive ranks to the warps: a lane finds its row from
-// the chunk prefixes and the row-order mask words, all its loads are in
-// flight together, and a batch's stores are contiguous.
-// No step waits for all consumer warps at once, so the stages keep streaming.
+// out batches of 32 consecutive ranks to the writer warps, kPdBatches at a
+// time: a lane finds its rows from the chunk prefixes and the row-order mask
+// words, all their loads are in flight together, and a batch's stores are
+// contiguous.  The gathers' DRAM round trips never hold a consumer warp, so a
+// stage is released as soon as it is evaluated and the stages keep streaming;
+// up to kPdBufs super-tiles separate evaluation from writing.
 // A CTA works on its super-tiles in increasing order, and what a super-tile
 // waits for (free stages, a free buffer, the look-backs of the CTA's earlier
 // super-tiles, the aggregates of smaller super-tiles) only involves smaller
@@ -244,7 +247,9 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 
 namespace {
 
-constexpr uint32_t kPdBufs = 3;      // super-tile buffers: evaluating j+1, look-back of j, scatter of j-1
+constexpr uint32_t kPdBufs = 4;      // super-tile buffers: evaluating j+1, look-back of j, writing j-1 and j-2
+constexpr int kPdWriters = 4;        // writer warps
+constexpr uint32_t kPdBatches = 4;   // batches of 32 rows a writer lane has in flight
 constexpr uint32_t kMaskWords = 8;   // 256 rows of a chunk, 32 per word, in row order
 
 // Shared-memory layout (bytes from the dynamic base) for S stages.
@@ -303,6 +308,26 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32
     return __all_sync(0xFFFFFFFFu, ok);
 }
 
+// The same, but it also gives up (false) as soon as another warp of the CTA
+// has flagged a failure: a wait on a role that stopped would otherwise last
+// its full bound.
+__device__ __forceinline__ bool warp_wait_live(uint64_t* bar, uint32_t parity, const uint32_t* s_fail,
+                                               uint32_t sleep_ns) {
+    bool ok = mbar_try_wait(bar, parity);
+    if (!ok) {
+        const unsigned long long t0 = global_ns();
+        while (true) {
+            if (sleep_ns) __nanosleep(sleep_ns);
+            if (mbar_try_wait(bar, parity)) {
+                ok = true;
+                break;
+            }
+            if (*reinterpret_cast<const volatile uint32_t*>(s_fail) || global_ns() - t0 > kWaitNs) break;
+        }
+    }
+    return __all_sync(0xFFFFFFFFu, ok);
+}
+
 __device__ __forceinline__ void fail_flag(const PushdownArgs& a, uint32_t* s_fail) {
     atomicOr(a.err, 1u);
     atomicOr(s_fail, 1u);
@@ -337,74 +362,92 @@ __device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t o) {
     return pos;
 }
 
-// Writes the selected rows of the super-tile in buffer b (first row R0) to
-// output positions excl + rank.  This warp takes the batches of 32 ranks
-// first, first + step, ...; ranks at positions >= max_rows are not written.
-__device__ __forceinline__ void scatter_super(const PushdownArgs& a, const PdSmem& sm, uint32_t b, int64_t R0,
-                                              unsigned long long excl, uint32_t first, uint32_t step, uint32_t lane) {
-    const uint32_t tot = sm.stot[b];
-    const unsigned long long room = a.max_rows - excl;   // excl < max_rows
-    const uint32_t n = room < tot ? static_cast<uint32_t>(room) : tot;
+// Row of rank r among the selected rows of the super-tile in buffer b.
+__device__ __forceinline__ int64_t rank_row(const PdSmem& sm, uint32_t b, int64_t R0, uint32_t r) {
     const uint32_t nch = sm.nch[b];
     const uint32_t* cp = sm.cp + b * kPdpMaxChunks;
     const uint32_t* mw = sm.mask + b * kPdpMaxChunks * kMaskWords;
-    for (uint32_t r0 = first * 32u; r0 < n; r0 += step * 32u) {
-        const uint32_t r = r0 + lane;
-        const bool act = r < n;
-        int64_t row = 0;
-        if (act) {
-            // the chunk: the last one whose prefix is <= r (cp[0] = 0)
-            uint32_t lo = 0, hi = nch;
-            while (hi - lo > 1u) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (cp[mid] <= r) lo = mid;
-                else hi = mid;
-            }
-            uint32_t o = r - cp[lo];
-            const uint4* w4 = reinterpret_cast<const uint4*>(mw + lo * kMaskWords);
-            const uint4 x = w4[0], y = w4[1];
-            const uint32_t wv[kMaskWords] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-            uint32_t word = 0, wbase = 0;
-            bool found = false;
+    // the chunk: the last one whose prefix is <= r (cp[0] = 0)
+    uint32_t lo = 0, hi = nch;
+    while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (cp[mid] <= r) lo = mid;
+        else hi = mid;
+    }
+    uint32_t o = r - cp[lo];
+    const uint4* w4 = reinterpret_cast<const uint4*>(mw + lo * kMaskWords);
+    const uint4 x = w4[0], y = w4[1];
+    const uint32_t wv[kMaskWords] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    uint32_t word = 0, wbase = 0;
+    bool found = false;
 #pragma unroll
-            for (uint32_t k = 0; k < kMaskWords; ++k) {
-                const uint32_t c = __popc(wv[k]);
-                if (!found) {
-                    if (o < c) {
-                        found = true;
-                        word = wv[k];
-                        wbase = 32u * k;
-                    } else {
-                        o -= c;
-                    }
+    for (uint32_t k = 0; k < kMaskWords; ++k) {
+        const uint32_t c = __popc(wv[k]);
+        if (!found) {
+            if (o < c) {
+                found = true;
+                word = wv[k];
+                wbase = 32u * k;
+            } else {
+                o -= c;
+            }
+        }
+    }
+    return R0 + static_cast<int64_t>(lo) * kChunkRows + wbase + select_bit(word, o);
+}
+
+// Writes the selected rows of the super-tile in buffer b (first row R0) to
+// output positions excl + rank.  This warp takes the groups of kPdBatches
+// batches of 32 ranks first, first + step, ...; ranks at positions >= max_rows
+// are not written.  Every load of a group is issued before its first store.
+__device__ __forceinline__ void scatter_super(const PushdownArgs& a, const PdSmem& sm, uint32_t b, int64_t R0,
+                                              unsigned long long excl, uint32_t first, uint32_t step, uint32_t lane) {
+    constexpr uint32_t K = kPdBatches;
+    const uint32_t tot = sm.stot[b];
+    const unsigned long long room = a.max_rows - excl;   // excl < max_rows
+    const uint32_t n = room < tot ? static_cast<uint32_t>(room) : tot;
+    for (uint32_t r0 = first * 32u * K; r0 < n; r0 += step * 32u * K) {
+        int64_t row[K];
+        bool act[K];
+#pragma unroll
+        for (uint32_t k = 0; k < K; ++k) {
+            const uint32_t r = r0 + 32u * k + lane;
+            act[k] = r < n;
+            row[k] = act[k] ? rank_row(sm, b, R0, r) : 0;
+        }
+        for (uint32_t j0 = 0; j0 < a.n_proj; j0 += 4) {
+            unsigned long long v[4][K];
+#pragma unroll
+            for (uint32_t q = 0; q < 4; ++q) {   // all loads first: they are in flight together
+                const uint32_t j = j0 + q;
+#pragma unroll
+                for (uint32_t k = 0; k < K; ++k) {
+                    v[q][k] = 0;
+                    if (act[k] && j < a.n_proj)
+                        v[q][k] = a.proj_width[j] == 8
+                                      ? __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[j]) + row[k])
+                                      : __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[j]) + row[k]);
                 }
             }
-            row = R0 + static_cast<int64_t>(lo) * kChunkRows + wbase + select_bit(word, o);
-        }
-        const unsigned long long pos = excl + r;
-        for (uint32_t j0 = 0; j0 < a.n_proj; j0 += 8) {
-            unsigned long long v[8];
 #pragma unroll
-            for (uint32_t q = 0; q < 8; ++q) {   // all loads first: they are in flight together
+            for (uint32_t q = 0; q < 4; ++q) {
                 const uint32_t j = j0 + q;
-                v[q] = 0;
-                if (act && j < a.n_proj)
-                    v[q] = a.proj_width[j] == 8
-                               ? __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[j]) + row)
-                               : __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[j]) + row);
-            }
+                if (j >= a.n_proj) break;
 #pragma unroll
-            for (uint32_t q = 0; q < 8; ++q) {
-                const uint32_t j = j0 + q;
-                if (act && j < a.n_proj) {
+                for (uint32_t k = 0; k < K; ++k) {
+                    if (!act[k]) continue;
+                    const unsigned long long pos = excl + r0 + 32u * k + lane;
                     if (a.proj_width[j] == 8)
-                        reinterpret_cast<unsigned long long*>(a.proj_dst[j])[pos] = v[q];
+                        reinterpret_cast<unsigned long long*>(a.proj_dst[j])[pos] = v[q][k];
                     else
-                        reinterpret_cast<unsigned int*>(a.proj_dst[j])[pos] = static_cast<unsigned int>(v[q]);
+                        reinterpret_cast<unsigned int*>(a.proj_dst[j])[pos] = static_cast<unsigned int>(v[q][k]);
                 }
             }
         }
-        if (act && a.rowids) a.rowids[pos] = static_cast<long long>(row);
+        if (a.rowids)
+#pragma unroll
+            for (uint32_t k = 0; k < K; ++k)
+                if (act[k]) a.rowids[excl + r0 + 32u * k + lane] = static_cast<long long>(row[k]);
     }
 }
 
@@ -415,7 +458,9 @@ __device__ __forceinline__ void scatter_super(const PushdownArgs& a, const PdSme
 // count scan), so the sub-tile size (a.tile_rows, a multiple of G chunks) is
 // independent of W and G.
 template <int W, int G>
-__global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(const __grid_constant__ PushdownArgs a) {
+__global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
+    pushdown_persistent_kernel(const __grid_constant__ PushdownArgs a) {
+    constexpr uint32_t PRODUCER = W + kPdWriters, LOOKBACK = W + kPdWriters + 1;
     const uint32_t TR = a.tile_rows;                   // rows per sub-tile
     const uint32_t NCH = TR / kChunkRows;              // chunks per sub-tile
     const uint32_t SR = a.super_rows;                  // rows per super-tile
@@ -438,7 +483,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
         for (uint32_t b = 0; b < kPdBufs; ++b) {
             mbar_init(&sm.evald[b], W);
             mbar_init(&sm.done[b], 1);
-            mbar_init(&sm.freeb[b], W);
+            mbar_init(&sm.freeb[b], kPdWriters);
         }
         fence_mbar_init();
         s_fail = 0;
@@ -452,7 +497,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
     __syncthreads();
     const uint8_t* blob = smem + a.smem_prog_off;
 
-    if (warp == W) {
+    if (warp == PRODUCER) {
         // ------------------------------- producer -------------------------------
         const uint64_t pol = policy_evict_first();
         uint32_t s = 0, ph = 0;
@@ -518,7 +563,7 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             }
         }
         if (lane == 0) s_issued = k;
-    } else if (warp == W + 1) {
+    } else if (warp == LOOKBACK) {
         // ------------------------------- look-back ------------------------------
         for (uint32_t j = 0;; ++j) {
             const uint32_t b = j % kPdBufs, par = (j / kPdBufs) & 1u;
@@ -527,7 +572,11 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
                 break;
             }
             const long long t = sm.st_id[b];
-            if (t < 0) break;
+            if (t < 0) {   // the end: pass the sentinel on to the writers
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.done[b]);
+                break;
+            }
             // chunk counts from the row words, their prefix in row order (chunks
             // past the super-tile's rows count 0) and the total
             const uint32_t nch = sm.nch[b];
@@ -570,18 +619,16 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             if (lane == 0) mbar_arrive(&sm.done[b]);   // release: offsets visible to the consumers
             if (!ok) break;
         }
-    } else {
+    } else if (warp < W) {
         // ------------------------------- consumers ------------------------------
         const Instr* ins = reinterpret_cast<const Instr*>(blob + a.instr_off);
         const uint8_t* pool = blob + a.pool_off;
-        const bool writes = a.n_proj > 0 || a.rowids != nullptr;
         uint32_t s = 0, ph = 0;
         uint32_t rot = 0;       // running group count: group k of a sub-tile belongs to warp (rot + k) % W
-        long long prev_id = -1;
         for (uint32_t j = 0;; ++j) {
             const uint32_t b = j % kPdBufs;
             // ---- the buffer was last used by super-tile j-3: wait until every warp wrote its rows ----
-            if (j >= kPdBufs && !warp_wait(&sm.freeb[b], ((j / kPdBufs) - 1) & 1u, lane)) {
+            if (j >= kPdBufs && !warp_wait_live(&sm.freeb[b], ((j / kPdBufs) - 1) & 1u, &s_fail, 0)) {
                 if (lane == 0) fail_flag(a, &s_fail);
                 break;
             }
@@ -639,29 +686,35 @@ __global__ void __launch_bounds__((W + 2) * 32, 1) pushdown_persistent_kernel(co
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&sm.evald[b]);   // release: masks, counts, id visible
-            // ---- write this warp's batches of super-tile j-1's selected rows ----
-            if (prev_id >= 0) {
-                const uint32_t pb = (j + kPdBufs - 1) % kPdBufs;
-                const bool ok = warp_wait(&sm.done[pb], ((j - 1) / kPdBufs) & 1u, lane);
-                if (!ok) {
-                    if (lane == 0) fail_flag(a, &s_fail);
-                    break;
-                }
-                if (writes && !volatile_flag(&s_fail)) {
-                    const unsigned long long excl = sm.excl[pb];
-                    // the first batch goes to a different warp for each super-tile
-                    const uint32_t first = (warp + W - static_cast<uint32_t>(prev_id % W)) % W;
-                    if (excl < a.max_rows) scatter_super(a, sm, pb, prev_id * static_cast<int64_t>(SR), excl, first, W, lane);
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&sm.freeb[pb]);
-            }
             if (t < 0 || volatile_flag(&s_fail)) break;
-            prev_id = t;
+        }
+    } else {
+        // -------------------------------- writers -------------------------------
+        const uint32_t wv = warp - W;
+        const bool writes = a.n_proj > 0 || a.rowids != nullptr;
+        for (uint32_t j = 0;; ++j) {
+            const uint32_t b = j % kPdBufs;
+            // idle writers sleep between tries: they would take issue slots from the consumers
+            if (!warp_wait_live(&sm.done[b], (j / kPdBufs) & 1u, &s_fail, 100)) {
+                if (lane == 0) fail_flag(a, &s_fail);
+                break;
+            }
+            const long long t = sm.st_id[b];
+            if (t < 0) break;
+            if (writes && !volatile_flag(&s_fail)) {
+                const unsigned long long excl = sm.excl[b];
+                // the first group of batches goes to a different writer for each super-tile
+                const uint32_t first = (wv + kPdWriters - static_cast<uint32_t>(t % kPdWriters)) % kPdWriters;
+                if (excl < a.max_rows)
+                    scatter_super(a, sm, b, t * static_cast<int64_t>(SR), excl, first, kPdWriters, lane);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&sm.freeb[b]);
+            if (volatile_flag(&s_fail)) break;
         }
     }
     __syncthreads();
-    if (s_fail && warp == W && lane == 0) {
+    if (s_fail && warp == PRODUCER && lane == 0) {
         // copies issued for stages nobody consumed must land before the CTA exits
         const long long issued = s_issued;
         for (long long k = issued > (long long)S ? issued - S : 0; k < issued; ++k)
@@ -720,13 +773,13 @@ cudaError_t launch_pushdown_persistent(const PushdownArgs& a, int grid, int warp
         a.super_rows > static_cast<uint32_t>(kPdpMaxChunks * kChunkRows))
         return cudaErrorInvalidValue;
     if (warps == 8 && chunks_per_warp == 1)
-        pushdown_persistent_kernel<8, 1><<<grid, 10 * 32, a.smem_bytes, st>>>(a);
+        pushdown_persistent_kernel<8, 1><<<grid, (8 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 8 && chunks_per_warp == 2)
-        pushdown_persistent_kernel<8, 2><<<grid, 10 * 32, a.smem_bytes, st>>>(a);
+        pushdown_persistent_kernel<8, 2><<<grid, (8 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 16 && chunks_per_warp == 1)
-        pushdown_persistent_kernel<16, 1><<<grid, 18 * 32, a.smem_bytes, st>>>(a);
+        pushdown_persistent_kernel<16, 1><<<grid, (16 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 16 && chunks_per_warp == 2)
-        pushdown_persistent_kernel<16, 2><<<grid, 18 * 32, a.smem_bytes, st>>>(a);
+        pushdown_persistent_kernel<16, 2><<<grid, (16 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -3,12 +3,15 @@ dimensions, 64 probes in one autotuned batch plan: the launch the bench
 times) and for the 1.2B-row table with its 256 probes.
 
 * Star schema: every batched count equals the threaded oracle's count.
-* 1.2B rows (too many row evaluations for the oracle on all 256 probes):
-  batched counts equal one-launch-per-probe counts; count(A) + count(NOT A) = n;
-  the oracle's counts on a 2M-row window (a view of the same columns); the
-  push-down of 3 columns for a few probes returns exactly count rows, strictly
-  increasing row ids, values equal to the table's, and every returned row
-  satisfies the predicate per the oracle."""
+* 1.2B rows: the threaded oracle over the whole table (copied to the host)
+  gives the batched count of every 16th probe (s from 1e-6 to 0.9, 16
+  probes), and the whole push-down output of the probes nearest s = 1e-4 and
+  1e-2 (row ids and the 3 projected columns, byte for byte); batched counts
+  equal one-launch-per-probe counts; count(A) + count(NOT A) = n; the
+  oracle's counts on a 2M-row window (a view of the same columns) for every
+  8th probe; the push-down of 3 columns for a few more probes returns exactly
+  count rows, strictly increasing row ids, values equal to the table's, and
+  every returned row satisfies the predicate per the oracle."""
 import os
 
 import numpy as np
@@ -37,13 +40,39 @@ def test_star_schema_full_size(ctx, dev):
         del ot
 
 
-def test_large_table_full_size(ctx, dev):
+@pytest.fixture(scope="module")
+def large(dev):
     t = dg.config5_table(device=dev)
-    n = t.n_rows
     T = sel.Table(t.columns)
     trees = dg.config5_predicates()
     preds = [sel.Predicate(T, tr) for tr in trees]
-    batched = sel.BatchPlan(ctx, preds, [T] * len(preds), autotune=False).run()
+    batched = sel.BatchPlan(sel.Context(), preds, [T] * len(preds), autotune=False).run()
+    yield t, T, trees, preds, batched
+    del t, T
+    torch.cuda.empty_cache()
+
+
+def test_large_table_against_the_oracle_on_every_row(ctx, large):
+    t, T, trees, preds, batched = large
+    ot = oracle.OTable.from_table(t)   # 28.8 GB on the host
+    for i in range(0, 256, 16):
+        assert batched[i] == oracle.count(ot, trees[i], threads=THREADS), i
+    proj = [t.index(c) for c in dg.CONFIG5_PROJECTION]
+    targets = np.logspace(-6, np.log10(0.9), 256)
+    for s in (1e-4, 1e-2):
+        i = int(np.argmin(np.abs(np.log(targets) - np.log(s))))
+        want = oracle.select(ot, trees[i], threads=THREADS)
+        st, cnt, cols, ids = ctx.pushdown(preds[i], T, proj, batched[i])
+        assert st == sel.SEL_OK and cnt == len(want) == batched[i]
+        assert np.array_equal(ids.cpu().numpy(), want)
+        for c, out in zip(proj, cols):
+            assert out.cpu().numpy().tobytes() == ot.arrays[c][want].tobytes(), (i, c)
+    del ot
+
+
+def test_large_table_full_size(ctx, dev, large):
+    t, T, trees, preds, batched = large
+    n = t.n_rows
     picks = [0, 37, 101, 150, 200, 255]
     for i in picks:
         assert ctx.count(preds[i], T) == batched[i]

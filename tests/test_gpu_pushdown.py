@@ -55,7 +55,7 @@ def proj_cfg2(t):
 
 
 # 1536, 2560 and 3584 rows are sub-tiles of the persistent kernel whose
-# super-tiles (15360, 15360, 14336 rows) are not powers of two; 256 and 1280
+# super-tiles (32256, 30720, 32256 rows) are not powers of two; 256 and 1280
 # are not whole 2-chunk groups and run on the one-CTA-per-tile kernel.
 @pytest.mark.parametrize("tile_rows", [0, 256, 1024, 1280, 1536, 2048, 2560, 3584, 4096, 8192])
 def test_config2_selectivities(ctx, medium, tile_rows):
@@ -74,7 +74,7 @@ def test_persistent_variants(ctx, dev, medium, variant):
     ctx.set_scan_variant(*variant)
     for s in (1e-3, 0.1):
         check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=21), proj_cfg2(t))
-    if variant[1] == 1:   # 3-chunk sub-tiles: 21 of them make a 16128-row super-tile
+    if variant[1] == 1:   # 3-chunk sub-tiles: 42 of them make a 32256-row super-tile
         ctx.set_scan_shape(768, 0, 0)
         check_pushdown(ctx, T, ot, dg.config2_predicate(0.1, seed=22), proj_cfg2(t))
         ctx.set_scan_shape(0, 0, 0)
@@ -149,8 +149,8 @@ def test_unaligned_columns(ctx, medium):
 def test_lookback_wait_times_out_and_context_recovers(ctx, dev, tile_rows):
     """A tile that never publishes makes its successors' bounded waits run out:
     the call returns SEL_ERR_TIMEOUT, and the context works afterwards (the
-    persistent kernel, whose look-back unit is a super-tile of up to 16384
-    rows -- 14336 for 3584-row sub-tiles --, and the one-CTA-per-tile kernel
+    persistent kernel, whose look-back unit is a super-tile of up to 32768
+    rows -- 32256 for 3584-row sub-tiles --, and the one-CTA-per-tile kernel
     for 1280-row tiles)."""
     t = dg.tiny_table(4 * 32768 + 1000, seed=3)
     ot = oracle.OTable.from_table(t)
