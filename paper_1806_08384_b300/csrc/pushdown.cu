@@ -254,14 +254,17 @@ constexpr uint32_t kMaskWords = 8;   // 256 rows of a chunk, 32 per word, in row
 
 // Shared-memory layout (bytes from the dynamic base) for S stages.
 struct PdLayout {
-    uint32_t tile, st_id, excl, nch, stot, cp, mask, end;
+    uint32_t tile, st_id, excl, nch, stot, claim, left, ngr, cp, mask, end;
     __host__ __device__ explicit PdLayout(uint32_t S) {
         tile = 16u * S + 3u * 8u * kPdBufs;           // after full[S], empty[S], evald/done/freeb[kPdBufs]
         st_id = tile + 8u * S;
         excl = st_id + 8u * kPdBufs;
         nch = excl + 8u * kPdBufs;
         stot = nch + 4u * kPdBufs;
-        cp = stot + 4u * kPdBufs;
+        claim = stot + 4u * kPdBufs;
+        left = claim + 4u * kPdBufs;
+        ngr = left + 4u * kPdBufs;
+        cp = ngr + 4u * kPdBufs;
         mask = (cp + 4u * kPdBufs * kPdpMaxChunks + 15u) & ~15u;   // read as uint4
         end = mask + 4u * kPdBufs * kPdpMaxChunks * kMaskWords;
     }
@@ -275,6 +278,9 @@ struct PdSmem {
     unsigned long long* excl;            // [kPdBufs] exclusive prefix of each buffer's super-tile
     uint32_t* nch;                       // [kPdBufs] chunks of each buffer's super-tile that hold rows
     uint32_t* stot;                      // [kPdBufs] selected rows of each buffer's super-tile
+    uint32_t* claim;                     // [kPdBufs] generation << 20 | next write group to hand out
+    uint32_t* left;                      // [kPdBufs] write groups not yet finished
+    uint32_t* ngr;                       // [kPdBufs] write groups of the buffer's super-tile
     uint32_t* cp;                        // [kPdBufs][kPdpMaxChunks] chunk prefixes
     uint32_t* mask;                      // [kPdBufs][kPdpMaxChunks][kMaskWords] row masks, row order
 };
@@ -292,6 +298,9 @@ __device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S) {
     m.excl = reinterpret_cast<unsigned long long*>(smem + L.excl);
     m.nch = reinterpret_cast<uint32_t*>(smem + L.nch);
     m.stot = reinterpret_cast<uint32_t*>(smem + L.stot);
+    m.claim = reinterpret_cast<uint32_t*>(smem + L.claim);
+    m.left = reinterpret_cast<uint32_t*>(smem + L.left);
+    m.ngr = reinterpret_cast<uint32_t*>(smem + L.ngr);
     m.cp = reinterpret_cast<uint32_t*>(smem + L.cp);
     m.mask = reinterpret_cast<uint32_t*>(smem + L.mask);
     return m;
@@ -396,59 +405,103 @@ __device__ __forceinline__ int64_t rank_row(const PdSmem& sm, uint32_t b, int64_
     return R0 + static_cast<int64_t>(lo) * kChunkRows + wbase + select_bit(word, o);
 }
 
-// Writes the selected rows of the super-tile in buffer b (first row R0) to
-// output positions excl + rank.  This warp takes the groups of kPdBatches
-// batches of 32 ranks first, first + step, ...; ranks at positions >= max_rows
-// are not written.  Every load of a group is issued before its first store.
-__device__ __forceinline__ void scatter_super(const PushdownArgs& a, const PdSmem& sm, uint32_t b, int64_t R0,
-                                              unsigned long long excl, uint32_t first, uint32_t step, uint32_t lane) {
+// Writes group g of the selected rows of the super-tile in buffer b (first
+// row R0): ranks g * 32 * kPdBatches .. + 32 * kPdBatches - 1 below n, to
+// output positions excl + rank.  Every load of the group is issued before its
+// first store.
+__device__ __forceinline__ void scatter_group(const PushdownArgs& a, const PdSmem& sm, uint32_t b, int64_t R0,
+                                              unsigned long long excl, uint32_t n, uint32_t g, uint32_t lane) {
     constexpr uint32_t K = kPdBatches;
-    const uint32_t tot = sm.stot[b];
-    const unsigned long long room = a.max_rows - excl;   // excl < max_rows
-    const uint32_t n = room < tot ? static_cast<uint32_t>(room) : tot;
-    for (uint32_t r0 = first * 32u * K; r0 < n; r0 += step * 32u * K) {
-        int64_t row[K];
-        bool act[K];
+    const uint32_t r0 = g * 32u * K;
+    int64_t row[K];
+    bool act[K];
 #pragma unroll
-        for (uint32_t k = 0; k < K; ++k) {
-            const uint32_t r = r0 + 32u * k + lane;
-            act[k] = r < n;
-            row[k] = act[k] ? rank_row(sm, b, R0, r) : 0;
-        }
-        for (uint32_t j0 = 0; j0 < a.n_proj; j0 += 4) {
-            unsigned long long v[4][K];
-#pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {   // all loads first: they are in flight together
-                const uint32_t j = j0 + q;
-#pragma unroll
-                for (uint32_t k = 0; k < K; ++k) {
-                    v[q][k] = 0;
-                    if (act[k] && j < a.n_proj)
-                        v[q][k] = a.proj_width[j] == 8
-                                      ? __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[j]) + row[k])
-                                      : __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[j]) + row[k]);
-                }
-            }
-#pragma unroll
-            for (uint32_t q = 0; q < 4; ++q) {
-                const uint32_t j = j0 + q;
-                if (j >= a.n_proj) break;
-#pragma unroll
-                for (uint32_t k = 0; k < K; ++k) {
-                    if (!act[k]) continue;
-                    const unsigned long long pos = excl + r0 + 32u * k + lane;
-                    if (a.proj_width[j] == 8)
-                        reinterpret_cast<unsigned long long*>(a.proj_dst[j])[pos] = v[q][k];
-                    else
-                        reinterpret_cast<unsigned int*>(a.proj_dst[j])[pos] = static_cast<unsigned int>(v[q][k]);
-                }
-            }
-        }
-        if (a.rowids)
-#pragma unroll
-            for (uint32_t k = 0; k < K; ++k)
-                if (act[k]) a.rowids[excl + r0 + 32u * k + lane] = static_cast<long long>(row[k]);
+    for (uint32_t k = 0; k < K; ++k) {
+        const uint32_t r = r0 + 32u * k + lane;
+        act[k] = r < n;
+        row[k] = act[k] ? rank_row(sm, b, R0, r) : 0;
     }
+    for (uint32_t j0 = 0; j0 < a.n_proj; j0 += 4) {
+        unsigned long long v[4][K];
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {   // all loads first: they are in flight together
+            const uint32_t j = j0 + q;
+#pragma unroll
+            for (uint32_t k = 0; k < K; ++k) {
+                v[q][k] = 0;
+                if (act[k] && j < a.n_proj)
+                    v[q][k] = a.proj_width[j] == 8
+                                  ? __ldg(reinterpret_cast<const unsigned long long*>(a.proj_src[j]) + row[k])
+                                  : __ldg(reinterpret_cast<const unsigned int*>(a.proj_src[j]) + row[k]);
+            }
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < 4; ++q) {
+            const uint32_t j = j0 + q;
+            if (j >= a.n_proj) break;
+#pragma unroll
+            for (uint32_t k = 0; k < K; ++k) {
+                if (!act[k]) continue;
+                const unsigned long long pos = excl + r0 + 32u * k + lane;
+                if (a.proj_width[j] == 8)
+                    reinterpret_cast<unsigned long long*>(a.proj_dst[j])[pos] = v[q][k];
+                else
+                    reinterpret_cast<unsigned int*>(a.proj_dst[j])[pos] = static_cast<unsigned int>(v[q][k]);
+            }
+        }
+    }
+    if (a.rowids)
+#pragma unroll
+        for (uint32_t k = 0; k < K; ++k)
+            if (act[k]) a.rowids[excl + r0 + 32u * k + lane] = static_cast<long long>(row[k]);
+}
+
+constexpr uint32_t kNoGroup = 0xFFFFFFFFu;
+
+// Hands out the next write group of buffer b's super-tile of generation gen
+// (the CTA's super-tile ordinal mod 4096): kNoGroup when all are handed out,
+// or when the buffer has moved on to a later super-tile.  Called by one lane.
+__device__ __forceinline__ uint32_t claim_group(uint32_t* word, uint32_t gen, uint32_t ngr) {
+    uint32_t old = *reinterpret_cast<volatile uint32_t*>(word);
+    while (true) {
+        if ((old >> 20) != gen || (old & 0xFFFFFu) >= ngr) return kNoGroup;
+        const uint32_t prev = atomicCAS(word, old, old + 1u);
+        if (prev == old) return old & 0xFFFFFu;
+        old = prev;
+    }
+}
+
+__device__ __forceinline__ uint32_t atom_add_acq_rel_cta(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v)
+                 : "memory");
+    return old;
+}
+
+// Claims and writes groups of buffer b's super-tile (its ordinal jj in the
+// CTA's order) until none is left; the warp that finishes the last group
+// frees the buffer (freeb[b]).  The buffer's look-back (done[b]) must have
+// completed.  Returns the number of groups this warp wrote.
+__device__ __forceinline__ uint32_t write_groups(const PushdownArgs& a, const PdSmem& sm, uint32_t b, uint32_t jj,
+                                                 uint32_t SR, uint32_t lane, uint32_t max_groups) {
+    const long long t = sm.st_id[b];
+    const unsigned long long excl = sm.excl[b];
+    const uint32_t ngr = sm.ngr[b];
+    const uint32_t n = excl < a.max_rows ? (a.max_rows - excl < sm.stot[b] ? static_cast<uint32_t>(a.max_rows - excl)
+                                                                           : sm.stot[b])
+                                         : 0u;
+    uint32_t done_groups = 0;
+    while (done_groups < max_groups) {
+        uint32_t g = 0;
+        if (lane == 0) g = claim_group(&sm.claim[b], jj & 0xFFFu, ngr);
+        g = __shfl_sync(0xFFFFFFFFu, g, 0);
+        if (g == kNoGroup) break;
+        scatter_group(a, sm, b, t * static_cast<int64_t>(SR), excl, n, g, lane);
+        ++done_groups;
+        __syncwarp();   // every lane's reads of the buffer come before its release
+        if (lane == 0 && atom_add_acq_rel_cta(&sm.left[b], 0xFFFFFFFFu) == 1u) mbar_arrive(&sm.freeb[b]);
+    }
+    return done_groups;
 }
 
 }  // namespace
@@ -483,7 +536,7 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
         for (uint32_t b = 0; b < kPdBufs; ++b) {
             mbar_init(&sm.evald[b], W);
             mbar_init(&sm.done[b], 1);
-            mbar_init(&sm.freeb[b], kPdWriters);
+            mbar_init(&sm.freeb[b], 1);   // the warp that finishes the last write group (or the look-back)
         }
         fence_mbar_init();
         s_fail = 0;
@@ -609,14 +662,26 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
                 if (lane == 0 && ok && t != a.skip_publish_tile)
                     st_relaxed(&a.status[t], kFlagInc | ((excl + tile_cnt) & kValMask));
             }
+            // write groups of kPdBatches batches of 32 rows (none past max_rows)
+            const bool writes = a.n_proj > 0 || a.rowids != nullptr;
+            const unsigned long long n_write =
+                (!writes || excl >= a.max_rows) ? 0ull
+                                                : (a.max_rows - excl < tile_cnt ? a.max_rows - excl : tile_cnt);
+            const uint32_t ngr = static_cast<uint32_t>((n_write + 32u * kPdBatches - 1) / (32u * kPdBatches));
             if (lane == 0) {
                 if (!ok) fail_flag(a, &s_fail);
                 sm.excl[b] = excl;
                 sm.stot[b] = tile_cnt;
+                sm.ngr[b] = ok ? ngr : 0u;
+                sm.left[b] = ok ? ngr : 0u;
+                sm.claim[b] = (j & 0xFFFu) << 20;
                 if (t == n_super - 1) *a.total = excl + tile_cnt;
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.done[b]);   // release: offsets visible to the consumers
+            if (lane == 0) {
+                mbar_arrive(&sm.done[b]);                  // release: offsets and groups visible to the writers
+                if (!ok || ngr == 0) mbar_arrive(&sm.freeb[b]);   // nothing to write: the buffer is free
+            }
             if (!ok) break;
         }
     } else if (warp < W) {
@@ -627,10 +692,25 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
         uint32_t rot = 0;       // running group count: group k of a sub-tile belongs to warp (rot + k) % W
         for (uint32_t j = 0;; ++j) {
             const uint32_t b = j % kPdBufs;
-            // ---- the buffer was last used by super-tile j-3: wait until every warp wrote its rows ----
-            if (j >= kPdBufs && !warp_wait_live(&sm.freeb[b], ((j / kPdBufs) - 1) & 1u, &s_fail, 0)) {
-                if (lane == 0) fail_flag(a, &s_fail);
-                break;
+            // ---- the buffer was last used by super-tile j - kPdBufs: until its rows are written,
+            //      help write them (a consumer waiting here has nothing else to do) ----
+            if (j >= kPdBufs) {
+                const uint32_t par = ((j / kPdBufs) - 1) & 1u;
+                const unsigned long long w0 = __shfl_sync(0xFFFFFFFFu, global_ns(), 0);
+                bool ok = true;
+                while (!__all_sync(0xFFFFFFFFu, mbar_try_wait(&sm.freeb[b], par))) {
+                    if (__all_sync(0xFFFFFFFFu, mbar_try_wait(&sm.done[b], par)) &&
+                        write_groups(a, sm, b, j - kPdBufs, SR, lane, 1u) > 0)
+                        continue;
+                    if (volatile_flag(&s_fail) || __shfl_sync(0xFFFFFFFFu, global_ns(), 0) - w0 > kWaitNs) {
+                        ok = false;
+                        break;
+                    }
+                }
+                if (!ok) {
+                    if (lane == 0) fail_flag(a, &s_fail);
+                    break;
+                }
             }
             // ---- evaluate super-tile j, sub-tile by sub-tile ----
             long long t = -1;
@@ -690,8 +770,6 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
         }
     } else {
         // -------------------------------- writers -------------------------------
-        const uint32_t wv = warp - W;
-        const bool writes = a.n_proj > 0 || a.rowids != nullptr;
         for (uint32_t j = 0;; ++j) {
             const uint32_t b = j % kPdBufs;
             // idle writers sleep between tries: they would take issue slots from the consumers
@@ -699,18 +777,8 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
                 if (lane == 0) fail_flag(a, &s_fail);
                 break;
             }
-            const long long t = sm.st_id[b];
-            if (t < 0) break;
-            if (writes && !volatile_flag(&s_fail)) {
-                const unsigned long long excl = sm.excl[b];
-                // the first group of batches goes to a different writer for each super-tile
-                const uint32_t first = (wv + kPdWriters - static_cast<uint32_t>(t % kPdWriters)) % kPdWriters;
-                if (excl < a.max_rows)
-                    scatter_super(a, sm, b, t * static_cast<int64_t>(SR), excl, first, kPdWriters, lane);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.freeb[b]);
-            if (volatile_flag(&s_fail)) break;
+            if (sm.st_id[b] < 0 || volatile_flag(&s_fail)) break;
+            write_groups(a, sm, b, j, SR, lane, 0xFFFFFFFFu);
         }
     }
     __syncthreads();
