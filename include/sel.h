@@ -277,16 +277,27 @@ sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stage
  * The same pair selects the persistent push-down kernel's consumer warps and
  * chunks per pass where that kernel has the variant (8 or 16 warps, 1 or 2
  * chunks; otherwise the push-down takes its one-CTA-per-tile kernel).
- * Results do not depend on the variant. */
+ * The batch plans' column-bucket kernel also takes 11 or 15 consumer warps
+ * (1 or 2 chunks per pass); with those pairs sel_count and sel_pushdown keep
+ * their defaults.  Results do not depend on the variant. */
 sel_status sel_ctx_set_scan_variant(sel_ctx* ctx, int32_t consumer_warps, int32_t chunks_per_pass);
 
 /* Number of kernels this context has launched so far (all entry points). */
 uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
 
+/* Super-tile size of the persistent push-down kernel (its look-back unit,
+ * Algorithm 1's output offsets are found per super-tile): the largest multiple
+ * of the kernel's sub-tile that is at most `rows` rows.  0 (the default):
+ * 384 KB of the predicate's columns, but at most 1/16 of a CTA's share of the
+ * table, and at least 32768 and at most 131072 rows.  rows must be
+ * 0 or a multiple of 256 up to 131072, else SEL_ERR_INVALID_ARG.  Results do
+ * not depend on it. */
+sel_status sel_ctx_set_pushdown_super_rows(sel_ctx* ctx, int32_t rows);
+
 /* Test hook for the bounded waits of the push-down look-back: look-back unit
- * skip_tile (a super-tile of the default kernel -- the largest multiple of
- * its tile up to 32768 rows --, a tile of the one-CTA-per-tile kernel; -1:
- * none) never publishes its prefix, and a waiting tile gives up after
+ * skip_tile (a super-tile of the persistent kernel -- see
+ * sel_ctx_set_pushdown_super_rows --, a tile of the one-CTA-per-tile kernel;
+ * -1: none) never publishes its prefix, and a waiting tile gives up after
  * wait_ns nanoseconds (0: the default of 2 s), so that later sel_pushdown
  * calls on this context return SEL_ERR_TIMEOUT instead of waiting forever.
  * The context stays usable; set skip_tile back to -1 to disarm. */

@@ -114,6 +114,7 @@ def _load():
         "sel_ctx_set_scan_variant": (C.c_int, [V, C.c_int32, C.c_int32]),
         "sel_ctx_launch_count": (C.c_uint64, [V]),
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
+        "sel_ctx_set_pushdown_super_rows": (C.c_int, [V, C.c_int32]),
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
         "sel_count_distinct": (C.c_int, [V, P(sel_table), C.c_int32, V, P(C.c_uint64), P(C.c_uint64)]),
         "sel_join_size_estimate": (C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]),
@@ -350,6 +351,10 @@ class Context:
     def set_batch_kernel(self, mode: int):
         """0: the faster of both kernels, 1: interpreter only, 2: bucket kernel only."""
         _check(lib.sel_ctx_set_batch_kernel(self.h, int(mode)), "sel_ctx_set_batch_kernel")
+
+    def set_pushdown_super_rows(self, rows: int):
+        """Super-tile target of the persistent push-down (0: from the table size)."""
+        _check(lib.sel_ctx_set_pushdown_super_rows(self.h, rows), "sel_ctx_set_pushdown_super_rows")
 
     def debug_pushdown_fault(self, skip_tile: int, wait_ns: int = 0):
         _check(lib.sel_ctx_debug_pushdown_fault(self.h, skip_tile, wait_ns), "sel_ctx_debug_pushdown_fault")

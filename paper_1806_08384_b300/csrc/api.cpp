@@ -120,6 +120,7 @@ struct sel_ctx {
     std::map<std::string, sel_batch_plan*> plans;   // sel_count_batch cache
     long long debug_skip_tile = -1;
     unsigned long long debug_wait_ns = kWaitNs;
+    uint32_t pd_super_rows = 0;   // push-down super-tile target (0: chosen from the table size)
 };
 
 struct sel_batch_plan {
@@ -425,8 +426,12 @@ static Shape single_shape(sel_ctx* ctx, uint32_t row_bytes) {
     s.ctas_per_sm = ctx->shape.ctas_per_sm > 0 ? ctx->shape.ctas_per_sm : 1;
     s.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : kMaxTileRows;
     s.auto_tile = ctx->shape.tile_rows <= 0;
-    s.warps = ctx->shape.warps > 0 ? ctx->shape.warps : kScanDefaultWarps;
-    s.group = ctx->shape.group > 0 ? ctx->shape.group : kScanDefaultGroup;
+    s.warps = kScanDefaultWarps;
+    s.group = kScanDefaultGroup;
+    if (ctx->shape.warps > 0 && scan_variant_ok(ctx->shape.warps, ctx->shape.group)) {   // not a bucket-only variant
+        s.warps = ctx->shape.warps;
+        s.group = ctx->shape.group;
+    }
     return s;
 }
 
@@ -507,8 +512,10 @@ extern "C" sel_status sel_ctx_set_scan_shape(sel_ctx* c, int32_t tile_rows, int3
 }
 
 extern "C" sel_status sel_ctx_set_scan_variant(sel_ctx* c, int32_t consumer_warps, int32_t chunks_per_pass) {
-    if (!c || !((consumer_warps == 0 && chunks_per_pass == 0) || scan_variant_ok(consumer_warps, chunks_per_pass))) {
-        set_error("sel_ctx_set_scan_variant: bad arguments (0,0; warps 8|16 with chunks 1|2; warps 8 with chunks 4)");
+    if (!c || !((consumer_warps == 0 && chunks_per_pass == 0) || scan_variant_ok(consumer_warps, chunks_per_pass) ||
+                bucket_variant_ok(consumer_warps, chunks_per_pass))) {
+        set_error("sel_ctx_set_scan_variant: bad arguments (0,0; warps 8|16 with chunks 1|2; warps 8 with chunks 4; "
+                  "bucket kernel only: warps 11|15 with chunks 1|2)");
         return SEL_ERR_INVALID_ARG;
     }
     c->shape.warps = consumer_warps;
@@ -538,6 +545,16 @@ int& thread_tally_depth() {
     return d;
 }
 void ctx_add_launches(sel_ctx* c, uint64_t n) { c->launches += n; }
+}
+
+extern "C" sel_status sel_ctx_set_pushdown_super_rows(sel_ctx* c, int32_t rows) {
+    if (!c || rows < 0 || (rows > 0 && (rows % kChunkRows || rows > kPdpMaxChunks * kChunkRows))) {
+        set_error("sel_ctx_set_pushdown_super_rows: rows must be 0 or a multiple of 256 up to %d",
+                  kPdpMaxChunks * kChunkRows);
+        return SEL_ERR_INVALID_ARG;
+    }
+    c->pd_super_rows = (uint32_t)rows;
+    return SEL_OK;
 }
 
 extern "C" sel_status sel_ctx_debug_pushdown_fault(sel_ctx* c, int64_t skip_tile, uint64_t wait_ns) {
@@ -653,21 +670,38 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     a.row_bytes = ta.row_bytes;
     a.tma = ta.tma;
     // The persistent kernel: super-tiles (the largest multiple of the sub-tile
-    // up to 32768 rows) streamed in sub-tiles through shared-memory stages.
+    // up to a target size) streamed in sub-tiles through shared-memory stages.
+    // The target: the context's, else 384 KB of predicate columns (a CTA's
+    // look-back of a super-tile takes a few microseconds: the super-tile
+    // should stream for longer) but no more than 1/16 of a CTA's share of the
+    // table (its last super-tile is looked back and written after the scan),
+    // at least 32768 and at most 131072 rows; larger super-tiles take shared
+    // memory (their row masks) from the stages.
     // Variant: the context's scan variant, else 16 consumer warps x 2 chunks
     // per pass.  Sub-tile and stages: the requested ones, else the count
     // scan's rule: 3 stages (2 if 3 do not fit) of the largest sub-tile, in
-    // whole chunk groups, that fits in shared memory.  A tile size the
-    // persistent kernel cannot use, or predicate columns too wide for two
-    // stages, take the one-CTA-per-tile kernel (1024 rows or as requested).
+    // whole chunk groups, that fits in shared memory beside the row masks.  A
+    // tile size the persistent kernel cannot use, or predicate columns too wide
+    // for two stages, take the one-CTA-per-tile kernel (1024 rows or as
+    // requested).
     {
         const int req = ctx->shape.tile_rows;
-        const int W = ctx->shape.warps > 0 ? ctx->shape.warps : 16;
-        const int G = ctx->shape.group > 0 ? ctx->shape.group : 2;
+        const bool own = ctx->shape.warps > 0 && scan_variant_ok(ctx->shape.warps, ctx->shape.group);
+        const int W = own ? ctx->shape.warps : 16;
+        const int G = own ? ctx->shape.group : 2;
         const int unit = kChunkRows * G;
+        uint32_t target = ctx->pd_super_rows;
+        if (target == 0) {
+            const int64_t per = table->n_rows / (16 * (int64_t)std::max(1, ctx->n_sm));
+            const int64_t by_bytes = (int64_t)(384u << 10) / std::max<int64_t>(1, ta.row_bytes);
+            target = (uint32_t)std::max<int64_t>(std::min<int64_t>(std::min<int64_t>(per, by_bytes),
+                                                                    kPdpMaxChunks * kChunkRows),
+                                                  kPdpMinSuperRows);
+        }
+        target = target / kChunkRows * kChunkRows;
         int best_tr = 0, best_s = 0;
         if (pushdown_persistent_ok(W, G) && ta.row_bytes > 0) {
-            const int tr0 = req > 0 ? req : kPdpMaxChunks * kChunkRows / unit * unit;
+            const int tr0 = req > 0 ? req : (int)target / unit * unit;
             for (int S = ctx->shape.stages > 0 ? ctx->shape.stages : 3; S >= 2 && best_tr == 0; --S) {
                 for (int tr = tr0; tr >= unit; tr -= unit) {
                     if (req > 0 && tr != req) break;
@@ -677,6 +711,7 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
                     p.row_bytes = ta.row_bytes;
                     p.tile_rows = (uint32_t)tr;
                     p.stages = (uint32_t)S;
+                    p.super_rows = pushdown_super_rows((uint32_t)tr, std::max<uint32_t>(target, (uint32_t)tr));
                     if (pushdown_persistent_layout(p) <= (size_t)ctx->max_smem_pdp) {
                         best_tr = tr;
                         best_s = S;
@@ -697,6 +732,7 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
             a.n_slots = ta.n_slots;
             a.row_bytes = ta.row_bytes;
             a.tma = ta.tma;
+            a.super_rows = pushdown_super_rows(a.tile_rows, std::max<uint32_t>(target, a.tile_rows));
             pushdown_persistent_layout(a);
             uint32_t off = 0;
             for (uint32_t j = 0; j < ta.n_slots; ++j) {
@@ -706,7 +742,6 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
                 off += a.tile_rows * ta.width[j];
             }
             a.n_rows = table->n_rows;
-            a.super_rows = pushdown_super_rows(a.tile_rows);
             a.n_tiles = (table->n_rows + a.super_rows - 1) / a.super_rows;   // look-back unit: super-tiles
             a.n_proj = (uint32_t)n_proj;
             a.rowids = reinterpret_cast<long long*>(dev_out_rowids);
@@ -1193,8 +1228,8 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     float best_ms = 0.f;
     if (autotune && bucket_ok) {
         struct BCand { int stage_kb, stages, warps, group; };
-        const BCand bc[] = {{0, 3, 16, 1}, {0, 3, 16, 2}, {0, 3, 8, 2}, {0, 2, 16, 1}, {0, 4, 16, 2},
-                            {32, 4, 16, 1}, {0, 3, 8, 1}, {0, 2, 8, 1}};
+        const BCand bc[] = {{0, 3, 16, 1}, {0, 3, 15, 1}, {0, 3, 15, 2}, {0, 3, 11, 1}, {0, 3, 16, 2},
+                            {0, 2, 15, 1}, {0, 4, 15, 2}, {0, 3, 8, 2}, {0, 3, 8, 1}};
         best_ms = 1e30f;
         for (const BCand& c : bc) {
             Shape sh = bucket_default;

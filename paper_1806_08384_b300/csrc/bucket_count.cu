@@ -471,7 +471,12 @@ size_t bucket_layout(ScanArgs& a, int warps, uint32_t gb_bytes_per_warp) {
     return static_cast<size_t>(a.stage_off) + static_cast<size_t>(a.stages) * a.stage_bytes;
 }
 
-bool bucket_variant_ok(int warps, int group) { return (warps == 8 || warps == 16) && (group == 1 || group == 2); }
+// 15 and 11 consumer warps (16 and 12 warps in all: 4 and 3 per scheduler's
+// register file) get 128 and 168 registers a thread; 16 consumer warps put 5
+// warps on one scheduler and get 96.
+bool bucket_variant_ok(int warps, int group) {
+    return (warps == 8 || warps == 11 || warps == 15 || warps == 16) && (group == 1 || group == 2);
+}
 
 template <int W, int G>
 static cudaError_t bucket_smem_limit(int optin, int* dyn_max) {
@@ -489,6 +494,10 @@ cudaError_t bucket_kernel_max_smem(int optin, int* dyn_max) {
     if (e == cudaSuccess) e = bucket_smem_limit<16, 1>(optin, dyn_max);
     if (e == cudaSuccess) e = bucket_smem_limit<8, 2>(optin, dyn_max);
     if (e == cudaSuccess) e = bucket_smem_limit<16, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = bucket_smem_limit<15, 1>(optin, dyn_max);
+    if (e == cudaSuccess) e = bucket_smem_limit<15, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = bucket_smem_limit<11, 1>(optin, dyn_max);
+    if (e == cudaSuccess) e = bucket_smem_limit<11, 2>(optin, dyn_max);
     return e;
 }
 
@@ -501,6 +510,14 @@ cudaError_t launch_bucket_count(const ScanArgs& a, int grid, size_t smem, cudaSt
         bucket_count_kernel<8, 2><<<grid, 9 * 32, smem, st>>>(a);
     else if (warps == 16 && group == 2)
         bucket_count_kernel<16, 2><<<grid, 17 * 32, smem, st>>>(a);
+    else if (warps == 15 && group == 1)
+        bucket_count_kernel<15, 1><<<grid, 16 * 32, smem, st>>>(a);
+    else if (warps == 15 && group == 2)
+        bucket_count_kernel<15, 2><<<grid, 16 * 32, smem, st>>>(a);
+    else if (warps == 11 && group == 1)
+        bucket_count_kernel<11, 1><<<grid, 12 * 32, smem, st>>>(a);
+    else if (warps == 11 && group == 2)
+        bucket_count_kernel<11, 2><<<grid, 12 * 32, smem, st>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

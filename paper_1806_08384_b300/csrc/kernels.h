@@ -107,14 +107,18 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
 // evaluating groups of G chunks (1 or 2), a producer warp and a look-back warp;
 // sub-tiles of tile_rows rows stream through `stages` shared-memory stages and
 // the look-back unit (n_tiles, status words) is a super-tile of super_rows
-// rows: the largest multiple of tile_rows that is at most kPdpMaxChunks chunks
-// (32768 rows).
-constexpr int kPdpMaxChunks = 128;
+// rows: the largest multiple of tile_rows that is at most a target of 32768
+// to kPdpMaxChunks chunks (131072 rows).
+constexpr int kPdpMaxChunks = 512;
+constexpr int kPdpMinSuperRows = 32768;
 bool pushdown_persistent_ok(int warps, int chunks_per_pass);
 // tile_rows: a multiple of chunks_per_pass chunks, at most kPdpMaxChunks chunks.
 bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass);
-uint32_t pushdown_super_rows(uint32_t tile_rows);
-// Fills the shared-memory offsets for a.stages stages of a.tile_rows rows; returns the bytes needed.
+// The largest multiple of tile_rows that is at most min(target, kPdpMaxChunks
+// chunks); 0 when tile_rows is larger.
+uint32_t pushdown_super_rows(uint32_t tile_rows, uint32_t target);
+// Fills the shared-memory offsets for a.stages stages of a.tile_rows rows and
+// the row masks of super-tiles of a.super_rows rows; returns the bytes needed.
 size_t pushdown_persistent_layout(PushdownArgs& a);
 cudaError_t pushdown_persistent_max_smem(int optin, int* dyn_max);
 cudaError_t launch_pushdown_persistent(const PushdownArgs& a, int grid, int warps, int chunks_per_warp,

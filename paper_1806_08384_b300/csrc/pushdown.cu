@@ -219,14 +219,16 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 //                   counter and bulk-copies each sub-tile's predicate columns
 //                   into the next free stage (full[s]);
 //   consumer warps  evaluate chunk groups of each sub-tile (ownership rotates
-//                   from sub-tile to sub-tile), store masks and chunk counts
-//                   into the super-tile's buffer and free the stage at once
-//                   (empty[s]); after their part of super-tile j (evald[b])
+//                   from sub-tile to sub-tile), store each chunk's row masks
+//                   (a byte per lane) into the super-tile's buffer and free
+//                   the stage at once (empty[s]); after their part of super-tile j (evald[b])
 //                   they go on with j+1 (once buffer b of j+1 is free);
-//   look-back warp  sums super-tile j's chunk counts, publishes its aggregate,
-//                   finds its exclusive prefix by decoupled look-back,
-//                   publishes the inclusive prefix and the chunk prefixes
-//                   (done[b]) while the consumers already stream j+1;
+//   look-back warp  sums super-tile j's chunk counts, finds its exclusive
+//                   prefix by decoupled look-back, publishes the inclusive
+//                   prefix and the chunk prefixes (done[b]) while the
+//                   consumers already stream j+1 (the aggregate of j was
+//                   published by the last consumer warp to finish it, so
+//                   that no look-back waits behind another one);
 //   writer warps    (kPdWriters) write the selected rows of each looked-back
 //                   super-tile, reading the projected values of those rows
 //                   from global memory, and release its buffer (freeb[b]).
@@ -252,10 +254,11 @@ constexpr int kPdWriters = 4;        // writer warps
 constexpr uint32_t kPdBatches = 4;   // batches of 32 rows a writer lane has in flight
 constexpr uint32_t kMaskWords = 8;   // 256 rows of a chunk, 32 per word, in row order
 
-// Shared-memory layout (bytes from the dynamic base) for S stages.
+// Shared-memory layout (bytes from the dynamic base) for S stages and
+// super-tiles of CH chunks.
 struct PdLayout {
-    uint32_t tile, st_id, excl, nch, stot, claim, left, ngr, cp, mask, end;
-    __host__ __device__ explicit PdLayout(uint32_t S) {
+    uint32_t tile, st_id, excl, nch, stot, claim, left, ngr, evc, cp, mask, end;
+    __host__ __device__ PdLayout(uint32_t S, uint32_t CH) {
         tile = 16u * S + 3u * 8u * kPdBufs;           // after full[S], empty[S], evald/done/freeb[kPdBufs]
         st_id = tile + 8u * S;
         excl = st_id + 8u * kPdBufs;
@@ -264,9 +267,10 @@ struct PdLayout {
         claim = stot + 4u * kPdBufs;
         left = claim + 4u * kPdBufs;
         ngr = left + 4u * kPdBufs;
-        cp = ngr + 4u * kPdBufs;
-        mask = (cp + 4u * kPdBufs * kPdpMaxChunks + 15u) & ~15u;   // read as uint4
-        end = mask + 4u * kPdBufs * kPdpMaxChunks * kMaskWords;
+        evc = ngr + 4u * kPdBufs;
+        cp = evc + 4u * kPdBufs;
+        mask = (cp + 4u * kPdBufs * CH + 15u) & ~15u;   // read as uint4
+        end = mask + 4u * kPdBufs * CH * kMaskWords;
     }
 };
 
@@ -281,13 +285,16 @@ struct PdSmem {
     uint32_t* claim;                     // [kPdBufs] generation << 20 | next write group to hand out
     uint32_t* left;                      // [kPdBufs] write groups not yet finished
     uint32_t* ngr;                       // [kPdBufs] write groups of the buffer's super-tile
-    uint32_t* cp;                        // [kPdBufs][kPdpMaxChunks] chunk prefixes
-    uint32_t* mask;                      // [kPdBufs][kPdpMaxChunks][kMaskWords] row masks, row order
+    uint32_t* evc;                       // [kPdBufs] consumer warps done with the buffer, over all its uses
+    uint32_t* cp;                        // [kPdBufs][ch] chunk prefixes
+    uint32_t* mask;                      // [kPdBufs][ch][kMaskWords] row masks (lane bytes, then row order)
+    uint32_t ch;                         // chunks of a super-tile (super_rows / 256)
 };
 
-__device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S) {
-    const PdLayout L(S);
+__device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S, uint32_t CH) {
+    const PdLayout L(S, CH);
     PdSmem m;
+    m.ch = CH;
     m.full = reinterpret_cast<uint64_t*>(smem);
     m.empty = m.full + S;
     m.evald = m.empty + S;
@@ -301,6 +308,7 @@ __device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S) {
     m.claim = reinterpret_cast<uint32_t*>(smem + L.claim);
     m.left = reinterpret_cast<uint32_t*>(smem + L.left);
     m.ngr = reinterpret_cast<uint32_t*>(smem + L.ngr);
+    m.evc = reinterpret_cast<uint32_t*>(smem + L.evc);
     m.cp = reinterpret_cast<uint32_t*>(smem + L.cp);
     m.mask = reinterpret_cast<uint32_t*>(smem + L.mask);
     return m;
@@ -344,20 +352,30 @@ __device__ __forceinline__ void fail_flag(const PushdownArgs& a, uint32_t* s_fai
 
 __device__ __forceinline__ bool volatile_flag(const uint32_t* f) { return *reinterpret_cast<const volatile uint32_t*>(f) != 0; }
 
-// Stores a warp's 8-bit lane masks of one chunk (bit i < 4: row 4*lane + i,
-// bit 4 + i: row 128 + 4*lane + i) as 8 row-order words: word k holds rows
-// 32k .. 32k + 31, i.e. the nibbles of lanes 8(k % 4) .. 8(k % 4) + 7 of half
-// k / 4.
-__device__ __forceinline__ void store_row_words(uint32_t* words, uint32_t m, uint32_t lane) {
-    const uint32_t sh = 4u * (lane & 7u);
-    uint32_t lo = (m & 0xFu) << sh, hi = (m >> 4) << sh;
+// A chunk's row masks are first stored by the consumers as one byte per lane
+// (byte l: bit i < 4 is row 4*l + i, bit 4 + i is row 128 + 4*l + i: the
+// lane's 8-bit mask as the interpreter produces it) and turned into 8
+// row-order words (word k holds rows 32k .. 32k + 31) by the look-back warp
+// before the writers read them.
+// The low nibbles of the 4 bytes of x, packed into 16 bits.
+__device__ __forceinline__ uint32_t pack_nibbles(uint32_t x) {
+    x &= 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    return (x | (x >> 8)) & 0x0000FFFFu;
+}
+
+// Rewrites one chunk's 32 lane bytes (two uint4: x holds lanes 0..15, y lanes
+// 16..31) as its 8 row-order words.
+__device__ __forceinline__ void lane_bytes_to_rows(uint4* w4, const uint4& x, const uint4& y) {
+    const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};   // w[i]: lanes 4i .. 4i + 3
+    uint32_t r[8];
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-        lo |= __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-        hi |= __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+    for (int k = 0; k < 4; ++k) {
+        r[k] = pack_nibbles(w[2 * k]) | (pack_nibbles(w[2 * k + 1]) << 16);
+        r[4 + k] = pack_nibbles(w[2 * k] >> 4) | (pack_nibbles(w[2 * k + 1] >> 4) << 16);
     }
-    if ((lane & 7u) == 0u) words[lane >> 3] = lo;
-    else if ((lane & 7u) == 1u) words[4u + (lane >> 3)] = hi;
+    w4[0] = make_uint4(r[0], r[1], r[2], r[3]);
+    w4[1] = make_uint4(r[4], r[5], r[6], r[7]);
 }
 
 // Position of the (o+1)-th set bit of w (o < popc(w)).
@@ -374,8 +392,8 @@ __device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t o) {
 // Row of rank r among the selected rows of the super-tile in buffer b.
 __device__ __forceinline__ int64_t rank_row(const PdSmem& sm, uint32_t b, int64_t R0, uint32_t r) {
     const uint32_t nch = sm.nch[b];
-    const uint32_t* cp = sm.cp + b * kPdpMaxChunks;
-    const uint32_t* mw = sm.mask + b * kPdpMaxChunks * kMaskWords;
+    const uint32_t* cp = sm.cp + b * sm.ch;
+    const uint32_t* mw = sm.mask + b * sm.ch * kMaskWords;
     // the chunk: the last one whose prefix is <= r (cp[0] = 0)
     uint32_t lo = 0, hi = nch;
     while (hi - lo > 1u) {
@@ -523,7 +541,7 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
     __shared__ uint32_t s_slot_off[kMaxSlots];   // read by every leaf: keep it in shared memory
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t S = a.stages;
-    const PdSmem sm = pd_smem(smem, S);
+    const PdSmem sm = pd_smem(smem, S, SR / kChunkRows);
     if (tid < kMaxSlots) s_slot_off[tid] = a.slot_off[tid];
     uint8_t* stages = smem + a.smem_stage_off;
     const long long n_super = a.n_tiles;
@@ -537,6 +555,7 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
             mbar_init(&sm.evald[b], W);
             mbar_init(&sm.done[b], 1);
             mbar_init(&sm.freeb[b], 1);   // the warp that finishes the last write group (or the look-back)
+            sm.evc[b] = 0;
         }
         fence_mbar_init();
         s_fail = 0;
@@ -634,14 +653,15 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
             // past the super-tile's rows count 0) and the total
             const uint32_t nch = sm.nch[b];
             uint32_t carry = 0;
-            for (uint32_t c0 = 0; c0 < kPdpMaxChunks; c0 += 32) {
+            for (uint32_t c0 = 0; c0 < sm.ch; c0 += 32) {
                 const uint32_t c = c0 + lane;
                 uint32_t v = 0;
                 if (c < nch) {
-                    const uint4* w4 = reinterpret_cast<const uint4*>(sm.mask + (b * kPdpMaxChunks + c) * kMaskWords);
+                    uint4* w4 = reinterpret_cast<uint4*>(sm.mask + (b * sm.ch + c) * kMaskWords);
                     const uint4 x = w4[0], y = w4[1];
                     v = __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w) + __popc(y.x) + __popc(y.y) +
                         __popc(y.z) + __popc(y.w);
+                    if (v) lane_bytes_to_rows(w4, x, y);   // a chunk with no rows is never ranked
                 }
                 uint32_t inc = v;
 #pragma unroll
@@ -649,12 +669,10 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
                     const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
                     if (lane >= static_cast<uint32_t>(o)) inc += y;
                 }
-                sm.cp[b * kPdpMaxChunks + c] = carry + inc - v;
+                if (c < sm.ch) sm.cp[b * sm.ch + c] = carry + inc - v;
                 carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
             }
-            const uint32_t tile_cnt = carry;
-            if (lane == 0 && t != a.skip_publish_tile)
-                st_relaxed(&a.status[t], (t == 0 ? kFlagInc : kFlagAgg) | tile_cnt);
+            const uint32_t tile_cnt = carry;   // its aggregate is already published by the last consumer warp
             unsigned long long excl = 0;
             bool ok = true;
             if (t > 0) {
@@ -748,7 +766,8 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
                                                                          : valid_mask(c0[q], lane, valid);
                         m[q] &= vm;
                         const uint32_t g = u * NCH + grp * G + q;   // chunk index in the super-tile (row order)
-                        store_row_words(sm.mask + (b * kPdpMaxChunks + g) * kMaskWords, m[q], lane);
+                        reinterpret_cast<uint8_t*>(sm.mask + (b * sm.ch + g) * kMaskWords)[lane] =
+                            static_cast<uint8_t>(m[q]);
                     }
                 }
                 rot += n_groups;
@@ -765,7 +784,28 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
                 sm.nch[b] = t >= 0 ? n_sub * NCH : 0u;
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&sm.evald[b]);   // release: masks, counts, id visible
+            // The last consumer warp done with super-tile j publishes its
+            // aggregate right away: successors' look-backs then wait only for
+            // the evaluation of their predecessors, never for this CTA's
+            // look-back warp (busy with an earlier super-tile).
+            uint32_t last = 0;
+            if (lane == 0) last = atom_add_acq_rel_cta(&sm.evc[b], 1u) + 1u == W * (j / kPdBufs + 1u);
+            last = __shfl_sync(0xFFFFFFFFu, last, 0);
+            __syncwarp();   // lane 0's acquire orders the other warps' mask stores before the reads below
+            if (last && t >= 0) {
+                const uint32_t nch = n_sub * NCH;
+                uint32_t v = 0;
+                for (uint32_t c = lane; c < nch; c += 32) {
+                    const uint4* w4 = reinterpret_cast<const uint4*>(sm.mask + (b * sm.ch + c) * kMaskWords);
+                    const uint4 x = w4[0], y = w4[1];
+                    v += __popc(x.x) + __popc(x.y) + __popc(x.z) + __popc(x.w) + __popc(y.x) + __popc(y.y) +
+                         __popc(y.z) + __popc(y.w);
+                }
+                v = __reduce_add_sync(0xFFFFFFFFu, v);
+                if (lane == 0 && t != a.skip_publish_tile)
+                    st_relaxed(&a.status[t], (t == 0 ? kFlagInc : kFlagAgg) | v);
+            }
+            if (lane == 0) mbar_arrive(&sm.evald[b]);   // release: masks, counts, id (and the aggregate) visible
             if (t < 0 || volatile_flag(&s_fail)) break;
         }
     } else {
@@ -801,13 +841,14 @@ bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass) {
     return tile_rows > 0 && tile_rows % unit == 0 && tile_rows <= static_cast<uint32_t>(kPdpMaxChunks * kChunkRows);
 }
 
-uint32_t pushdown_super_rows(uint32_t tile_rows) {
-    const uint32_t cap = kPdpMaxChunks * kChunkRows;
-    return tile_rows == 0 ? 0u : cap / tile_rows * tile_rows;
+uint32_t pushdown_super_rows(uint32_t tile_rows, uint32_t target) {
+    const uint32_t cap = target < (uint32_t)(kPdpMaxChunks * kChunkRows) ? target : kPdpMaxChunks * kChunkRows;
+    if (tile_rows == 0 || tile_rows > cap) return 0u;
+    return cap / tile_rows * tile_rows;
 }
 
 size_t pushdown_persistent_layout(PushdownArgs& a) {
-    const PdLayout L(a.stages);
+    const PdLayout L(a.stages, a.super_rows / kChunkRows);
     a.smem_prog_off = align_up_u32(L.end, 16u);
     a.smem_stage_off = align_up_u32(a.smem_prog_off + align_up_u32(a.blob_bytes, 16u), 128u);
     a.stage_bytes = align_up_u32(a.tile_rows * a.row_bytes, 128u);   // one sub-tile of the predicate columns

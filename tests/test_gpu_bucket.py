@@ -66,7 +66,8 @@ def medium():
 
 
 @pytest.mark.parametrize("shape", [(256, 2, 8, 1), (768, 3, 8, 2), (2048, 4, 16, 1), (0, 0, 0, 0), (0, 2, 16, 2),
-                                   (16384, 3, 8, 1), (1280, 3, 16, 2), (256, 3, 8, 2)])
+                                   (16384, 3, 8, 1), (1280, 3, 16, 2), (256, 3, 8, 2), (0, 3, 15, 1), (2816, 3, 11, 2),
+                                   (0, 4, 15, 2), (768, 2, 11, 1)])
 def test_config2_shapes(medium, shape):
     """Ragged last tile (n = 300,001), tiles with fewer chunks than warps, every
     ring depth, one or two chunks per pass (an odd chunk count leaves the last
@@ -82,7 +83,7 @@ def test_config2_shapes(medium, shape):
     assert _run(ctx, preds, [T] * len(preds)) == [oracle.count(ot, tr, threads=THREADS) for tr in trees]
 
 
-@pytest.mark.parametrize("variant", [(8, 1), (16, 1), (8, 2), (16, 2)])
+@pytest.mark.parametrize("variant", [(8, 1), (16, 1), (8, 2), (16, 2), (15, 1), (11, 2)])
 def test_several_blocks_on_one_table(dev, variant):
     """256 probes (4 blocks of 64) and 300 random estimator-workload probes (5 blocks)."""
     t = dg.config5_table(n=1_000_003, device=dev)

@@ -97,9 +97,26 @@ def test_variants_tiny(ctx, dev, variant):
 
 
 def test_bad_variant_is_rejected(ctx):
-    for w, g in [(4, 1), (8, 3), (0, 1), (32, 2), (16, 4)]:
+    for w, g in [(4, 1), (8, 3), (0, 1), (32, 2), (16, 4), (15, 4), (11, 3), (12, 1)]:
         with pytest.raises(sel.SelError):
             ctx.set_scan_variant(w, g)
+
+
+def test_bucket_only_variant_keeps_the_count_default(ctx, medium):
+    """11 and 15 consumer warps exist for the batch plans' bucket kernel only:
+    sel_count and sel_pushdown keep their own defaults under them."""
+    t, ot, T = medium
+    tree = dg.config2_predicate(1e-2, seed=5)
+    want = oracle.count(ot, tree)
+    try:
+        for w, g in [(15, 1), (11, 2)]:
+            ctx.set_scan_variant(w, g)
+            P = sel.Predicate(T, tree)
+            assert ctx.count(P, T) == want
+            status, n, _, _ = ctx.pushdown(P, T, [0], max_rows=T.n_rows)
+            assert status == sel.SEL_OK and n == want
+    finally:
+        ctx.set_scan_variant(0, 0)
 
 
 def test_unaligned_columns_take_the_plain_path(ctx, medium):

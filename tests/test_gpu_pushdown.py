@@ -87,6 +87,33 @@ def test_persistent_variants(ctx, dev, medium, variant):
             check_pushdown(ctx, TT, ott, dg.random_tree(tt, rng, depth=4), [0, 1, 2, 3, 4])
 
 
+@pytest.mark.parametrize("super_rows", [65536, 131072, 99_840, 256])
+def test_super_tile_sizes(ctx, dev, medium, super_rows):
+    """Super-tiles above the default 32768 rows (the masks and chunk prefixes
+    of up to 512 chunks per buffer), one that is no multiple of the sub-tile
+    and one smaller than the sub-tile (one sub-tile per super-tile), on the
+    1,000,003-row table and on a table of 3 super-tiles and a ragged part."""
+    t, ot, T = medium
+    ctx.set_pushdown_super_rows(super_rows)
+    try:
+        for s in (1e-3, 0.1, 0.5):
+            check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=23), proj_cfg2(t))
+        tt = dg.tiny_table(3 * 131072 + 777, seed=9)
+        ott = oracle.OTable.from_table(tt)
+        TT = sel.Table(tt.to(dev).columns)
+        rng = np.random.default_rng(super_rows)
+        for _ in range(4):
+            check_pushdown(ctx, TT, ott, dg.random_tree(tt, rng, depth=4), [0, 1, 2, 3, 4])
+    finally:
+        ctx.set_pushdown_super_rows(0)
+
+
+def test_bad_super_rows_are_rejected(ctx):
+    for r in (-256, 100, 131072 + 256, 1 << 20):
+        with pytest.raises(sel.SelError):
+            ctx.set_pushdown_super_rows(r)
+
+
 def test_projection_of_non_predicate_columns_and_no_rowids(ctx, medium):
     t, ot, T = medium
     tree = dg.p_between(t.index("f0"), 100.0, 2000.0)
@@ -145,7 +172,7 @@ def test_unaligned_columns(ctx, medium):
         check_pushdown(ctx, T, sub, dg.config2_predicate(s, seed=13), proj_cfg2(t))
 
 
-@pytest.mark.parametrize("tile_rows", [1024, 2048, 3584, 4096, 1280])
+@pytest.mark.parametrize("tile_rows", [1024, 2048, 3584, 4096, 1280, -65536])
 def test_lookback_wait_times_out_and_context_recovers(ctx, dev, tile_rows):
     """A tile that never publishes makes its successors' bounded waits run out:
     the call returns SEL_ERR_TIMEOUT, and the context works afterwards (the
@@ -157,14 +184,18 @@ def test_lookback_wait_times_out_and_context_recovers(ctx, dev, tile_rows):
     T = sel.Table(t.to(dev).columns)
     tree = dg.p_cmp(0, "<", 2)
     p = sel.Predicate(T, tree)
-    ctx.set_scan_shape(tile_rows, 0, 0)
-    ctx.debug_pushdown_fault(2, 50_000_000)          # tile 2 never publishes; waits give up after 50 ms
+    if tile_rows < 0:                                # 65536-row super-tiles of the default sub-tile
+        ctx.set_pushdown_super_rows(-tile_rows)
+    else:
+        ctx.set_scan_shape(tile_rows, 0, 0)
+    ctx.debug_pushdown_fault(1 if tile_rows < 0 else 2, 50_000_000)   # never publishes; waits give up after 50 ms
     with pytest.raises(sel.SelError) as e:
         ctx.pushdown(p, T, [0], T.n_rows)
     assert e.value.status == sel.SEL_ERR_TIMEOUT
     ctx.debug_pushdown_fault(-1, 0)
     check_pushdown(ctx, T, ot, tree, [0, 1, 2])
     assert ctx.count(p, T) == oracle.count(ot, tree)
+    ctx.set_pushdown_super_rows(0)
 
 
 @pytest.mark.slow
