@@ -275,11 +275,12 @@ sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stage
  * over the program's instructions), or 8 warps with 4 chunks per pass.  Any
  * other pair: SEL_ERR_INVALID_ARG.
  * The same pair selects the persistent push-down kernel's consumer warps and
- * chunks per pass where that kernel has the variant (8 or 16 warps, 1 or 2
- * chunks; otherwise the push-down takes its one-CTA-per-tile kernel).
+ * chunks per pass where that kernel has the variant (8, 12 or 16 warps, 1 or
+ * 2 chunks; default 12 x 2; with 8 x 4 the push-down keeps its default).
  * The batch plans' column-bucket kernel also takes 11 or 15 consumer warps
- * (1 or 2 chunks per pass); with those pairs sel_count and sel_pushdown keep
- * their defaults.  Results do not depend on the variant. */
+ * (1 or 2 chunks per pass), and the push-down 12 warps; with pairs a kernel
+ * does not have, sel_count, sel_pushdown and the batch plans keep their
+ * defaults.  Results do not depend on the variant. */
 sel_status sel_ctx_set_scan_variant(sel_ctx* ctx, int32_t consumer_warps, int32_t chunks_per_pass);
 
 /* Number of kernels this context has launched so far (all entry points). */

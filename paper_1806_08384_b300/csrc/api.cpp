@@ -513,9 +513,10 @@ extern "C" sel_status sel_ctx_set_scan_shape(sel_ctx* c, int32_t tile_rows, int3
 
 extern "C" sel_status sel_ctx_set_scan_variant(sel_ctx* c, int32_t consumer_warps, int32_t chunks_per_pass) {
     if (!c || !((consumer_warps == 0 && chunks_per_pass == 0) || scan_variant_ok(consumer_warps, chunks_per_pass) ||
-                bucket_variant_ok(consumer_warps, chunks_per_pass))) {
+                bucket_variant_ok(consumer_warps, chunks_per_pass) ||
+                pushdown_persistent_ok(consumer_warps, chunks_per_pass))) {
         set_error("sel_ctx_set_scan_variant: bad arguments (0,0; warps 8|16 with chunks 1|2; warps 8 with chunks 4; "
-                  "bucket kernel only: warps 11|15 with chunks 1|2)");
+                  "bucket kernel only: warps 11|15 with chunks 1|2; push-down only: warps 12 with chunks 1|2)");
         return SEL_ERR_INVALID_ARG;
     }
     c->shape.warps = consumer_warps;
@@ -677,8 +678,10 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     // table (its last super-tile is looked back and written after the scan),
     // at least 32768 and at most 131072 rows; larger super-tiles take shared
     // memory (their row masks) from the stages.
-    // Variant: the context's scan variant, else 16 consumer warps x 2 chunks
-    // per pass.  Sub-tile and stages: the requested ones, else the count
+    // Variant: the context's scan variant, else 12 consumer warps x 2 chunks
+    // per pass (with the producer, look-back and 2 writer warps, 16 warps of
+    // 128 registers: no spills in the evaluation loop; measured faster on
+    // config 5's push-downs than 16 consumer warps of 96 registers).  Sub-tile and stages: the requested ones, else the count
     // scan's rule: 3 stages (2 if 3 do not fit) of the largest sub-tile, in
     // whole chunk groups, that fits in shared memory beside the row masks.  A
     // tile size the persistent kernel cannot use, or predicate columns too wide
@@ -686,8 +689,8 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     // requested).
     {
         const int req = ctx->shape.tile_rows;
-        const bool own = ctx->shape.warps > 0 && scan_variant_ok(ctx->shape.warps, ctx->shape.group);
-        const int W = own ? ctx->shape.warps : 16;
+        const bool own = ctx->shape.warps > 0 && pushdown_persistent_ok(ctx->shape.warps, ctx->shape.group);
+        const int W = own ? ctx->shape.warps : 12;
         const int G = own ? ctx->shape.group : 2;
         const int unit = kChunkRows * G;
         uint32_t target = ctx->pd_super_rows;

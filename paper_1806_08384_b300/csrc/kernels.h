@@ -103,7 +103,7 @@ struct PushdownArgs {
 size_t pushdown_layout(PushdownArgs& a);
 cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
 
-// Persistent push-down: one CTA per SM with W consumer warps (8 or 16)
+// Persistent push-down: one CTA per SM with W consumer warps (8, 12 or 16)
 // evaluating groups of G chunks (1 or 2), a producer warp and a look-back warp;
 // sub-tiles of tile_rows rows stream through `stages` shared-memory stages and
 // the look-back unit (n_tiles, status words) is a super-tile of super_rows

@@ -250,29 +250,38 @@ cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st) {
 namespace {
 
 constexpr uint32_t kPdBufs = 4;      // super-tile buffers: evaluating j+1, look-back of j, writing j-1 and j-2
-constexpr int kPdWriters = 4;        // writer warps
+constexpr int kPdWriters = 2;        // writer warps: with 12 consumers, 16 warps a CTA and 128 registers a thread
 constexpr uint32_t kPdBatches = 4;   // batches of 32 rows a writer lane has in flight
 constexpr uint32_t kMaskWords = 8;   // 256 rows of a chunk, 32 per word, in row order
 
-// Shared-memory layout (bytes from the dynamic base) for S stages and
-// super-tiles of CH chunks.
-struct PdLayout {
-    uint32_t tile, st_id, excl, nch, stot, claim, left, ngr, evc, cp, mask, end;
-    __host__ __device__ PdLayout(uint32_t S, uint32_t CH) {
-        tile = 16u * S + 3u * 8u * kPdBufs;           // after full[S], empty[S], evald/done/freeb[kPdBufs]
-        st_id = tile + 8u * S;
-        excl = st_id + 8u * kPdBufs;
-        nch = excl + 8u * kPdBufs;
-        stot = nch + 4u * kPdBufs;
-        claim = stot + 4u * kPdBufs;
-        left = claim + 4u * kPdBufs;
-        ngr = left + 4u * kPdBufs;
-        evc = ngr + 4u * kPdBufs;
-        cp = evc + 4u * kPdBufs;
-        mask = (cp + 4u * kPdBufs * CH + 15u) & ~15u;   // read as uint4
-        end = mask + 4u * kPdBufs * CH * kMaskWords;
-    }
-};
+// Shared-memory layout (bytes from the dynamic base): a control block at
+// fixed offsets (room for kPdMaxStages stages), so that every access to it is
+// the shared base plus a constant, then the chunk prefixes and row masks of
+// kPdBufs super-tiles of CH chunks.
+constexpr uint32_t kPdMaxStages = 16;
+namespace pdo {
+constexpr uint32_t full = 0;
+constexpr uint32_t empty = full + 8u * kPdMaxStages;
+constexpr uint32_t evald = empty + 8u * kPdMaxStages;
+constexpr uint32_t done = evald + 8u * kPdBufs;
+constexpr uint32_t freeb = done + 8u * kPdBufs;
+constexpr uint32_t tile = freeb + 8u * kPdBufs;
+constexpr uint32_t st_id = tile + 8u * kPdMaxStages;
+constexpr uint32_t excl = st_id + 8u * kPdBufs;
+constexpr uint32_t nch = excl + 8u * kPdBufs;
+constexpr uint32_t stot = nch + 4u * kPdBufs;
+constexpr uint32_t claim = stot + 4u * kPdBufs;
+constexpr uint32_t left = claim + 4u * kPdBufs;
+constexpr uint32_t ngr = left + 4u * kPdBufs;
+constexpr uint32_t evc = ngr + 4u * kPdBufs;
+constexpr uint32_t cp = (evc + 4u * kPdBufs + 15u) & ~15u;
+}  // namespace pdo
+__host__ __device__ __forceinline__ uint32_t pd_mask_off(uint32_t CH) {
+    return (pdo::cp + 4u * kPdBufs * CH + 15u) & ~15u;   // read as uint4
+}
+__host__ __device__ __forceinline__ uint32_t pd_ctrl_end(uint32_t CH) {
+    return pd_mask_off(CH) + 4u * kPdBufs * CH * kMaskWords;
+}
 
 struct PdSmem {
     uint64_t *full, *empty;              // [S]
@@ -291,26 +300,25 @@ struct PdSmem {
     uint32_t ch;                         // chunks of a super-tile (super_rows / 256)
 };
 
-__device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t S, uint32_t CH) {
-    const PdLayout L(S, CH);
+__device__ __forceinline__ PdSmem pd_smem(uint8_t* smem, uint32_t CH) {
     PdSmem m;
     m.ch = CH;
-    m.full = reinterpret_cast<uint64_t*>(smem);
-    m.empty = m.full + S;
-    m.evald = m.empty + S;
-    m.done = m.evald + kPdBufs;
-    m.freeb = m.done + kPdBufs;
-    m.tile = reinterpret_cast<long long*>(smem + L.tile);
-    m.st_id = reinterpret_cast<long long*>(smem + L.st_id);
-    m.excl = reinterpret_cast<unsigned long long*>(smem + L.excl);
-    m.nch = reinterpret_cast<uint32_t*>(smem + L.nch);
-    m.stot = reinterpret_cast<uint32_t*>(smem + L.stot);
-    m.claim = reinterpret_cast<uint32_t*>(smem + L.claim);
-    m.left = reinterpret_cast<uint32_t*>(smem + L.left);
-    m.ngr = reinterpret_cast<uint32_t*>(smem + L.ngr);
-    m.evc = reinterpret_cast<uint32_t*>(smem + L.evc);
-    m.cp = reinterpret_cast<uint32_t*>(smem + L.cp);
-    m.mask = reinterpret_cast<uint32_t*>(smem + L.mask);
+    m.full = reinterpret_cast<uint64_t*>(smem + pdo::full);
+    m.empty = reinterpret_cast<uint64_t*>(smem + pdo::empty);
+    m.evald = reinterpret_cast<uint64_t*>(smem + pdo::evald);
+    m.done = reinterpret_cast<uint64_t*>(smem + pdo::done);
+    m.freeb = reinterpret_cast<uint64_t*>(smem + pdo::freeb);
+    m.tile = reinterpret_cast<long long*>(smem + pdo::tile);
+    m.st_id = reinterpret_cast<long long*>(smem + pdo::st_id);
+    m.excl = reinterpret_cast<unsigned long long*>(smem + pdo::excl);
+    m.nch = reinterpret_cast<uint32_t*>(smem + pdo::nch);
+    m.stot = reinterpret_cast<uint32_t*>(smem + pdo::stot);
+    m.claim = reinterpret_cast<uint32_t*>(smem + pdo::claim);
+    m.left = reinterpret_cast<uint32_t*>(smem + pdo::left);
+    m.ngr = reinterpret_cast<uint32_t*>(smem + pdo::ngr);
+    m.evc = reinterpret_cast<uint32_t*>(smem + pdo::evc);
+    m.cp = reinterpret_cast<uint32_t*>(smem + pdo::cp);
+    m.mask = reinterpret_cast<uint32_t*>(smem + pd_mask_off(CH));
     return m;
 }
 
@@ -327,14 +335,18 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, uint32
 
 // The same, but it also gives up (false) as soon as another warp of the CTA
 // has flagged a failure: a wait on a role that stopped would otherwise last
-// its full bound.
+// its full bound.  The sleep between tries doubles from sleep_ns up to
+// max_sleep_ns: an idle writer would otherwise take issue slots from the
+// consumers all through a scan that selects few rows.
 __device__ __forceinline__ bool warp_wait_live(uint64_t* bar, uint32_t parity, const uint32_t* s_fail,
-                                               uint32_t sleep_ns) {
+                                               uint32_t sleep_ns, uint32_t max_sleep_ns) {
     bool ok = mbar_try_wait(bar, parity);
     if (!ok) {
         const unsigned long long t0 = global_ns();
+        uint32_t ns = sleep_ns;
         while (true) {
-            if (sleep_ns) __nanosleep(sleep_ns);
+            __nanosleep(ns);
+            ns = ns * 2u < max_sleep_ns ? ns * 2u : max_sleep_ns;
             if (mbar_try_wait(bar, parity)) {
                 ok = true;
                 break;
@@ -541,7 +553,7 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
     __shared__ uint32_t s_slot_off[kMaxSlots];   // read by every leaf: keep it in shared memory
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     const uint32_t S = a.stages;
-    const PdSmem sm = pd_smem(smem, S, SR / kChunkRows);
+    const PdSmem sm = pd_smem(smem, SR / kChunkRows);
     if (tid < kMaxSlots) s_slot_off[tid] = a.slot_off[tid];
     uint8_t* stages = smem + a.smem_stage_off;
     const long long n_super = a.n_tiles;
@@ -813,7 +825,7 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
         for (uint32_t j = 0;; ++j) {
             const uint32_t b = j % kPdBufs;
             // idle writers sleep between tries: they would take issue slots from the consumers
-            if (!warp_wait_live(&sm.done[b], (j / kPdBufs) & 1u, &s_fail, 100)) {
+            if (!warp_wait_live(&sm.done[b], (j / kPdBufs) & 1u, &s_fail, 100, 2000)) {
                 if (lane == 0) fail_flag(a, &s_fail);
                 break;
             }
@@ -833,7 +845,7 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
 static inline uint32_t align_up_u32(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 bool pushdown_persistent_ok(int warps, int chunks_per_pass) {
-    return (warps == 8 || warps == 16) && (chunks_per_pass == 1 || chunks_per_pass == 2);
+    return (warps == 8 || warps == 12 || warps == 16) && (chunks_per_pass == 1 || chunks_per_pass == 2);
 }
 
 bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass) {
@@ -848,8 +860,7 @@ uint32_t pushdown_super_rows(uint32_t tile_rows, uint32_t target) {
 }
 
 size_t pushdown_persistent_layout(PushdownArgs& a) {
-    const PdLayout L(a.stages, a.super_rows / kChunkRows);
-    a.smem_prog_off = align_up_u32(L.end, 16u);
+    a.smem_prog_off = align_up_u32(pd_ctrl_end(a.super_rows / kChunkRows), 16u);
     a.smem_stage_off = align_up_u32(a.smem_prog_off + align_up_u32(a.blob_bytes, 16u), 128u);
     a.stage_bytes = align_up_u32(a.tile_rows * a.row_bytes, 128u);   // one sub-tile of the predicate columns
     a.smem_bytes = a.smem_stage_off + a.stages * a.stage_bytes;
@@ -870,6 +881,8 @@ cudaError_t pushdown_persistent_max_smem(int optin, int* dyn_max) {
     *dyn_max = -1;
     cudaError_t e = pdp_set_smem<8, 1>(optin, dyn_max);
     if (e == cudaSuccess) e = pdp_set_smem<8, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = pdp_set_smem<12, 1>(optin, dyn_max);
+    if (e == cudaSuccess) e = pdp_set_smem<12, 2>(optin, dyn_max);
     if (e == cudaSuccess) e = pdp_set_smem<16, 1>(optin, dyn_max);
     if (e == cudaSuccess) e = pdp_set_smem<16, 2>(optin, dyn_max);
     return e;
@@ -879,12 +892,16 @@ cudaError_t launch_pushdown_persistent(const PushdownArgs& a, int grid, int warp
                                        cudaStream_t st) {
     if (a.n_tiles <= 0) return cudaSuccess;
     if (a.super_rows == 0 || a.super_rows % a.tile_rows != 0 ||
-        a.super_rows > static_cast<uint32_t>(kPdpMaxChunks * kChunkRows))
+        a.super_rows > static_cast<uint32_t>(kPdpMaxChunks * kChunkRows) || a.stages < 1 || a.stages > kPdMaxStages)
         return cudaErrorInvalidValue;
     if (warps == 8 && chunks_per_warp == 1)
         pushdown_persistent_kernel<8, 1><<<grid, (8 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 8 && chunks_per_warp == 2)
         pushdown_persistent_kernel<8, 2><<<grid, (8 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
+    else if (warps == 12 && chunks_per_warp == 1)
+        pushdown_persistent_kernel<12, 1><<<grid, (12 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
+    else if (warps == 12 && chunks_per_warp == 2)
+        pushdown_persistent_kernel<12, 2><<<grid, (12 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 16 && chunks_per_warp == 1)
         pushdown_persistent_kernel<16, 1><<<grid, (16 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 16 && chunks_per_warp == 2)

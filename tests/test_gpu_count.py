@@ -97,19 +97,19 @@ def test_variants_tiny(ctx, dev, variant):
 
 
 def test_bad_variant_is_rejected(ctx):
-    for w, g in [(4, 1), (8, 3), (0, 1), (32, 2), (16, 4), (15, 4), (11, 3), (12, 1)]:
+    for w, g in [(4, 1), (8, 3), (0, 1), (32, 2), (16, 4), (15, 4), (11, 3), (12, 4), (13, 1)]:
         with pytest.raises(sel.SelError):
             ctx.set_scan_variant(w, g)
 
 
 def test_bucket_only_variant_keeps_the_count_default(ctx, medium):
-    """11 and 15 consumer warps exist for the batch plans' bucket kernel only:
-    sel_count and sel_pushdown keep their own defaults under them."""
+    """11 and 15 consumer warps exist for the batch plans' bucket kernel only,
+    12 for the push-down only: the other kernels keep their own defaults."""
     t, ot, T = medium
     tree = dg.config2_predicate(1e-2, seed=5)
     want = oracle.count(ot, tree)
     try:
-        for w, g in [(15, 1), (11, 2)]:
+        for w, g in [(15, 1), (11, 2), (12, 2)]:
             ctx.set_scan_variant(w, g)
             P = sel.Predicate(T, tree)
             assert ctx.count(P, T) == want

@@ -65,7 +65,7 @@ def test_config2_selectivities(ctx, medium, tile_rows):
         check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=11), proj_cfg2(t))
 
 
-@pytest.mark.parametrize("variant", [(16, 2), (16, 1), (8, 2), (8, 1)])
+@pytest.mark.parametrize("variant", [(12, 2), (12, 1), (16, 2), (16, 1), (8, 2), (8, 1)])
 def test_persistent_variants(ctx, dev, medium, variant):
     """Every persistent push-down variant (consumer warps x chunks per warp), on
     the 1,000,003-row table (ragged last super-tile and sub-tile) and on sizes at
