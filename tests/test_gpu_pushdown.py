@@ -108,6 +108,36 @@ def test_super_tile_sizes(ctx, dev, medium, super_rows):
         ctx.set_pushdown_super_rows(0)
 
 
+@pytest.mark.parametrize("super_rows", [0, 65536])
+def test_four_byte_projections(ctx, dev, medium, super_rows):
+    """Projections of 4-byte columns only: 6 such columns (two rounds of 4
+    loads a write batch), 1 column, and no column with row ids only, at
+    selectivities from 1e-4 to 0.5."""
+    t, ot, T = medium
+    narrow = [t.index(c) for c in ("k0", "k1", "f0", "f1", "d", "s0")]
+    ctx.set_pushdown_super_rows(super_rows)
+    try:
+        for s in (1e-4, 1e-2, 0.1, 0.5):
+            tree = dg.config2_predicate(s, seed=31)
+            check_pushdown(ctx, T, ot, tree, narrow)
+            check_pushdown(ctx, T, ot, tree, [t.index("f1")], rowids=False)
+        check_pushdown(ctx, T, ot, dg.config2_predicate(0.1, seed=32), [], rowids=True)
+        # a limit inside a write group: the first max_rows rows are written,
+        # nothing after them
+        tree = dg.config2_predicate(1e-2, seed=33)
+        want = oracle.select(ot, tree, threads=THREADS)
+        m = len(want) - 77
+        outs = [torch.full((m + 64,), 7, dtype=t.columns[j].data.dtype, device="cuda") for j in narrow]
+        ids = torch.full((m + 64,), -5, dtype=torch.int64, device="cuda")
+        st, cnt, _, _ = ctx.pushdown(sel.Predicate(T, tree), T, narrow, m, out_cols=outs, out_rowids=ids)
+        assert st == sel.SEL_ERR_TOO_LARGE and cnt == len(want)
+        assert np.array_equal(ids[:m].cpu().numpy(), want[:m]) and bool((ids[m:] == -5).all())
+        for j, o in zip(narrow, outs):
+            assert np.array_equal(o[:m].cpu().numpy(), ot.arrays[j][want[:m]]) and bool((o[m:] == 7).all())
+    finally:
+        ctx.set_pushdown_super_rows(0)
+
+
 def test_bad_super_rows_are_rejected(ctx):
     for r in (-256, 100, 131072 + 256, 1 << 20):
         with pytest.raises(sel.SelError):
