@@ -489,10 +489,11 @@ sel_status sel_debug_fail_allocation(int64_t nth);
  * exact counts of preds[0..n) over `table`, whose column pointers are HOST
  * memory here, evaluated on the CPU from the same bucket tables the GPU
  * kernel reads (counts: host, n entries; n_blocks, may be NULL: blocks of 64
- * probes the form used).  SEL_ERR_UNSUPPORTED (message in sel_last_error)
- * when the probes do not fit the form. */
+ * probes the form used; n_quads, may be NULL: quads of 4 blocks when the
+ * table took the quad form, else 0).  SEL_ERR_UNSUPPORTED (message in
+ * sel_last_error) when the probes do not fit the form. */
 sel_status sel_debug_bucket_count_host(const sel_pred* const* preds, int32_t n, const sel_table* table,
-                                       uint64_t* counts, int32_t* n_blocks);
+                                       uint64_t* counts, int32_t* n_blocks, int32_t* n_quads);
 
 #ifdef __cplusplus
 }

@@ -109,7 +109,8 @@ def _load():
         "sel_batch_plan_kernel": (C.c_int, [V, P(C.c_int32)]),
         "sel_debug_fail_allocation": (C.c_int, [C.c_int64]),
         "sel_ctx_set_batch_kernel": (C.c_int, [V, C.c_int32]),
-        "sel_debug_bucket_count_host": (C.c_int, [P(V), C.c_int32, P(sel_table), P(C.c_uint64), P(C.c_int32)]),
+        "sel_debug_bucket_count_host": (C.c_int, [P(V), C.c_int32, P(sel_table), P(C.c_uint64), P(C.c_int32),
+                                                  P(C.c_int32)]),
         "sel_ctx_set_scan_shape": (C.c_int, [V, C.c_int32, C.c_int32, C.c_int32]),
         "sel_ctx_set_scan_variant": (C.c_int, [V, C.c_int32, C.c_int32]),
         "sel_ctx_launch_count": (C.c_uint64, [V]),
@@ -702,15 +703,19 @@ def debug_fail_allocation(nth: int):
     _check(lib.sel_debug_fail_allocation(int(nth)), "sel_debug_fail_allocation")
 
 
-def debug_bucket_count_host(preds: Sequence[Predicate], table):
+def debug_bucket_count_host(preds: Sequence[Predicate], table, with_quads: bool = False):
     """sel_debug_bucket_count_host: (counts, blocks) of the column-bucket form
-    evaluated on the CPU; ``table`` holds CPU tensors."""
+    evaluated on the CPU, plus the number of quads when ``with_quads`` (0: the
+    block form); ``table`` holds CPU tensors."""
     table = Table.of(table)
     n = len(preds)
     pa = (C.c_void_p * n)(*[p.h.value for p in preds])
     out = (C.c_uint64 * n)()
-    nb = C.c_int32()
-    _check(lib.sel_debug_bucket_count_host(pa, n, table.ref(), out, C.byref(nb)), "sel_debug_bucket_count_host")
+    nb, nq = C.c_int32(), C.c_int32()
+    _check(lib.sel_debug_bucket_count_host(pa, n, table.ref(), out, C.byref(nb), C.byref(nq)),
+           "sel_debug_bucket_count_host")
+    if with_quads:
+        return [int(x) for x in out], int(nb.value), int(nq.value)
     return [int(x) for x in out], int(nb.value)
 
 

@@ -138,7 +138,7 @@ struct sel_batch_plan {
     // the column-bucket form of the same probes (bucket.h), when they fit it
     int kernel = 0;                    // the kernel the plan runs: 0 interpreter, 1 bucket
     void* d_bk_blob = nullptr;
-    uint32_t bk_blob_bytes = 0, bk_gb_bytes = 0, bk_n_out = 0;
+    uint32_t bk_blob_bytes = 0, bk_gb_slots = 0, bk_gb_quad = 0, bk_n_out = 0;
     // graphs that write the counts to a caller's device buffer, by buffer
     std::vector<std::pair<void*, cudaGraphExec_t>> out_graphs;
     ~sel_batch_plan() {
@@ -350,7 +350,8 @@ static sel_status resolve_bucket(sel_ctx* ctx, const sel_batch_plan* p, const st
         max_rb = std::max(max_rb, t.row_bytes);
         rows += t.n_rows;
     }
-    const uint32_t gb_bytes = p->bk_gb_bytes * (uint32_t)sh.group;   // bucket indices of a warp's chunk group
+    // bucket indices of a warp's chunk group (the kernel computes the same stride)
+    const uint32_t gb_bytes = bk_gb_bytes_per_warp(p->bk_gb_slots, p->bk_gb_quad, (uint32_t)sh.group);
     const size_t fixed = bucket_layout(a, sh.warps, gb_bytes);
     if (fixed + 128 * (size_t)sh.stages > (size_t)ctx->max_smem_bucket) {
         set_error("bucket scan: %zu bytes of tables and counters leave no room for %d stages", fixed, sh.stages);
@@ -386,6 +387,13 @@ static sel_status resolve_bucket(sel_ctx* ctx, const sel_batch_plan* p, const st
         a.t[i] = ta;
     }
     a.total_tiles = tiles;
+    {   // the kernel's per-CTA counts are 32-bit: a CTA (one of at least n_sm) must scan fewer than 2^32 rows
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)ctx->n_sm * sh.ctas_per_sm));
+        if ((tiles + grid - 1) / grid * (int64_t)sh.tile_rows >= (int64_t(1) << 32)) {
+            set_error("bucket scan: more than 2^32 rows a CTA");
+            return SEL_ERR_UNSUPPORTED;
+        }
+    }
     a.stage_bytes = ((uint32_t)sh.tile_rows * max_rb + 127u) / 128u * 128u;
     *smem = bucket_layout(a, sh.warps, gb_bytes);
     if (*smem > (size_t)ctx->max_smem_bucket) {
@@ -1178,7 +1186,8 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
             std::memcpy(&hdr, bp.blob.data(), sizeof(hdr));
             p->bk_blob_bytes = (uint32_t)bp.blob.size();
             p->bk_n_out = bp.n_out;
-            p->bk_gb_bytes = hdr.gb_slots * 8u * 32u * 2u;
+            p->bk_gb_slots = hdr.gb_slots;
+            p->bk_gb_quad = hdr.gb_quad;
             SEL_CUDA("cudaMalloc", dev_alloc(&p->d_bk_blob, bp.blob.size()));
             SEL_CUDA("cudaMemcpy", cudaMemcpy(p->d_bk_blob, bp.blob.data(), bp.blob.size(), cudaMemcpyHostToDevice));
             bucket_ok = true;
@@ -1193,19 +1202,23 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     // default shape is the single-probe count's, with the context's overrides
     Shape best = single_shape(ctx, max_rb);
     int best_kernel = 0;
-    Shape bucket_default;   // 16 consumer warps, 3 stages that fill shared memory, or the context's overrides
+    // 15 consumer warps (11 when a table takes the quad form: its passes hold
+    // more registers), one chunk a pass, 3 stages that fill shared memory, or
+    // the context's overrides (measured on config 2's 5 probes and config 5's
+    // 256)
+    Shape bucket_default;
     bucket_default.stages = ctx->shape.stages > 0 ? ctx->shape.stages : 3;
     bucket_default.ctas_per_sm = 1;
     bucket_default.tile_rows = ctx->shape.tile_rows > 0 ? ctx->shape.tile_rows : kMaxTileRows;
     bucket_default.auto_tile = ctx->shape.tile_rows <= 0;
-    bucket_default.warps = 16;
+    bucket_default.warps = p->bk_gb_quad ? 11 : 15;
     bucket_default.group = 1;
     if (bucket_variant_ok(ctx->shape.warps, ctx->shape.group > 0 ? ctx->shape.group : 1)) {
         bucket_default.warps = ctx->shape.warps;
         bucket_default.group = ctx->shape.group > 0 ? ctx->shape.group : 1;
     }
     if (bucket_ok) {   // the first shape that fits (tables too large for any: the interpreter)
-        const int fallback[][3] = {{16, 1, 3}, {8, 1, 3}, {8, 1, 2}};   // warps, chunks per pass, stages
+        const int fallback[][3] = {{11, 1, 3}, {8, 1, 3}, {8, 1, 2}};   // warps, chunks per pass, stages
         sel_status rs = SEL_ERR_UNSUPPORTED;
         for (int c = -1; c < 3 && rs != SEL_OK; ++c) {
             Shape sh = bucket_default;

@@ -29,6 +29,18 @@
 // Several blocks on one table share the column's global bucket search; a
 // block whose leaves distinguish fewer buckets reads its gm table through a
 // remap of global to local bucket indices (uint16).
+//
+// Tables with 3 or more blocks take the quad form instead: blocks are grouped
+// by 4 into quads, and a quad's gm rows for a column are 128 bytes, block p's
+// 8 group words at bytes 32p .. 32p + 31 (each block still indexed by its own
+// local bucket, through a remap that gives the 4 local indices of a global
+// bucket in 8 bytes).  In the kernel a quarter-warp evaluates one row for the
+// whole quad: lane pair p reads block p's 32 bytes, so the 8 lanes of a
+// quarter always read 8 different 16-byte bank groups (one wavefront), where
+// the one-row-per-lane gathers of the block form collide in the banks about
+// half the time.  The block's init mask is folded into the rows of the quad's
+// first column, and each remap has two extra entries: k + 1 (rows past the
+// table's end) reads an all-zero row.
 #pragma once
 #include <stdint.h>
 
@@ -48,6 +60,10 @@ constexpr int kBkLinear = 8;         // at most this many boundaries: a linear c
 constexpr int kBkMaxCells = 2048;    // cells of a BK_CELLS column
 constexpr int kBkMaxOcc = 3;         // boundaries per cell for BK_CELLS
 constexpr uint32_t kBkIdentity = 0xFFFFFFFFu;   // remap_off: global bucket = local bucket
+constexpr int kBkQuadBlocks = 4;     // blocks of a quad
+constexpr int kBkQuadMinBlocks = 3;  // tables with at least this many blocks take the quad form
+constexpr int kBkQuadMaxSlots = 8;   // columns a quad table may read (bucket indices of a row: 16 bytes)
+constexpr uint32_t kBkNoOut = 0xFFFFFFFFu;      // a quad program slot with no probe
 
 // How a row's bucket on one column is found (BkSlot.mode).
 enum BkMode : uint32_t {
@@ -55,15 +71,18 @@ enum BkMode : uint32_t {
     BK_BINARY = 1,   // branch-free binary search over 2^steps - 1 padded boundaries
     BK_CELLS = 2,    // cell c = (x - lo) >> shift gives the buckets before the cell; at most occ
                      // boundaries inside one cell are then compared with x
+    BK_CELLS_BIN = 3,  // the same cells, then a branch-free binary search of 2^steps - 1 boundaries
+                       // from the cell's first (half = 2^(steps - 1); a cell holds fewer): boundaries
+                       // of later cells are all above x, so the search never passes the cell
 };
 
 // Search data of one referenced column of a table (48 bytes).
 struct BkSlot {
     uint32_t bnd_off;   // byte offset of the sorted boundaries (uint32 or uint64 by the slot width),
                         // padded with all-ones values (to 2^steps - 1 entries when searched, by occ
-                        // entries for cells)
+                        // entries for cells, by 2^steps - 1 for cells searched)
     uint32_t k;         // number of real boundaries; buckets 0..k
-    uint32_t half;      // BK_BINARY: 2^(steps - 1)
+    uint32_t half;      // BK_BINARY, BK_CELLS_BIN: 2^(steps - 1)
     uint32_t mode;      // BkMode
     uint32_t cells_off; // BK_CELLS: byte offset of n_cells uint16 counts of boundaries before each cell
     uint32_t n_cells;
@@ -88,8 +107,21 @@ struct BkBlock {
     uint32_t gm_off[kMaxSlots];     // per used column: gm table [local bucket][stride] uint32
 };
 
+// Up to 4 blocks of a quad table (quad form above).  A quad reads every
+// column of its table, in slot order (used[u] = u).
+struct BkQuad {
+    uint32_t n_used;                // columns the quad reads: the table's (<= kBkQuadMaxSlots)
+    uint32_t out_off;               // byte offset of 256 uint32 output indices: program k of block p at 64p + k
+                                    // (kBkNoOut: none)
+    uint32_t pad[2];
+    uint32_t used[kBkQuadMaxSlots];       // slot of each column the quad reads
+    uint32_t remap_off[kBkQuadMaxSlots];  // per used column: (k + 2) x 4 uint16 local rows of blocks 0..3
+    uint32_t gm_off[kBkQuadMaxSlots];     // per used column: 128-byte rows, block p's words at 32p
+};
+
 struct BkTable {
     uint32_t n_slots, n_blocks, block_off, max_buckets;   // block_off: byte offset of BkBlock[n_blocks]
+    uint32_t n_quads, quad_off, pad[2];                   // quad form: BkQuad[n_quads] (n_blocks is then 0)
     BkSlot slot[kMaxSlots];
 };
 
@@ -98,9 +130,20 @@ struct BkHeader {
     uint32_t n_tables;
     uint32_t n_out;       // per-CTA counters (one per probe of the launch)
     uint32_t gb_slots;    // >0: the kernel keeps global bucket indices of this many slots per warp in shared memory
-    uint32_t pad;
+    uint32_t gb_quad;     // 1: a quad table keeps a 16-byte record of bucket indices per row of a chunk per warp
     BkTable t[kMaxTables];
 };
+
+// Bytes of shared memory a consumer warp keeps bucket indices in, for G
+// chunks a pass: global indices of gb_slots slots (block form), or one
+// 16-byte record per row of a chunk (quad form; a chunk at a time).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t bk_gb_bytes_per_warp(uint32_t gb_slots, uint32_t gb_quad, uint32_t G) {
+    const uint32_t blocks = gb_slots * 8u * G * 32u * 2u, quads = gb_quad ? 256u * 16u : 0u;
+    return blocks > quads ? blocks : quads;
+}
 
 // The host side of a bucket plan: one blob for one launch (at most kMaxTables tables).
 struct BucketPlan {

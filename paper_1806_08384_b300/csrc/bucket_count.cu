@@ -39,7 +39,7 @@ __device__ __forceinline__ void bucket_rows(const BkSlot& sl, const uint8_t* blo
     const T* __restrict__ bnd = reinterpret_cast<const T*>(blob + sl.bnd_off);
     const uint32_t k = sl.k;
     const uint32_t mode = sl.mode;
-    if (mode == BK_CELLS) {
+    if (mode == BK_CELLS || mode == BK_CELLS_BIN) {
         // cell c = (x - lo) >> shift, clamped to the last cell above the
         // boundaries' span; below lo every boundary is above x: bucket 0
         const uint16_t* __restrict__ cells = reinterpret_cast<const uint16_t*>(blob + sl.cells_off);
@@ -53,6 +53,19 @@ __device__ __forceinline__ void bucket_rows(const BkSlot& sl, const uint8_t* blo
             const uint32_t b0 = cells[cc];
             idx[i] = v[i] < lo ? 0u : b0;
             base[i] = bnd + b0;
+        }
+        if (mode == BK_CELLS_BIN) {
+            // boundaries past the cell are above x: the search stays inside it
+            for (uint32_t h = sl.half; h; h >>= 1) {
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const uint32_t j = idx[i] + h;
+                    if (v[i] >= bnd[j - 1]) idx[i] = j;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < R; ++i) idx[i] = min(idx[i], k);
+            return;
         }
 #pragma unroll
         for (uint32_t t = 0; t < (uint32_t)kBkMaxOcc; ++t) {
@@ -126,7 +139,7 @@ __device__ __forceinline__ void slot_buckets(const uint8_t* blob, const BkSlot& 
 template <int NW>
 __device__ __forceinline__ void count_fields(const uint8_t* blob, const BkBlock& bk, const uint32_t (&N0)[NW],
                                              const uint32_t (&N1)[NW], uint32_t chunks, uint32_t lane,
-                                             unsigned long long* cnt) {
+                                             uint32_t* cnt) {
     const uint32_t* outs = reinterpret_cast<const uint32_t*>(blob + bk.out_off);
     const uint32_t n_words = bk.n_words, n_progs = bk.n_progs;
 #pragma unroll
@@ -141,7 +154,7 @@ __device__ __forceinline__ void count_fields(const uint8_t* blob, const BkBlock&
         const uint32_t pair = (j & 3u) == 0 ? f0 : (j & 3u) == 1 ? f1 : (j & 3u) == 2 ? f2 : f3;
         const uint32_t c = (pair >> (16u * (j >> 2))) & 0xFFFFu;
         const uint32_t k = 8u * (uint32_t)w + j;
-        if (lane < 8 && k < n_progs && c) atomicAdd(&cnt[outs[k]], static_cast<unsigned long long>(c));
+        if (lane < 8 && k < n_progs && c) atomicAdd(&cnt[outs[k]], c);
     }
 }
 
@@ -153,7 +166,7 @@ template <int NW>
 __device__ __forceinline__ void eval_block(const uint8_t* blob, const BkTable& bt, const BkBlock& bk,
                                            const TableArg& T, const uint32_t* s_off, uint32_t st_addr, uint32_t c0,
                                            uint32_t lane, uint32_t vm, const uint16_t* gbuf, uint32_t gstride,
-                                           unsigned long long* cnt) {
+                                           uint32_t* cnt) {
     constexpr int STRIDE = NW == 8 ? 12 : NW;
     constexpr int ROWS = NW == 8 ? 4 : 8;
     uint32_t N[NW];
@@ -225,7 +238,7 @@ template <int NW>
 __device__ __forceinline__ void eval_block2(const uint8_t* blob, const BkTable& bt, const BkBlock& bk,
                                             const TableArg& T, const uint32_t* s_off, uint32_t st_addr,
                                             const uint32_t (&c0)[2], uint32_t lane, const uint32_t (&vm)[2],
-                                            const uint16_t* gbuf, unsigned long long* cnt) {
+                                            const uint16_t* gbuf, uint32_t* cnt) {
     uint32_t R[16][NW];
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
@@ -292,12 +305,166 @@ __device__ __forceinline__ void eval_block2(const uint8_t* blob, const BkTable& 
     count_fields<NW>(blob, bk, N0, N1, 2, lane, cnt);
 }
 
+__device__ __forceinline__ uint32_t lds_u16(uint32_t addr) {
+    uint32_t v;
+    asm("ld.shared.u16 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
+// The bucket record of every row of the chunk at c0 (quad form): entry
+// e = 32 i + lane (the lane's row i) holds the bucket index of slot s at
+// uint16 s of its 16 bytes; rows past the table's end (vm bit clear) get
+// index k + 1, whose remap entry reads the all-zero row.
+__device__ __forceinline__ void fill_records(const uint8_t* blob, const BkTable& bt, const TableArg& T,
+                                             const uint32_t* s_off, uint32_t st_addr, uint32_t c0, uint32_t lane,
+                                             uint32_t vm, uint32_t rec_addr) {
+    for (uint32_t sl = 0; sl < bt.n_slots; ++sl) {
+        uint32_t b[8];
+        slot_buckets<8>(blob, bt.slot[sl], T.width[sl], st_addr + s_off[sl], c0, lane, 0u, b);
+        if (vm != 0xFFu) {
+            const uint32_t past = bt.slot[sl].k + 1u;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (!((vm >> i) & 1u)) b[i] = past;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t a = rec_addr + ((32u * i + lane) * 8u + sl) * 2u;
+            asm volatile("st.shared.u16 [%0], %1;" ::"r"(a), "h"(static_cast<unsigned short>(b[i])) : "memory");
+        }
+    }
+}
+
+// The 4-bit fields of w, each OR-ed into its low bit (bit 4k).
+__device__ __forceinline__ uint32_t field_any(uint32_t w) {
+    uint32_t t = w | (w >> 1);
+    t |= t >> 2;
+    return t & 0x11111111u;
+}
+
+// One quad on one chunk whose row records are at rec_addr (NS slots): quarter
+// qq takes rows e = 4t + qq; in it lane pair p ANDs block p's group words
+// (lane h of the pair words 4h .. 4h + 3) over the slots, ORs each program's
+// group bits and counts them in 4-bit fields (flushed every 8 rows into
+// 8-bit fields).  At the end the 4 quarters' counts are summed and each
+// program's count is added to the per-CTA counters.
+template <int NS>
+__device__ __forceinline__ void eval_quad(const uint8_t* blob, const BkQuad& Q, uint32_t blob_addr, uint32_t rec_addr,
+                                          uint32_t lane, uint32_t* cnt) {
+    const uint32_t qq = lane >> 3, p = (lane >> 1) & 3u, h = lane & 1u;
+    uint32_t rmb[NS], gmb[NS];
+#pragma unroll
+    for (int u = 0; u < NS; ++u) {
+        rmb[u] = blob_addr + Q.remap_off[u] + 2u * p;
+        gmb[u] = blob_addr + Q.gm_off[u] + 32u * p + 16u * h;
+    }
+    uint32_t N[4] = {0u, 0u, 0u, 0u}, C[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+    const uint32_t rec0 = rec_addr + qq * 16u;
+#pragma unroll 1
+    for (uint32_t t8 = 0; t8 < 64u; t8 += 8u) {
+#pragma unroll 2
+        for (uint32_t t = t8; t < t8 + 8u; ++t) {
+            const uint4 r = lds128(rec0 + t * 64u);
+            const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
+            uint32_t R[4];
+#pragma unroll
+            for (int u = 0; u < NS; ++u) {
+                const uint32_t b = (u & 1) ? (rw[u >> 1] >> 16) : (rw[u >> 1] & 0xFFFFu);
+                const uint32_t l = lds_u16(rmb[u] + b * 8u);
+                const uint4 x = lds128(gmb[u] + l * 128u);
+                if (u == 0) {
+                    R[0] = x.x;
+                    R[1] = x.y;
+                    R[2] = x.z;
+                    R[3] = x.w;
+                } else {
+                    R[0] &= x.x;
+                    R[1] &= x.y;
+                    R[2] &= x.z;
+                    R[3] &= x.w;
+                }
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) N[w] += field_any(R[w]);   // a field stays <= 8
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {   // fields 0, 2, 4, 6 and 1, 3, 5, 7 into bytes (<= 64 a chunk)
+            C[2 * w] += N[w] & 0x0F0F0F0Fu;
+            C[2 * w + 1] += (N[w] >> 4) & 0x0F0F0F0Fu;
+            N[w] = 0u;
+        }
+    }
+    // bytes to 16-bit halves (field f of word w: C[2w + (f & 1)], byte f / 2),
+    // summed over the quarters (<= 256)
+    uint32_t H[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        H[2 * j] = C[j] & 0x00FF00FFu;             // bytes 0, 2
+        H[2 * j + 1] = (C[j] >> 8) & 0x00FF00FFu;  // bytes 1, 3
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        H[j] += __shfl_xor_sync(0xFFFFFFFFu, H[j], 8);
+        H[j] += __shfl_xor_sync(0xFFFFFFFFu, H[j], 16);
+    }
+    // quarter qq adds word w = qq of the lane's 4: fields f = 0..7 of block
+    // p's word 4h + qq, i.e. program 8 (4h + qq) + f
+    const uint32_t* outs = reinterpret_cast<const uint32_t*>(blob + Q.out_off) + 64u * p + 8u * (4u * h + qq);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        if ((uint32_t)w != qq) continue;
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+            // C[2w + (f & 1)] byte f / 2: byte 0 or 2 -> H[2j] low/high half, byte 1 or 3 -> H[2j + 1]
+            const int j = 2 * w + (f & 1), byte = f >> 1;
+            const uint32_t hv = H[2 * j + (byte & 1)];
+            const uint32_t c = (byte >> 1) ? (hv >> 16) : (hv & 0xFFFFu);
+            const uint32_t o = outs[f];
+            if (c && o != kBkNoOut) atomicAdd(&cnt[o], c);
+        }
+    }
+}
+
+// Every quad of a quad table on the chunk at c0 (the warp's records at
+// rec_addr are rewritten for each chunk).
+__device__ __forceinline__ void eval_quads(const uint8_t* blob, const BkTable& bt, const TableArg& T,
+                                           const uint32_t* s_off, uint32_t st_addr, uint32_t c0, uint32_t lane,
+                                           uint32_t vm, uint32_t rec_addr, uint32_t* cnt) {
+    fill_records(blob, bt, T, s_off, st_addr, c0, lane, vm, rec_addr);
+    __syncwarp();
+    const BkQuad* quads = reinterpret_cast<const BkQuad*>(blob + bt.quad_off);
+    const uint32_t blob_addr = smem_u32(blob);
+    for (uint32_t qi = 0; qi < bt.n_quads; ++qi) {
+        const BkQuad& Q = quads[qi];
+        switch (Q.n_used) {
+        case 1: eval_quad<1>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        case 2: eval_quad<2>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        case 3: eval_quad<3>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        case 4: eval_quad<4>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        case 5: eval_quad<5>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        case 6: eval_quad<6>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        case 7: eval_quad<7>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        default: eval_quad<8>(blob, Q, blob_addr, rec_addr, lane, cnt); break;
+        }
+    }
+    __syncwarp();   // the records are rewritten for the next chunk
+}
+
 // All blocks of a table on G chunks (c0[q], valid rows vm[q]; vm 0: no chunk).
 template <int G>
 __device__ __forceinline__ void eval_chunks(const uint8_t* blob, const BkTable& bt, const TableArg& T,
                                             const uint32_t* s_off, uint32_t st_addr, const uint32_t (&c0)[G],
                                             uint32_t lane, const uint32_t (&vm)[G], uint32_t n_have, uint16_t* gbuf,
-                                            unsigned long long* cnt) {
+                                            uint32_t* cnt) {
+    if (bt.n_quads > 0) {
+        const uint32_t rec_addr = smem_u32(gbuf);
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            if ((uint32_t)q >= n_have) break;   // the group's missing chunk (the same on every lane)
+            eval_quads(blob, bt, T, s_off, st_addr, c0[q], lane, vm[q], rec_addr, cnt);
+        }
+        return;
+    }
     const BkBlock* blocks = reinterpret_cast<const BkBlock*>(blob + bt.block_off);
     const uint32_t n_blocks = bt.n_blocks;
     const uint16_t* gb = nullptr;
@@ -341,13 +508,13 @@ __device__ __forceinline__ void eval_chunks(const uint8_t* blob, const BkTable& 
 
 template <int W, int G>
 __device__ __forceinline__ void consume_buckets(const ScanArgs& a, const uint8_t* blob, uint64_t* full, uint64_t* empty,
-                                                unsigned long long* cnt, uint8_t* stages, uint16_t* gbuf_all,
+                                                uint32_t* cnt, uint8_t* stages, uint16_t* gbuf_all,
                                                 const uint32_t (&s_off)[kMaxTables][kMaxSlots], uint32_t* s_fail,
                                                 uint32_t warp, uint32_t lane) {
     const BkHeader* hdr = reinterpret_cast<const BkHeader*>(blob);
     const int64_t NB = gridDim.x;
     const uint32_t S = a.stages;
-    uint16_t* gbuf = gbuf_all + (size_t)warp * hdr->gb_slots * 8u * G * 32u;
+    uint16_t* gbuf = gbuf_all + (size_t)warp * (bk_gb_bytes_per_warp(hdr->gb_slots, hdr->gb_quad, G) / 2u);
     uint32_t rot = 0;   // running chunk-group count: group c of a tile belongs to warp (rot + c) % W
     uint32_t s = 0, parity = 0;
     for (int64_t k = 0;; ++k) {
@@ -406,7 +573,8 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) bucket_count_kernel(const __g
     const uint32_t S = a.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + S;
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(smem + a.cnt_off);
+    // per-CTA counts: 32 bits (a CTA scans fewer than 2^32 rows: checked on the host)
+    uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + a.cnt_off);
     uint8_t* stages = smem + a.stage_off;
 
     if (tid == 0) {
@@ -419,7 +587,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) bucket_count_kernel(const __g
     }
     for (uint32_t i = tid; i < kMaxTables * kMaxSlots; i += blockDim.x)
         s_off[i / kMaxSlots][i % kMaxSlots] = a.t[i / kMaxSlots].slot_off[i % kMaxSlots];
-    for (uint32_t p = tid; p < a.n_progs; p += blockDim.x) cnt[p] = 0ull;
+    for (uint32_t p = tid; p < a.n_progs; p += blockDim.x) cnt[p] = 0u;
     {
         uint4* dst = reinterpret_cast<uint4*>(smem + a.prog_off);
         const uint4* src = reinterpret_cast<const uint4*>(a.blob);
@@ -457,7 +625,7 @@ __global__ void __launch_bounds__((W + 1) * 32, 1) bucket_count_kernel(const __g
     __syncthreads();
     if (s_fail) return;
     for (uint32_t p = tid; p < a.n_progs; p += blockDim.x)
-        if (cnt[p]) atomicAdd(&a.counts[p], cnt[p]);
+        if (cnt[p]) atomicAdd(&a.counts[p], static_cast<unsigned long long>(cnt[p]));
 }
 
 static inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -465,7 +633,7 @@ static inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a
 size_t bucket_layout(ScanArgs& a, int warps, uint32_t gb_bytes_per_warp) {
     a.prog_in_smem = 1;
     a.cnt_off = align_up(16u * a.stages, 16u);
-    a.prog_off = align_up(a.cnt_off + 8u * a.n_progs, 16u);
+    a.prog_off = align_up(a.cnt_off + 4u * a.n_progs, 16u);
     a.aux_off = align_up(a.prog_off + align_up(a.blob_bytes, 16u), 16u);
     a.stage_off = align_up(a.aux_off + (uint32_t)warps * gb_bytes_per_warp, 128u);
     return static_cast<size_t>(a.stage_off) + static_cast<size_t>(a.stages) * a.stage_bytes;

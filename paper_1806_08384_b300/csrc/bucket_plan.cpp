@@ -402,8 +402,9 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
         }
         // search data: a linear count for up to 4 boundaries, a direct table
         // when every cell is one value, cells when at most kBkMaxOcc
-        // boundaries share a cell, else a linear count (up to kBkLinear) or a
-        // binary search
+        // boundaries share a cell, cells and a binary search inside the cell
+        // when that takes 2 or more steps fewer than a binary search of all
+        // boundaries, else a linear count (up to kBkLinear) or a binary search
         for (uint32_t s = 0; s < bt.n_slots; ++s) {
             const uint32_t w = T.slot_width[s];
             const std::vector<uint64_t>& B = bnd[s];
@@ -434,27 +435,34 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
                         upto += occ[c];
                         cells[c] = (uint16_t)upto;
                     }
-                } else if (mx <= (uint32_t)kBkMaxOcc) {
-                    sl.mode = BK_CELLS;
-                    sl.lo = B.front();
-                    sl.shift = shift;
-                    sl.n_cells = n_cells;
-                    sl.occ = mx;
-                    cells.resize(n_cells);
-                    uint32_t before = 0;
-                    for (uint32_t c = 0; c < n_cells; ++c) {
-                        cells[c] = (uint16_t)before;
-                        before += occ[c];
-                    }
-                    n_entries = (size_t)sl.k + mx;
-                } else if (sl.k <= (uint32_t)kBkLinear) {
-                    sl.mode = BK_LINEAR;
                 } else {
-                    sl.mode = BK_BINARY;
-                    uint32_t steps = 0;
+                    uint32_t steps = 0, cell_steps = 0;   // full binary search; search inside the fullest cell
                     while (((size_t)1 << steps) < (size_t)sl.k + 1) ++steps;
-                    sl.half = 1u << (steps - 1);
-                    n_entries = ((size_t)1 << steps) - 1;
+                    while (((size_t)1 << cell_steps) < (size_t)mx + 1) ++cell_steps;
+                    if (mx <= (uint32_t)kBkMaxOcc || (sl.k > (uint32_t)kBkLinear && cell_steps + 1 < steps)) {
+                        // cells, then up to 3 compares, or a search of cell_steps steps
+                        // (a cell lookup costs about one step)
+                        const bool bin = mx > (uint32_t)kBkMaxOcc;
+                        sl.mode = bin ? BK_CELLS_BIN : BK_CELLS;
+                        sl.lo = B.front();
+                        sl.shift = shift;
+                        sl.n_cells = n_cells;
+                        sl.occ = bin ? 0u : mx;
+                        sl.half = bin ? 1u << (cell_steps - 1) : 0u;
+                        cells.resize(n_cells);
+                        uint32_t before = 0;
+                        for (uint32_t c = 0; c < n_cells; ++c) {
+                            cells[c] = (uint16_t)before;
+                            before += occ[c];
+                        }
+                        n_entries = (size_t)sl.k + (bin ? ((size_t)1 << cell_steps) - 1 : mx);
+                    } else if (sl.k <= (uint32_t)kBkLinear) {
+                        sl.mode = BK_LINEAR;
+                    } else {
+                        sl.mode = BK_BINARY;
+                        sl.half = 1u << (steps - 1);
+                        n_entries = ((size_t)1 << steps) - 1;
+                    }
                 }
             }
             std::vector<uint8_t> raw(std::max<size_t>(n_entries, 1) * w, 0xFF);
@@ -470,11 +478,18 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
             if (!cells.empty()) sl.cells_off = (uint32_t)append(blob, cells.data(), cells.size() * 2);
             bt.max_buckets = std::max(bt.max_buckets, sl.k + 1);
         }
-        // blocks
+        // blocks: for each, its columns, and per column the gm rows of its
+        // distinct buckets (local rows) and the global -> local remap
         const size_t np = T.progs.size();
         const uint32_t n_blocks = (uint32_t)((np + kBkBlockProgs - 1) / kBkBlockProgs);
-        bt.n_blocks = n_blocks;
+        struct SlotRows {
+            std::vector<uint32_t> rows;    // local rows, stride words each
+            std::vector<uint16_t> remap;   // global bucket -> local row
+            bool identity;                 // local rows are the global buckets
+        };
         std::vector<BkBlock> blocks(n_blocks);
+        std::vector<std::vector<uint32_t>> block_outs(n_blocks);
+        std::vector<std::vector<SlotRows>> block_rows(n_blocks);
         for (uint32_t bi = 0; bi < n_blocks; ++bi) {
             BkBlock& bk = blocks[bi];
             std::memset(&bk, 0, sizeof(bk));
@@ -483,22 +498,20 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
             bk.n_words = (bk.n_progs + kBkProgsPerWord - 1) / kBkProgsPerWord;
             bk.nw = bk.n_words <= 1 ? 1 : bk.n_words <= 2 ? 2 : bk.n_words <= 4 ? 4 : 8;
             bk.stride = bk.nw == 8 ? 12 : bk.nw;
-            std::vector<uint32_t> outs(bk.n_progs);
+            std::vector<uint32_t>& outs = block_outs[bi];
+            outs.resize(bk.n_progs);
             for (size_t k = 0; k < bk.n_progs; ++k) {
                 outs[k] = T.outs[p0 + k];
                 const size_t g = dnfs[p0 + k].size();
                 bk.init[k / kBkProgsPerWord] |= ((1u << g) - 1u) << (4 * (k % kBkProgsPerWord));
             }
-            bk.out_off = (uint32_t)append(blob, outs.data(), outs.size() * 4);
-            // the block's columns
             std::vector<uint8_t> uses(bt.n_slots, 0);
             for (size_t k = p0; k < p1; ++k)
                 for (const Group& g : dnfs[k])
                     for (Lit l : g) uses[b.leaves[l >> 1].slot] = 1;
             for (uint32_t s = 0; s < bt.n_slots; ++s) {
                 if (!uses[s]) continue;
-                const uint32_t u = bk.n_used++;
-                bk.used[u] = s;
+                bk.used[bk.n_used++] = s;
                 const uint32_t nb = (uint32_t)bnd[s].size() + 1;
                 // gm rows per global bucket
                 std::vector<uint32_t> rows((size_t)nb * bk.stride, 0xFFFFFFFFu);
@@ -515,13 +528,12 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
                         }
                     }
                 }
-                std::vector<uint32_t> gm;
-                if (n_blocks == 1) {
-                    bk.remap_off[u] = kBkIdentity;
-                    gm.swap(rows);
-                } else {
+                SlotRows sr;
+                sr.identity = true;
+                if (n_blocks > 1) {
                     std::map<std::vector<uint32_t>, uint16_t> local;
-                    std::vector<uint16_t> remap(nb);
+                    std::vector<uint32_t> gm;
+                    sr.remap.resize(nb);
                     for (uint32_t j = 0; j < nb; ++j) {
                         std::vector<uint32_t> r(rows.begin() + (size_t)j * bk.stride,
                                                 rows.begin() + (size_t)(j + 1) * bk.stride);
@@ -530,20 +542,97 @@ sel_status build_bucket_plan(const std::vector<BkTableIn>& tabs, BucketPlan* out
                             it = local.emplace(r, (uint16_t)(gm.size() / bk.stride)).first;
                             gm.insert(gm.end(), r.begin(), r.end());
                         }
-                        remap[j] = it->second;
+                        sr.remap[j] = it->second;
                     }
-                    if (gm.size() == rows.size()) {
-                        bk.remap_off[u] = kBkIdentity;
-                        gm.swap(rows);
-                    } else {
-                        bk.remap_off[u] = (uint32_t)append(blob, remap.data(), remap.size() * 2);
+                    if (gm.size() != rows.size()) {
+                        sr.identity = false;
+                        rows.swap(gm);
                     }
                 }
-                bk.gm_off[u] = (uint32_t)append(blob, gm.data(), gm.size() * 4);
+                if (sr.identity) {
+                    sr.remap.resize(nb);
+                    for (uint32_t j = 0; j < nb; ++j) sr.remap[j] = (uint16_t)j;
+                }
+                sr.rows.swap(rows);
+                block_rows[bi].push_back(std::move(sr));
             }
         }
-        bt.block_off = (uint32_t)append(blob, blocks.data(), blocks.size() * sizeof(BkBlock));
-        if (n_blocks > 1) hdr.gb_slots = std::max(hdr.gb_slots, bt.n_slots);
+        // the quad form: at least kBkQuadMinBlocks blocks and 1 to
+        // kBkQuadMaxSlots columns
+        const bool quad = n_blocks >= (uint32_t)kBkQuadMinBlocks && bt.n_slots >= 1 &&
+                          bt.n_slots <= (uint32_t)kBkQuadMaxSlots;
+        const uint32_t n_quads = (n_blocks + kBkQuadBlocks - 1) / kBkQuadBlocks;
+        if (!quad) {
+            for (uint32_t bi = 0; bi < n_blocks; ++bi) {
+                BkBlock& bk = blocks[bi];
+                bk.out_off = (uint32_t)append(blob, block_outs[bi].data(), block_outs[bi].size() * 4);
+                for (uint32_t u = 0; u < bk.n_used; ++u) {
+                    const SlotRows& sr = block_rows[bi][u];
+                    bk.remap_off[u] =
+                        sr.identity ? kBkIdentity : (uint32_t)append(blob, sr.remap.data(), sr.remap.size() * 2);
+                    bk.gm_off[u] = (uint32_t)append(blob, sr.rows.data(), sr.rows.size() * 4);
+                }
+            }
+            bt.n_blocks = n_blocks;
+            bt.block_off = (uint32_t)append(blob, blocks.data(), blocks.size() * sizeof(BkBlock));
+            if (n_blocks > 1) hdr.gb_slots = std::max(hdr.gb_slots, bt.n_slots);
+        } else {
+            std::vector<BkQuad> quads(n_quads);
+            for (uint32_t qi = 0; qi < n_quads; ++qi) {
+                BkQuad& Q = quads[qi];
+                std::memset(&Q, 0, sizeof(Q));
+                const uint32_t b0 = qi * kBkQuadBlocks, nq = std::min<uint32_t>(kBkQuadBlocks, n_blocks - b0);
+                std::vector<uint32_t> outs(kBkQuadBlocks * kBkBlockProgs, kBkNoOut);
+                for (uint32_t p = 0; p < nq; ++p)
+                    for (size_t k = 0; k < block_outs[b0 + p].size(); ++k) outs[p * kBkBlockProgs + k] = block_outs[b0 + p][k];
+                Q.out_off = (uint32_t)append(blob, outs.data(), outs.size() * 4);
+                // every column of the table, in slot order (the kernel's row
+                // records hold the indices in that order; a column no block of
+                // the quad reads has only the all-ones and the zero row)
+                for (uint32_t s = 0; s < bt.n_slots; ++s) {
+                    const uint32_t u = Q.n_used++;
+                    Q.used[u] = s;
+                    // block p's local rows of column s (none: it has no leaf there)
+                    const SlotRows* sr[kBkQuadBlocks] = {nullptr, nullptr, nullptr, nullptr};
+                    uint32_t n_local = 0;
+                    for (uint32_t p = 0; p < nq; ++p) {
+                        const BkBlock& bk = blocks[b0 + p];
+                        for (uint32_t v = 0; v < bk.n_used; ++v)
+                            if (bk.used[v] == s) sr[p] = &block_rows[b0 + p][v];
+                        if (sr[p]) n_local = std::max<uint32_t>(n_local, (uint32_t)(sr[p]->rows.size() / bk.stride));
+                    }
+                    const uint32_t R = n_local + 2, one = R - 2, zero = R - 1;
+                    const uint32_t nb = (uint32_t)bnd[s].size() + 1;
+                    std::vector<uint32_t> gm((size_t)R * 32, 0u);
+                    for (uint32_t p = 0; p < nq; ++p) {
+                        const uint32_t stride = blocks[b0 + p].stride;
+                        for (uint32_t r = 0; r < R; ++r)
+                            for (uint32_t w = 0; w < (uint32_t)kBkMaxWords; ++w) {
+                                uint32_t v = 0;
+                                if (r == one) v = 0xFFFFFFFFu;
+                                else if (sr[p] && r < sr[p]->rows.size() / stride && w < stride)
+                                    v = sr[p]->rows[(size_t)r * stride + w];
+                                if (u == 0) v &= blocks[b0 + p].init[w];   // the init mask, once
+                                gm[(size_t)r * 32 + 8 * p + w] = v;
+                            }
+                    }
+                    std::vector<uint16_t> remap((size_t)(nb + 1) * kBkQuadBlocks, (uint16_t)zero);
+                    for (uint32_t j = 0; j < nb; ++j)
+                        for (uint32_t p = 0; p < nq; ++p)
+                            remap[(size_t)j * kBkQuadBlocks + p] = sr[p] ? sr[p]->remap[j] : (uint16_t)one;
+                    if (R > 65536u) {
+                        *why = "internal: more than 65536 local rows";
+                        return SEL_ERR_UNSUPPORTED;
+                    }
+                    Q.remap_off[u] = (uint32_t)append(blob, remap.data(), remap.size() * 2);
+                    Q.gm_off[u] = (uint32_t)append(blob, gm.data(), gm.size() * 4);
+                }
+            }
+            bt.n_blocks = n_blocks;   // the blocks themselves are not kept: n_quads > 0 selects the quad form
+            bt.n_quads = n_quads;
+            bt.quad_off = (uint32_t)append(blob, quads.data(), quads.size() * sizeof(BkQuad));
+            hdr.gb_quad = 1;
+        }
     }
     hdr.n_out = n_out;
     while (blob.size() % 16) blob.push_back(0);
@@ -567,12 +656,17 @@ uint32_t host_bucket(const std::vector<uint8_t>& blob, const BkSlot& sl, uint32_
         for (uint32_t j = 0; j < sl.k; ++j) idx += x >= bnd(j) ? 1u : 0u;
         return idx;
     }
-    if (sl.mode == BK_CELLS) {
+    if (sl.mode == BK_CELLS || sl.mode == BK_CELLS_BIN) {
         if (x < sl.lo) return 0;
         const uint64_t c = std::min<uint64_t>((x - sl.lo) >> sl.shift, sl.n_cells - 1);
         const uint32_t base = rd<uint16_t>(blob, sl.cells_off + 2 * (size_t)c);
         idx = base;
-        for (uint32_t t = 0; t < sl.occ; ++t) idx += x >= bnd(base + t) ? 1u : 0u;
+        if (sl.mode == BK_CELLS) {
+            for (uint32_t t = 0; t < sl.occ; ++t) idx += x >= bnd(base + t) ? 1u : 0u;
+        } else {
+            for (uint32_t h = sl.half; h; h >>= 1)
+                if (x >= bnd(idx + h - 1)) idx += h;
+        }
         return std::min(idx, sl.k);
     }
     for (uint32_t h = sl.half; h; h >>= 1)
@@ -590,8 +684,11 @@ void bucket_eval_host(const BucketPlan& plan, const std::vector<std::vector<cons
     std::memcpy(&hdr, blob.data(), sizeof(hdr));
     for (uint32_t ti = 0; ti < hdr.n_tables; ++ti) {
         const BkTable& bt = hdr.t[ti];
-        std::vector<BkBlock> blocks(bt.n_blocks);
+        const bool quad = bt.n_quads > 0;
+        std::vector<BkBlock> blocks(quad ? 0 : bt.n_blocks);
         std::memcpy(blocks.data(), blob.data() + bt.block_off, blocks.size() * sizeof(BkBlock));
+        std::vector<BkQuad> quads(bt.n_quads);
+        std::memcpy(quads.data(), blob.data() + bt.quad_off, quads.size() * sizeof(BkQuad));
         std::vector<uint32_t> gb(bt.n_slots);
         for (int64_t r = 0; r < n_rows[ti]; ++r) {
             for (uint32_t s = 0; s < bt.n_slots; ++s) {
@@ -600,6 +697,24 @@ void bucket_eval_host(const BucketPlan& plan, const std::vector<std::vector<cons
                 std::memcpy(&x, cols[ti][s] + (size_t)r * w, w);
                 gb[s] = host_bucket(blob, bt.slot[s], w, x);
             }
+            // quad form: block p's words of the row are the AND over the
+            // quad's columns of its 8 words in the row its remap gives
+            for (const BkQuad& Q : quads)
+                for (uint32_t p = 0; p < (uint32_t)kBkQuadBlocks; ++p) {
+                    uint32_t R[kBkMaxWords];
+                    for (uint32_t w = 0; w < kBkMaxWords; ++w) R[w] = 0xFFFFFFFFu;
+                    for (uint32_t u = 0; u < Q.n_used; ++u) {
+                        const uint32_t s = Q.used[u];
+                        const uint32_t lb = rd<uint16_t>(blob, Q.remap_off[u] + 2 * ((size_t)gb[s] * kBkQuadBlocks + p));
+                        for (uint32_t w = 0; w < kBkMaxWords; ++w)
+                            R[w] &= rd<uint32_t>(blob, Q.gm_off[u] + 4 * ((size_t)lb * 32 + 8 * p + w));
+                    }
+                    for (uint32_t k = 0; k < (uint32_t)kBkBlockProgs; ++k) {
+                        const uint32_t o = rd<uint32_t>(blob, Q.out_off + 4 * ((size_t)p * kBkBlockProgs + k));
+                        if (o != kBkNoOut && ((R[k / kBkProgsPerWord] >> (4 * (k % kBkProgsPerWord))) & 0xFu))
+                            ++counts[o];
+                    }
+                }
             for (const BkBlock& bk : blocks) {
                 uint32_t R[kBkMaxWords];
                 for (uint32_t w = 0; w < kBkMaxWords; ++w) R[w] = bk.init[w];
@@ -623,7 +738,7 @@ void bucket_eval_host(const BucketPlan& plan, const std::vector<std::vector<cons
 using namespace sel;
 
 extern "C" sel_status sel_debug_bucket_count_host(const sel_pred* const* preds, int32_t n, const sel_table* table,
-                                                  uint64_t* counts, int32_t* n_blocks) {
+                                                  uint64_t* counts, int32_t* n_blocks, int32_t* n_quads) {
     if (!preds || n <= 0 || !table || !counts || table->n_rows < 0 || (table->n_cols > 0 && !table->cols)) {
         set_error("sel_debug_bucket_count_host: bad arguments");
         return SEL_ERR_INVALID_ARG;
@@ -673,6 +788,7 @@ extern "C" sel_status sel_debug_bucket_count_host(const sel_pred* const* preds, 
     BkHeader hdr;
     std::memcpy(&hdr, plan.blob.data(), sizeof(hdr));
     if (n_blocks) *n_blocks = (int32_t)hdr.t[0].n_blocks;
+    if (n_quads) *n_quads = (int32_t)hdr.t[0].n_quads;
     std::memset(counts, 0, sizeof(uint64_t) * (size_t)n);
     bucket_eval_host(plan, {ptrs}, {in.slot_width}, {table->n_rows}, counts);
     return SEL_OK;

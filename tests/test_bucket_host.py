@@ -23,6 +23,10 @@ def _host_counts(preds, T):
     return sel.debug_bucket_count_host(preds, T)
 
 
+def _quads(preds, T):
+    return sel.debug_bucket_count_host(preds, T, with_quads=True)[2]
+
+
 def _fits(T, trees):
     """The trees whose programs fit the form (each checked alone), in order."""
     out = []
@@ -47,7 +51,15 @@ def test_random_trees_tiny(n):
     preds = [sel.Predicate(T, tr) for tr in fit]
     got, blocks = _host_counts(preds, T)
     assert blocks == (len(fit) + 63) // 64
-    assert got == [oracle.count(ot, tr) for tr in fit]
+    want = [oracle.count(ot, tr) for tr in fit]
+    assert got == want
+    # 3 or more blocks take the quad form (here 4 blocks, one quad); 2 blocks
+    # the block form with remapped tables
+    assert _quads(preds, T) == (blocks + 3) // 4 and blocks >= 3
+    got2, blocks2 = _host_counts(preds[:128], T)
+    assert blocks2 == 2 and _quads(preds[:128], T) == 0 and got2 == want[:128]
+    got3 = _host_counts(preds[:129], T)[0]      # a quad of 3 blocks, the last of 1 probe
+    assert _quads(preds[:129], T) == 1 and got3 == want[:129]
 
 
 def _edge_table():
@@ -140,11 +152,35 @@ def test_config_shaped_batches():
     got, blocks = _host_counts([sel.Predicate(T5, tr) for tr in trees], T5)
     assert blocks == 4
     assert got == [oracle.count(ot5, tr) for tr in trees]
+    assert _quads([sel.Predicate(T5, tr) for tr in trees], T5) == 1
     rng = np.random.default_rng(9)
     trees = [dg.random_dnf_predicate(dg.config2_specs(), rng) for _ in range(300)]
     got, blocks = _host_counts([sel.Predicate(T2, tr) for tr in trees], T2)
     assert blocks == 5
+    assert _quads([sel.Predicate(T2, tr) for tr in trees], T2) == 2     # the second quad holds 1 block
     assert got == [oracle.count(ot2, tr) for tr in trees]
+
+
+def test_quad_form_needs_at_most_eight_columns():
+    """A table of 10 columns keeps the block form at 4 blocks; 8 columns take
+    quads (rows of a column no probe of a quad reads are all ones)."""
+    specs = [dg.ColumnSpec(f"c{i}", "i32", "uniform", 0, 50) for i in range(10)]
+    t = dg.gen_table("wide10", specs, 5_003, "cpu")
+    ot, T = oracle.OTable.from_table(t), sel.Table(t.columns)
+    rng = np.random.default_rng(12)
+    trees = [dg.random_dnf_predicate(specs, rng) for _ in range(256)]
+    preds = [sel.Predicate(T, tr) for tr in trees]
+    got, blocks = _host_counts(preds, T)
+    assert blocks == 4 and _quads(preds, T) == 0
+    assert got == [oracle.count(ot, tr) for tr in trees]
+    t8 = dg.gen_table("wide8", specs[:8], 5_003, "cpu")
+    ot8, T8 = oracle.OTable.from_table(t8), sel.Table(t8.columns)
+    trees = [dg.random_dnf_predicate(specs[:8], rng) for _ in range(200)]
+    trees += [dg.p_between(0, 3, 9)] * 64      # a fourth block that reads one column only
+    preds = [sel.Predicate(T8, tr) for tr in trees]
+    got, blocks = _host_counts(preds, T8)
+    assert blocks == 5 and _quads(preds, T8) == 2
+    assert got == [oracle.count(ot8, tr) for tr in trees]
 
 
 def test_programs_beyond_four_groups_are_refused():

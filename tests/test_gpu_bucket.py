@@ -3,10 +3,12 @@
 Plans are forced onto the bucket kernel (sel_ctx_set_batch_kernel mode 2) and
 run over tiny tables of every ragged size, the edge-value table (float32 +-0,
 infinities, NaN, denormals, the ends of int32 and int64), config 2's probes
-on a 300,001-row table in several launch shapes (tile rows, stages, 8 or 16
-consumer warps), several blocks of probes on one table (config 5's 256
-probes: shared bucket search, per-warp bucket buffers, remapped gm tables)
-and the five tables of config 3's star in one launch."""
+on a 300,001-row table in several launch shapes (tile rows, stages, 8, 11,
+15 or 16 consumer warps), several blocks of probes on one table: 2 blocks
+(block form: shared bucket search, per-warp bucket buffers, remapped gm
+tables) and 3 to 5 blocks (quad form: per-row bucket records, a quarter-warp
+per row, quads of 3 blocks and of 1 block), a 10-column table that keeps the
+block form, and the five tables of config 3's star in one launch."""
 import os
 
 import numpy as np
@@ -83,9 +85,11 @@ def test_config2_shapes(medium, shape):
     assert _run(ctx, preds, [T] * len(preds)) == [oracle.count(ot, tr, threads=THREADS) for tr in trees]
 
 
-@pytest.mark.parametrize("variant", [(8, 1), (16, 1), (8, 2), (16, 2), (15, 1), (11, 2)])
+@pytest.mark.parametrize("variant", [(8, 1), (16, 1), (8, 2), (16, 2), (15, 1), (11, 2), (11, 1)])
 def test_several_blocks_on_one_table(dev, variant):
-    """256 probes (4 blocks of 64) and 300 random estimator-workload probes (5 blocks)."""
+    """256 probes (4 blocks of 64: one quad), 129 (a quad of 3 blocks, the
+    last with 1 probe), 128 (2 blocks: the block form) and 300 random
+    estimator-workload probes (5 blocks: 2 quads, the second of 1 block)."""
     t = dg.config5_table(n=1_000_003, device=dev)
     ot = oracle.OTable.from_table(t)
     T = sel.Table(t.columns)
@@ -93,13 +97,26 @@ def test_several_blocks_on_one_table(dev, variant):
     ctx.set_scan_variant(*variant)
     trees = dg.config5_predicates(256, seed=4)
     preds = [sel.Predicate(T, tr) for tr in trees]
-    assert _run(ctx, preds, [T] * len(preds)) == [oracle.count(ot, tr, threads=THREADS) for tr in trees]
+    want = [oracle.count(ot, tr, threads=THREADS) for tr in trees]
+    assert _run(ctx, preds, [T] * len(preds)) == want
+    assert _run(ctx, preds[:129], [T] * 129) == want[:129]
+    assert _run(ctx, preds[:128], [T] * 128) == want[:128]
     t2 = dg.gen_table("cfg2", dg.config2_specs(), 200_000, dev)
     ot2, T2 = oracle.OTable.from_table(t2), sel.Table(t2.columns)
     rng = np.random.default_rng(11)
     trees = [dg.random_dnf_predicate(dg.config2_specs(), rng) for _ in range(300)]
     preds = [sel.Predicate(T2, tr) for tr in trees]
     assert _run(ctx, preds, [T2] * len(preds)) == [oracle.count(ot2, tr, threads=THREADS) for tr in trees]
+
+
+def test_ten_columns_keep_the_block_form(dev):
+    specs = [dg.ColumnSpec(f"c{i}", "i32", "uniform", 0, 50) for i in range(10)]
+    t = dg.gen_table("wide10", specs, 200_003, dev)
+    ot, T = oracle.OTable.from_table(t), sel.Table(t.columns)
+    rng = np.random.default_rng(12)
+    trees = [dg.random_dnf_predicate(specs, rng) for _ in range(256)]
+    preds = [sel.Predicate(T, tr) for tr in trees]
+    assert _run(_bucket_ctx(), preds, [T] * len(preds)) == [oracle.count(ot, tr, threads=THREADS) for tr in trees]
 
 
 def test_star_schema_one_launch(dev):
