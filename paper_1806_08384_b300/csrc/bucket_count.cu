@@ -409,19 +409,37 @@ __device__ __forceinline__ void eval_quad(const uint8_t* blob, const BkQuad& Q, 
     }
     // quarter qq adds word w = qq of the lane's 4: fields f = 0..7 of block
     // p's word 4h + qq, i.e. program 8 (4h + qq) + f
-    const uint32_t* outs = reinterpret_cast<const uint32_t*>(blob + Q.out_off) + 64u * p + 8u * (4u * h + qq);
+    uint32_t cf[8];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        if ((uint32_t)w != qq) continue;
+    for (int f = 0; f < 8; ++f) {
+        cf[f] = 0u;
 #pragma unroll
-        for (int f = 0; f < 8; ++f) {
+        for (int w = 0; w < 4; ++w) {
             // C[2w + (f & 1)] byte f / 2: byte 0 or 2 -> H[2j] low/high half, byte 1 or 3 -> H[2j + 1]
             const int j = 2 * w + (f & 1), byte = f >> 1;
             const uint32_t hv = H[2 * j + (byte & 1)];
-            const uint32_t c = (byte >> 1) ? (hv >> 16) : (hv & 0xFFFFu);
-            const uint32_t o = outs[f];
-            if (c && o != kBkNoOut) atomicAdd(&cnt[o], c);
+            if ((uint32_t)w == qq) cf[f] = (byte >> 1) ? (hv >> 16) : (hv & 0xFFFFu);
         }
+    }
+    // lane (p, h) of a quarter takes its fields in the order rot, rot + 1, ...
+    // (rot = 2p + h): the 32 lanes of one add then hit 32 different banks
+    // (program 8 (4h + qq) + f of block p sits in bank 8 qq + f when the
+    // probes' counters are in order); cf is rotated by rot in 3 select steps
+    const uint32_t rot = 2u * p + h;
+#pragma unroll
+    for (int st = 1; st < 8; st <<= 1) {
+        const bool take = (rot & (uint32_t)st) != 0u;
+        uint32_t nx[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) nx[f] = take ? cf[(f + st) & 7] : cf[f];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) cf[f] = nx[f];
+    }
+    const uint32_t* outs = reinterpret_cast<const uint32_t*>(blob + Q.out_off) + 64u * p + 8u * (4u * h + qq);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t o = outs[(i + rot) & 7u];
+        if (cf[i] && o != kBkNoOut) atomicAdd(&cnt[o], cf[i]);
     }
 }
 
