@@ -788,6 +788,24 @@ def issue_roofline(kernel: str, n_rows: int, launch_ms: float, sm_mhz: float):
             "peak_source": f"148 SMs x 4 schedulers x 1 warp instruction/cycle x {sm_mhz:.0f} MHz"}
 
 
+def smem_roofline(kernel: str, n_rows: int, launch_ms: float, sm_mhz: float):
+    """A kernel bound by its shared-memory accesses (the column-bucket batch
+    kernel's gathers): achieved = the shared-memory wavefronts per row that ncu
+    measured on a smaller case of the same kernel and probe set
+    (profiles/traffic.json) times this launch's rows, over the launch time;
+    peak = 148 SMs x 1 wavefront (128 bytes) per cycle x the SM clock.  None
+    when the kernel source changed since the capture."""
+    e = _traffic_entry(kernel)
+    if not e or "smem_wavefronts_per_row" not in e or launch_ms <= 0:
+        return None
+    achieved = e["smem_wavefronts_per_row"] * n_rows / (launch_ms / 1e3) / 1e9
+    peak = 148 * sm_mhz / 1e3
+    return {"bound": "smem", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G shared-memory wavefronts/s", "frac": round(achieved / peak, 4), "kernel": kernel,
+            "smem_wavefronts_per_row": e["smem_wavefronts_per_row"],
+            "peak_source": f"148 SMs x 1 wavefront/cycle x {sm_mhz:.0f} MHz"}
+
+
 # ----------------------------------------------------------------------------
 
 def main():
@@ -915,6 +933,7 @@ def main():
         "roofline": roof(dominant),
         "roofline_other": roof(other),
         "roofline_issue": issue_roofline(count_kernel, w.n, count_ms, float((clk or {}).get("sm_max_mhz") or 2032.0)),
+        "roofline_smem": smem_roofline(count_kernel, w.n, count_ms, float((clk or {}).get("sm_max_mhz") or 2032.0)),
         "gpu_launches": int(launches),
         "clocks": clk,
         "batch_plan_create_s": round(step.plan_s, 2),

@@ -1,6 +1,7 @@
 """Host-side helpers of bench.py that need no GPU: the instruction-issue
 roofline of a count scan is the measured instructions per row scaled to the
-launch, over 148 SMs x 4 schedulers x the SM clock; the algorithmic bytes of a
+launch, over 148 SMs x 4 schedulers x the SM clock, the shared-memory roofline
+the measured wavefronts per row over 148 SMs x 1 wavefront a cycle; the algorithmic bytes of a
 step count each predicate column of the batched scan once and each push-down's
 reads and writes."""
 import json
@@ -29,6 +30,23 @@ def test_issue_roofline_scales_the_measured_instructions():
 
 def test_issue_roofline_needs_a_capture():
     assert bench.issue_roofline("bucket_count_kernel", 1000, 0.0, 2032.0) is None
+
+
+def test_smem_roofline_scales_the_measured_wavefronts():
+    """The shared-memory roofline: measured wavefronts per row scaled to the
+    launch, over 148 SMs x 1 wavefront a cycle x the SM clock."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        e = json.load(f).get("bucket_count_kernel")
+    r = bench.smem_roofline("bucket_count_kernel", 1_200_000_000, 50.0, 2000.0)
+    if not e or "smem_wavefronts_per_row" not in e or e.get("source_hash") != bench.kernel_source_hash(
+            "bucket_count_kernel"):
+        assert r is None
+        return
+    want = e["smem_wavefronts_per_row"] * 1_200_000_000 / 50e-3 / 1e9
+    assert r["bound"] == "smem" and r["peak"] == 148 * 2.0
+    assert abs(r["achieved"] - want) <= 0.05 + 1e-9 * want
+    assert abs(r["frac"] - want / (148 * 2.0)) < 1e-4
+    assert bench.smem_roofline("bucket_count_kernel", 1000, 0.0, 2032.0) is None
 
 
 def test_algorithmic_bytes_of_a_step():
