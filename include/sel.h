@@ -198,7 +198,8 @@ sel_status sel_pushdown_async(sel_ctx* ctx, const sel_pred* pred, const sel_tabl
  * stream reaches the end of the call means a look-back wait timed out and
  * the count and rows are invalid).  Enqueue only: nothing waits for the GPU.
  * The first call on each device looks up the array's device address, so make
- * that first call before any stream capture.  All calls share the one array:
+ * that first call before any stream capture; later calls can be captured in
+ * a CUDA graph (the graph holds the program).  All calls share the one array:
  * each call clears the parts that must start at zero, and calls that overlap
  * on the GPU (different streams, or different host threads on one device)
  * race on it -- order them on one stream. */

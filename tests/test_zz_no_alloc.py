@@ -80,3 +80,51 @@ def test_noalloc_rejects_tables_beyond_its_fixed_scratch(dev):
         sel.pushdown_noalloc(p, big, [0], 10, [col], None, cnt, err)
     assert e.value.status == sel.SEL_ERR_UNSUPPORTED
     assert "tiles" in str(e.value)
+
+
+def test_noalloc_call_captured_in_a_graph_replays_its_own_program(dev):
+    """The call can be captured in a CUDA graph once the first call on the
+    device is done: the program reaches the scratch array as kernel
+    parameters, so the graph holds it.  Between the capture and the replay
+    another call with another program rewrites the shared array; the replay
+    must still give the captured predicate's rows (against the oracle)."""
+    t = dg.gen_table("cfg2", dg.config2_specs(), 300_001, dev)
+    ot = oracle.OTable.from_table(t)
+    T = sel.Table(t.columns)
+    proj = [t.index(c) for c in ("k0", "f0")]
+    tree_a, tree_b = dg.config2_predicate(1e-2, seed=41), dg.config2_predicate(0.1, seed=42)
+    pa, pb = sel.Predicate(T, tree_a), sel.Predicate(T, tree_b)
+    cap = T.n_rows
+
+    def bufs():
+        return ([torch.full((cap,), -1, dtype=t.columns[c].data.dtype, device=dev) for c in proj],
+                torch.full((cap,), -1, dtype=torch.int64, device=dev),
+                torch.zeros(1, dtype=torch.int64, device=dev), torch.zeros(1, dtype=torch.int32, device=dev))
+
+    outs_a, rid_a, cnt_a, err_a = bufs()
+    outs_b, rid_b, cnt_b, err_b = bufs()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):          # the first call on the device, outside the capture
+        sel.pushdown_noalloc(pa, T, proj, cap, outs_a, rid_a, cnt_a, err_a, stream=s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        sel.pushdown_noalloc(pa, T, proj, cap, outs_a, rid_a, cnt_a, err_a, stream=s)
+    for o in outs_a:
+        o.fill_(-1)
+    rid_a.fill_(-1)
+    cnt_a.zero_()
+    sel.pushdown_noalloc(pb, T, proj, cap, outs_b, rid_b, cnt_b, err_b)   # rewrites the shared array
+    torch.cuda.synchronize()
+    g.replay()
+    torch.cuda.synchronize()
+    want = oracle.select(ot, tree_a, threads=8)
+    n = int(cnt_a.item())
+    assert int(err_a.item()) == 0 and n == len(want)
+    assert np.array_equal(rid_a[:n].cpu().numpy(), want) and bool((rid_a[n:] == -1).all())
+    for o, c in zip(outs_a, proj):
+        assert o[:n].cpu().numpy().tobytes() == ot.arrays[c][want].tobytes()
+    want_b = oracle.select(ot, tree_b, threads=8)
+    assert int(err_b.item()) == 0 and int(cnt_b.item()) == len(want_b)
+    assert np.array_equal(rid_b[:len(want_b)].cpu().numpy(), want_b)
