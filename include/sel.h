@@ -277,9 +277,10 @@ sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stage
  * other pair: SEL_ERR_INVALID_ARG.
  * The same pair selects the persistent push-down kernel's consumer warps and
  * chunks per pass where that kernel has the variant (8, 12 or 16 warps, 1 or
- * 2 chunks; default 12 x 2; with 8 x 4 the push-down keeps its default).
+ * 2 chunks, and 12 x 3; default 12 x 3, or 12 x 2 for a requested tile that is
+ * not a multiple of 768 rows; with 8 x 4 the push-down keeps its default).
  * The batch plans' column-bucket kernel also takes 11 or 15 consumer warps
- * (1 or 2 chunks per pass), and the push-down 12 warps; with pairs a kernel
+ * (1 or 2 chunks per pass), and the push-down 12 warps (1, 2 or 3 chunks); with pairs a kernel
  * does not have, sel_count, sel_pushdown and the batch plans keep their
  * defaults.  Results do not depend on the variant. */
 sel_status sel_ctx_set_scan_variant(sel_ctx* ctx, int32_t consumer_warps, int32_t chunks_per_pass);

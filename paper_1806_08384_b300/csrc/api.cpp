@@ -524,7 +524,7 @@ extern "C" sel_status sel_ctx_set_scan_variant(sel_ctx* c, int32_t consumer_warp
                 bucket_variant_ok(consumer_warps, chunks_per_pass) ||
                 pushdown_persistent_ok(consumer_warps, chunks_per_pass))) {
         set_error("sel_ctx_set_scan_variant: bad arguments (0,0; warps 8|16 with chunks 1|2; warps 8 with chunks 4; "
-                  "bucket kernel only: warps 11|15 with chunks 1|2; push-down only: warps 12 with chunks 1|2)");
+                  "bucket kernel only: warps 11|15 with chunks 1|2; push-down only: warps 12 with chunks 1|2|3)");
         return SEL_ERR_INVALID_ARG;
     }
     c->shape.warps = consumer_warps;
@@ -686,10 +686,12 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     // table (its last super-tile is looked back and written after the scan),
     // at least 32768 and at most 131072 rows; larger super-tiles take shared
     // memory (their row masks) from the stages.
-    // Variant: the context's scan variant, else 12 consumer warps x 2 chunks
+    // Variant: the context's scan variant, else 12 consumer warps x 3 chunks
     // per pass (with the producer, look-back and 2 writer warps, 16 warps of
     // 128 registers: no spills in the evaluation loop; measured faster on
-    // config 5's push-downs than 16 consumer warps of 96 registers).  Sub-tile and stages: the requested ones, else the count
+    // config 5's push-downs than 16 consumer warps of 96 registers, and 3
+    // chunks a pass than 2), or 2 chunks when a requested sub-tile is a
+    // multiple of 512 rows but not of 768.  Sub-tile and stages: the requested ones, else the count
     // scan's rule: 3 stages (2 if 3 do not fit) of the largest sub-tile, in
     // whole chunk groups, that fits in shared memory beside the row masks.  A
     // tile size the persistent kernel cannot use, or predicate columns too wide
@@ -699,7 +701,7 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
         const int req = ctx->shape.tile_rows;
         const bool own = ctx->shape.warps > 0 && pushdown_persistent_ok(ctx->shape.warps, ctx->shape.group);
         const int W = own ? ctx->shape.warps : 12;
-        const int G = own ? ctx->shape.group : 2;
+        const int G = own ? ctx->shape.group : (req > 0 && req % (3 * kChunkRows) != 0 ? 2 : 3);
         const int unit = kChunkRows * G;
         uint32_t target = ctx->pd_super_rows;
         if (target == 0) {

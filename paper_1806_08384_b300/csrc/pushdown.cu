@@ -845,7 +845,8 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
 static inline uint32_t align_up_u32(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 bool pushdown_persistent_ok(int warps, int chunks_per_pass) {
-    return (warps == 8 || warps == 12 || warps == 16) && (chunks_per_pass == 1 || chunks_per_pass == 2);
+    return ((warps == 8 || warps == 12 || warps == 16) && (chunks_per_pass == 1 || chunks_per_pass == 2)) ||
+           (warps == 12 && chunks_per_pass == 3);
 }
 
 bool pushdown_persistent_tile_ok(uint32_t tile_rows, int chunks_per_pass) {
@@ -883,6 +884,7 @@ cudaError_t pushdown_persistent_max_smem(int optin, int* dyn_max) {
     if (e == cudaSuccess) e = pdp_set_smem<8, 2>(optin, dyn_max);
     if (e == cudaSuccess) e = pdp_set_smem<12, 1>(optin, dyn_max);
     if (e == cudaSuccess) e = pdp_set_smem<12, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = pdp_set_smem<12, 3>(optin, dyn_max);
     if (e == cudaSuccess) e = pdp_set_smem<16, 1>(optin, dyn_max);
     if (e == cudaSuccess) e = pdp_set_smem<16, 2>(optin, dyn_max);
     return e;
@@ -902,6 +904,8 @@ cudaError_t launch_pushdown_persistent(const PushdownArgs& a, int grid, int warp
         pushdown_persistent_kernel<12, 1><<<grid, (12 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 12 && chunks_per_warp == 2)
         pushdown_persistent_kernel<12, 2><<<grid, (12 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
+    else if (warps == 12 && chunks_per_warp == 3)
+        pushdown_persistent_kernel<12, 3><<<grid, (12 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 16 && chunks_per_warp == 1)
         pushdown_persistent_kernel<16, 1><<<grid, (16 + kPdWriters + 2) * 32, a.smem_bytes, st>>>(a);
     else if (warps == 16 && chunks_per_warp == 2)

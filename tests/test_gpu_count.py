@@ -109,7 +109,7 @@ def test_bucket_only_variant_keeps_the_count_default(ctx, medium):
     tree = dg.config2_predicate(1e-2, seed=5)
     want = oracle.count(ot, tree)
     try:
-        for w, g in [(15, 1), (11, 2), (12, 2)]:
+        for w, g in [(15, 1), (11, 2), (12, 2), (12, 3)]:
             ctx.set_scan_variant(w, g)
             P = sel.Predicate(T, tree)
             assert ctx.count(P, T) == want

@@ -54,10 +54,11 @@ def proj_cfg2(t):
     return [t.index(c) for c in dg.CONFIG2_PROJECTION]
 
 
-# 1536, 2560 and 3584 rows are sub-tiles of the persistent kernel whose
-# super-tiles (32256, 30720, 32256 rows) are not powers of two; 256 and 1280
-# are not whole 2-chunk groups and run on the one-CTA-per-tile kernel.
-@pytest.mark.parametrize("tile_rows", [0, 256, 1024, 1280, 1536, 2048, 2560, 3584, 4096, 8192])
+# The persistent kernel takes 3-chunk groups by default (768 rows: 1536 and
+# the default tile), 2-chunk groups for requested tiles that are multiples of
+# 512 rows only (1024, 2048, 2560, 3584, 4096, 8192); 256 and 1280 are neither
+# and run on the one-CTA-per-tile kernel.
+@pytest.mark.parametrize("tile_rows", [0, 256, 768, 1024, 1280, 1536, 2048, 2304, 2560, 3584, 4096, 8192])
 def test_config2_selectivities(ctx, medium, tile_rows):
     t, ot, T = medium
     ctx.set_scan_shape(tile_rows, 0, 0)
@@ -65,7 +66,7 @@ def test_config2_selectivities(ctx, medium, tile_rows):
         check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=11), proj_cfg2(t))
 
 
-@pytest.mark.parametrize("variant", [(12, 2), (12, 1), (16, 2), (16, 1), (8, 2), (8, 1)])
+@pytest.mark.parametrize("variant", [(12, 3), (12, 2), (12, 1), (16, 2), (16, 1), (8, 2), (8, 1)])
 def test_persistent_variants(ctx, dev, medium, variant):
     """Every persistent push-down variant (consumer warps x chunks per warp), on
     the 1,000,003-row table (ragged last super-tile and sub-tile) and on sizes at
@@ -74,7 +75,7 @@ def test_persistent_variants(ctx, dev, medium, variant):
     ctx.set_scan_variant(*variant)
     for s in (1e-3, 0.1):
         check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=21), proj_cfg2(t))
-    if variant[1] == 1:   # 3-chunk sub-tiles: 42 of them make a 32256-row super-tile
+    if variant[1] in (1, 3):   # 3-chunk sub-tiles: 42 of them make a 32256-row super-tile
         ctx.set_scan_shape(768, 0, 0)
         check_pushdown(ctx, T, ot, dg.config2_predicate(0.1, seed=22), proj_cfg2(t))
         ctx.set_scan_shape(0, 0, 0)
