@@ -508,6 +508,51 @@ def distinct_and_join(sel, ctx, T, table, pred, reps=3):
     return out
 
 
+def config5_gated(step: "OurStep", n_train=100_000, n_val=10_000, reps=3):
+    """Config 5's gated mode: an estimator trained on config 5's own table
+    (random OR-of-AND probes labelled by the batched count, 256 a launch), tau
+    chosen on a validation split, then the step's 256 probes answered through
+    the library's gated call (sel_mlp_estimate: features, forward, the gate,
+    and one batched exact count of every probe the network does not answer).
+    The fallbacks' counts are checked against the step's exact counts."""
+    sel, w, T = step.sel, step.w, step.T
+    ctx = sel.Context()
+    rng = np.random.default_rng(dg.mix_seed("bench_cfg5_estimator"))
+    specs = dg.config5_specs()
+    trees = [dg.random_dnf_predicate(specs, rng) for _ in range(n_train + n_val)]
+    preds = [sel.Predicate(T, t) for t in trees]
+    t0 = time.perf_counter()
+    counts = np.array(sel.count_many(ctx, preds, T, chunk=256), dtype=np.uint64)
+    label_s = time.perf_counter() - t0
+    wl = [sel.Predicate(T, t) for t in w.trees]
+    exact = np.array(step.counts_dev.tolist(), dtype=np.uint64)
+    model, tau, _, quality, okt = train_and_gate(sel, ctx, T, preds + wl, np.concatenate([counts, exact]),
+                                                 n_train, n_val, len(wl))
+    model.estimate(wl, T, tau)          # the first call builds and caches the fallback's batch plan
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        est, sig, used = model.estimate(wl, T, tau)
+    gated_ms = (time.perf_counter() - t0) * 1e3 / reps
+    assert all(int(e) == int(c) for e, c, u in zip(est, exact, used) if u), "an exact fallback differs"
+    q = q_error(est, exact)
+    acc = ~used
+    return {
+        "workload": "config 5's 256 probes on the 1.2B-row table; estimator trained on %d random OR-of-AND "
+                    "probes of the same table (labelled by the batched count), tau on %d more" % (n_train, n_val),
+        "labels": len(preds), "label_seconds": round(label_s, 1), "ms_per_label": round(label_s * 1e3 / len(preds), 4),
+        "tau": quality["tau"], "train_seconds": quality["train_seconds"],
+        "featurizable_fraction": round(float(okt.mean()), 3),
+        "answered_by_network": int(acc.sum()), "exact_fallbacks": int(used.sum()),
+        "gated_ms": round(gated_ms, 3), "gated_ms_per_estimate": round(gated_ms / len(wl), 4),
+        "exact_batched_ms_per_estimate": round(statistics.mean(a.elapsed_time(b) for k, a, b in step.events
+                                                               if k == "count") / len(wl), 4),
+        "q_error_p50": round(float(np.median(q)), 3), "q_error_p95": round(float(np.percentile(q, 95)), 3),
+        "accepted_q_error_p95": round(float(np.percentile(q[acc], 95)), 3) if acc.any() else None,
+        "network_q_error_p50_featurizable": quality["q_error_p50"],
+        "network_q_error_p95_featurizable": quality["q_error_p95"]}
+
+
 def config5_extras(step: "OurStep", peak: float, reps=3):
     """On the headline table: three single-probe counts and the push-down of
     the s = 0.9 probe (about 1.08B rows written; its own maxSize = n)."""
@@ -942,6 +987,7 @@ def main():
         out["surrogate"] = sur.summary()
     if rank == 0 and not args.no_extras:
         out["config5_extras"] = config5_extras(step, peak)
+        out["config5_gated"] = config5_gated(step)
         out["config2"] = config2_measurements(sel, cfg2_table, peak)
         out["star_batch"] = star_batch(sel, peak, dev)
         out["config1_latency"] = config1_latency(sel, dev)
