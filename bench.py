@@ -522,7 +522,7 @@ def config5_gated(step: "OurStep", n_train=100_000, n_val=10_000, reps=3):
     trees = [dg.random_dnf_predicate(specs, rng) for _ in range(n_train + n_val)]
     preds = [sel.Predicate(T, t) for t in trees]
     t0 = time.perf_counter()
-    counts = np.array(sel.count_many(ctx, preds, T, chunk=256), dtype=np.uint64)
+    counts = np.array(sel.count_many(ctx, preds, T), dtype=np.uint64)
     label_s = time.perf_counter() - t0
     wl = [sel.Predicate(T, t) for t in w.trees]
     exact = np.array(step.counts_dev.tolist(), dtype=np.uint64)
