@@ -233,7 +233,10 @@ sel_status sel_ctx_synchronize(sel_ctx* ctx);
 /* The plan behind sel_count_batch, for callers that run the same probe set
  * many times.  The predicates and table descriptors must outlive the plan.
  * autotune: 1 = time the candidate launch shapes now and keep the fastest,
- * 0 = use the default shape. */
+ * 0 = use the default shape.  A plan with more than 256 probes on one table
+ * runs as parts of at most 256 probes a table, one launch each (all in its
+ * graph), which add into the same counts; sel_batch_plan_kernel, _info and
+ * _variant then report the first part. */
 sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
                                  int32_t n, int32_t autotune, sel_batch_plan** out);
 /* Runs the plan: counts to dev_out_counts (device, n u64, enqueue only) when

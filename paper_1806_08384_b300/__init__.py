@@ -644,10 +644,10 @@ def flatten(params: dict) -> np.ndarray:
 
 
 def count_many(ctx: "Context", preds: Sequence[Predicate], table, chunk: int = 256) -> List[int]:
-    """Exact counts of many predicates over one table, in batched launches of
-    `chunk` probes (256: one quad of the bucket kernel; measured on config 2's
-    300M rows, 0.090 ms per label against 0.145 with 128 and 0.58 with 512,
-    whose larger tables leave smaller pipeline stages)."""
+    """Exact counts of many predicates over one table, in batch plans of
+    `chunk` probes (256: one quad of the bucket kernel, 0.083 ms per label on
+    config 2's 300M rows against 0.145 with 128; a plan of more probes runs
+    as parts of 256 anyway)."""
     T = Table.of(table)
     out = []
     for i in range(0, len(preds), chunk):

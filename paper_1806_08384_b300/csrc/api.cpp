@@ -141,7 +141,11 @@ struct sel_batch_plan {
     uint32_t bk_blob_bytes = 0, bk_gb_slots = 0, bk_gb_quad = 0, bk_n_out = 0;
     // graphs that write the counts to a caller's device buffer, by buffer
     std::vector<std::pair<void*, cudaGraphExec_t>> out_graphs;
+    // a plan with more than kPlanPartProbes probes on one table runs as parts of
+    // at most that many per table, one launch each, into the same counts
+    std::vector<sel_batch_plan*> parts;
     ~sel_batch_plan() {
+        for (sel_batch_plan* q : parts) delete q;
         if (graph) cudaGraphExecDestroy(graph);
         for (auto& kv : out_graphs) cudaGraphExecDestroy(kv.second);
         if (d_bk_blob) cudaFree(d_bk_blob);
@@ -1086,7 +1090,15 @@ static sel_status plan_capture(sel_batch_plan* p, void* counts, cudaGraphExec_t*
     int nl = 0;
     if (s == SEL_OK) {
         cudaMemsetAsync(counts, 0, (size_t)p->n * 8, cs);
-        s = plan_launch(p, p->kernel, p->shape, &nl, counts);
+        if (p->parts.empty()) {
+            s = plan_launch(p, p->kernel, p->shape, &nl, counts);
+        } else {
+            for (sel_batch_plan* q : p->parts) {   // every part adds its probes' counts to the same buffer
+                int nq = 0;
+                if (s == SEL_OK) s = plan_launch(q, q->kernel, q->shape, &nq, counts);
+                nl += nq;
+            }
+        }
         e = cudaStreamEndCapture(cs, &g);
         if (s == SEL_OK && e != cudaSuccess) s = cuda_fail("cudaStreamEndCapture", e);
     }
@@ -1104,19 +1116,20 @@ static sel_status plan_capture(sel_batch_plan* p, void* counts, cudaGraphExec_t*
 
 }  // namespace sel
 
-extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const* preds,
-                                            const sel_table* const* tables, int32_t n, int32_t autotune,
-                                            sel_batch_plan** out) {
+namespace sel {
+
+// Probes of one table a plan launch takes: one quad of the bucket kernel.
+// Larger groups leave too little shared memory for the stages (measured on
+// config 2: 512 probes in one launch counted 6x slower per probe than 256).
+constexpr int kPlanPartProbes = 256;
+
+// A plan of preds[0..n) over tables[0..n) whose counts go to outs[i] (null:
+// i) of a counts buffer of n_total entries.
+static sel_status plan_create(sel_ctx* ctx, const sel_pred* const* preds, const sel_table* const* tables,
+                              int32_t n, int32_t autotune, const int32_t* omap, int32_t n_total,
+                              sel_batch_plan** out) {
     const char* who = "sel_batch_plan_create";
-    if (!ctx || !out || n <= 0 || !preds || !tables) {
-        set_error("%s: bad arguments", who);
-        return SEL_ERR_INVALID_ARG;
-    }
     *out = nullptr;
-    for (int32_t i = 0; i < n; ++i) {
-        sel_status s = check_pred_on_table(preds[i], tables[i], who);
-        if (s != SEL_OK) return s;
-    }
     // group predicates by table (same data pointers and row count)
     std::vector<std::string> keys;
     std::map<std::string, int> gid;
@@ -1133,7 +1146,7 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     }
     std::unique_ptr<sel_batch_plan> p(new sel_batch_plan());
     p->ctx = ctx;
-    p->n = n;
+    p->n = n_total;
     std::vector<const Program*> progs;
     std::vector<std::vector<int32_t>> maps;
     std::vector<uint32_t> outs;
@@ -1157,12 +1170,13 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
             std::vector<int32_t> m;
             for (int32_t c : preds[i]->prog.slot_col)
                 m.push_back((int32_t)(std::lower_bound(cols.begin(), cols.end(), c) - cols.begin()));
+            const uint32_t o = omap ? (uint32_t)omap[i] : (uint32_t)i;
             progs.push_back(&preds[i]->prog);
             maps.push_back(m);
-            outs.push_back((uint32_t)i);
+            outs.push_back(o);
             bk_in[g].progs.push_back(&preds[i]->prog);
             bk_in[g].slot_maps.push_back(m);
-            bk_in[g].outs.push_back((uint32_t)i);
+            bk_in[g].outs.push_back(o);
         }
         ta.prog_end = (uint32_t)progs.size();
         for (uint32_t j = 0; j < ta.n_slots; ++j) bk_in[g].slot_width.push_back(ta.width[j]);
@@ -1174,7 +1188,7 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
     p->blob_bytes = (uint32_t)blob.size();
     SEL_CUDA("cudaMalloc", dev_alloc(&p->d_blob, blob.size()));
     SEL_CUDA("cudaMemcpy", cudaMemcpy(p->d_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice));
-    SEL_CUDA("cudaMalloc", dev_alloc(&p->d_counts, (size_t)n * 8));
+    SEL_CUDA("cudaMalloc", dev_alloc(&p->d_counts, (size_t)n_total * 8));
     uint32_t max_rb = 0;
     for (auto& t : p->tables) max_rb = std::max(max_rb, t.row_bytes);
     // the column-bucket form, when the probes fit it (bucket.h)
@@ -1308,6 +1322,61 @@ extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const*
         if (rs != SEL_OK) return rs;
     }
     p->ms = best_ms;
+    sel_status s = plan_capture(p.get(), p->d_counts, &p->graph);
+    if (s != SEL_OK) return s;
+    *out = p.release();
+    return SEL_OK;
+}
+
+}  // namespace sel
+
+extern "C" sel_status sel_batch_plan_create(sel_ctx* ctx, const sel_pred* const* preds,
+                                            const sel_table* const* tables, int32_t n, int32_t autotune,
+                                            sel_batch_plan** out) {
+    const char* who = "sel_batch_plan_create";
+    if (!ctx || !out || n <= 0 || !preds || !tables) {
+        set_error("%s: bad arguments", who);
+        return SEL_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    for (int32_t i = 0; i < n; ++i) {
+        sel_status s = check_pred_on_table(preds[i], tables[i], who);
+        if (s != SEL_OK) return s;
+    }
+    // probes of each table, in order; part j takes the j-th kPlanPartProbes of every table
+    std::map<std::string, std::vector<int32_t>> by_table;
+    size_t most = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        std::vector<int32_t>& v = by_table[table_key(tables[i])];
+        v.push_back(i);
+        most = std::max(most, v.size());
+    }
+    if (most <= (size_t)kPlanPartProbes) return plan_create(ctx, preds, tables, n, autotune, nullptr, n, out);
+    std::unique_ptr<sel_batch_plan> p(new sel_batch_plan());
+    p->ctx = ctx;
+    p->n = n;
+    const size_t n_parts = (most + kPlanPartProbes - 1) / kPlanPartProbes;
+    for (size_t j = 0; j < n_parts; ++j) {
+        std::vector<int32_t> idx;
+        for (auto& kv : by_table)
+            for (size_t k = j * kPlanPartProbes; k < std::min(kv.second.size(), (j + 1) * kPlanPartProbes); ++k)
+                idx.push_back(kv.second[k]);
+        std::sort(idx.begin(), idx.end());
+        std::vector<const sel_pred*> pp;
+        std::vector<const sel_table*> tt;
+        for (int32_t i : idx) {
+            pp.push_back(preds[i]);
+            tt.push_back(tables[i]);
+        }
+        sel_batch_plan* q = nullptr;
+        sel_status s = plan_create(ctx, pp.data(), tt.data(), (int32_t)idx.size(), autotune, idx.data(), n, &q);
+        if (s != SEL_OK) return s;
+        p->parts.push_back(q);
+        p->ms += q->ms;
+    }
+    p->kernel = p->parts[0]->kernel;   // reported by sel_batch_plan_kernel / _info / _variant
+    p->shape = p->parts[0]->shape;
+    SEL_CUDA("cudaMalloc", dev_alloc(&p->d_counts, (size_t)n * 8));
     sel_status s = plan_capture(p.get(), p->d_counts, &p->graph);
     if (s != SEL_OK) return s;
     *out = p.release();

@@ -77,3 +77,38 @@ def test_256_probes_one_table(ctx, dev):
     got = sel.BatchPlan(ctx, preds, [T] * len(preds), autotune=True).run()
     want = [oracle.count(ot, tr, threads=THREADS) for tr in trees]
     assert got == want
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_plans_above_256_probes_a_table_run_as_parts(ctx, dev, autotune):
+    """600 probes on one table and 40 on another: the plan runs as three
+    parts of at most 256 probes a table (the second table's probes all in the
+    first part), every part adding into the same counts; interleaved order,
+    host and device outputs, graph replay."""
+    t1 = dg.gen_table("cfg2", dg.config2_specs(), 200_003, dev)
+    t2 = dg.tiny_table(50_001, seed=5, device=dev)
+    o1, o2 = oracle.OTable.from_table(t1), oracle.OTable.from_table(t2)
+    T1, T2 = sel.Table(t1.columns), sel.Table(t2.columns)
+    rng = np.random.default_rng(31)
+    trees1 = [dg.random_dnf_predicate(dg.config2_specs(), rng) for _ in range(600)]
+    trees2 = [dg.random_tree(t2, rng, depth=3) for _ in range(40)]
+    preds, tables, want = [], [], []
+    it2 = iter(trees2)
+    for k, tr in enumerate(trees1):
+        preds.append(sel.Predicate(T1, tr))
+        tables.append(T1)
+        want.append(oracle.count(o1, tr, threads=THREADS))
+        if k % 15 == 0:
+            tr2 = next(it2, None)
+            if tr2 is not None:
+                preds.append(sel.Predicate(T2, tr2))
+                tables.append(T2)
+                want.append(oracle.count(o2, tr2))
+    plan = sel.BatchPlan(ctx, preds, tables, autotune=autotune)
+    assert plan.run() == want
+    assert plan.run() == want                                   # graph replay
+    out = torch.full((len(preds),), -1, dtype=torch.int64, device=dev)
+    plan.run(device_out=out)
+    torch.cuda.synchronize()
+    assert out.cpu().tolist() == want
+    assert ctx.count_batch(preds, tables) == want              # the cached-plan entry point
