@@ -1043,7 +1043,8 @@ def kernel_case(sel, dev, args):
     targets = np.logspace(-6, np.log10(0.9), len(trees))
     i = int(np.argmin(np.abs(np.log(targets) - np.log(args.case_s))))
     proj = [t.index(c) for c in dg.CONFIG5_PROJECTION]
-    mr = int(math.floor(args.rows * MAX_SELECTIVITY))
+    # the step's maxSize, or every row for a case above it (the write-heavy path)
+    mr = int(math.floor(args.rows * MAX_SELECTIVITY)) if args.case_s <= MAX_SELECTIVITY else args.rows
     outs = [torch.empty(mr, dtype=t.columns[c].data.dtype, device=dev) for c in proj]
     ids = torch.empty(mr, dtype=torch.int64, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)

@@ -401,13 +401,22 @@ __device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t o) {
     return pos;
 }
 
-// Row of rank r among the selected rows of the super-tile in buffer b.
-__device__ __forceinline__ int64_t rank_row(const PdSmem& sm, uint32_t b, int64_t R0, uint32_t r) {
+// Row of rank r among the selected rows of the super-tile in buffer b.  lo:
+// on entry a chunk whose prefix is <= r (0 always is), on return r's chunk,
+// the last one whose prefix is <= r (cp[0] = 0).  The search gallops forward
+// from lo and then halves: the ranks of a write group are consecutive, so
+// starting from the previous rank's chunk takes a step or two where chunks
+// hold many selected rows, and O(log distance) otherwise.
+__device__ __forceinline__ int64_t rank_row(const PdSmem& sm, uint32_t b, int64_t R0, uint32_t r, uint32_t& lo) {
     const uint32_t nch = sm.nch[b];
     const uint32_t* cp = sm.cp + b * sm.ch;
     const uint32_t* mw = sm.mask + b * sm.ch * kMaskWords;
-    // the chunk: the last one whose prefix is <= r (cp[0] = 0)
-    uint32_t lo = 0, hi = nch;
+    uint32_t step = 1u;
+    while (lo + step < nch && cp[lo + step] <= r) {
+        lo += step;
+        step <<= 1;
+    }
+    uint32_t hi = lo + step < nch ? lo + step : nch;   // cp[hi] > r, or hi = nch
     while (hi - lo > 1u) {
         const uint32_t mid = (lo + hi) >> 1;
         if (cp[mid] <= r) lo = mid;
@@ -445,11 +454,12 @@ __device__ __forceinline__ void scatter_group(const PushdownArgs& a, const PdSme
     const uint32_t r0 = g * 32u * K;
     int64_t row[K];
     bool act[K];
+    uint32_t lo = 0;   // the chunk of the lane's previous rank (the ranks increase)
 #pragma unroll
     for (uint32_t k = 0; k < K; ++k) {
         const uint32_t r = r0 + 32u * k + lane;
         act[k] = r < n;
-        row[k] = act[k] ? rank_row(sm, b, R0, r) : 0;
+        row[k] = act[k] ? rank_row(sm, b, R0, r, lo) : 0;
     }
     for (uint32_t j0 = 0; j0 < a.n_proj; j0 += 4) {
         unsigned long long v[4][K];
@@ -736,6 +746,7 @@ __global__ void __launch_bounds__((W + kPdWriters + 2) * 32, 1)
                         ok = false;
                         break;
                     }
+                    __nanosleep(200);   // nothing to write yet: leave the issue slots to the warps that have
                 }
                 if (!ok) {
                     if (lane == 0) fail_flag(a, &s_fail);
