@@ -154,8 +154,9 @@ sel_status sel_count_async(sel_ctx* ctx, const sel_pred* pred, const sel_table* 
                            uint64_t* dev_out_count);
 
 /* a3 + a4 -- selection push-down (Algorithm 1, Execute with isSPD = true):
- * one fused pass computes the exact count and writes the rows of
- * sigma_P(R), projected on proj_cols[0 .. n_proj), in ascending row order
+ * computes the exact count and writes the rows of sigma_P(R) (in two passes
+ * or one fused pass: sel_ctx_set_pushdown_method),
+ * projected on proj_cols[0 .. n_proj), in ascending row order
  * into caller-allocated device buffers dev_out_cols[j] (capacity max_rows
  * elements of column proj_cols[j]'s type), plus their int64 row ids into
  * dev_out_rowids when it is not NULL.  *out_count (host) always receives the
@@ -169,8 +170,10 @@ sel_status sel_pushdown(sel_ctx* ctx, const sel_pred* pred, const sel_table* tab
 
 /* Same push-down, enqueued only: the exact count is written to dev_out_count
  * (device, 8 bytes) and nothing waits for it; the caller compares it with
- * max_rows (rows past max_rows are never written).  A timed-out look-back
- * wait is reported by sel_ctx_synchronize. */
+ * max_rows (rows past max_rows are never written).  A timed-out device wait
+ * (a look-back, or a stage of the scan) is reported by sel_ctx_synchronize.
+ * The two-pass method keeps its scratch in the context: calls on one
+ * context run in its stream's order. */
 sel_status sel_pushdown_async(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
                               const int32_t* proj_cols, int32_t n_proj, void* const* dev_out_cols,
                               int64_t* dev_out_rowids, uint64_t max_rows, uint64_t* dev_out_count);
@@ -300,7 +303,26 @@ uint64_t sel_ctx_launch_count(const sel_ctx* ctx);
  * not depend on it. */
 sel_status sel_ctx_set_pushdown_super_rows(sel_ctx* ctx, int32_t rows);
 
-/* Test hook for the bounded waits of the push-down look-back: look-back unit
+/* Push-down method of sel_pushdown / sel_pushdown_async; results do not
+ * depend on it.
+ *   SEL_PD_AUTO      (0, the default) the library's choice: two passes.
+ *   SEL_PD_TWO_PASS  (1) the count scan (sel_count's kernel and launch shape)
+ *                    also stores each 256-row chunk's row mask and count and
+ *                    each 16384-row segment's count (1/8 byte per row plus
+ *                    2 bytes per chunk of context scratch); a one-CTA kernel
+ *                    turns the segment counts into output offsets; a scatter
+ *                    kernel (one warp per segment) writes the selected rows.
+ *                    No device wait on another CTA.
+ *   SEL_PD_ONE_PASS  (2) count and compaction in one pass: the persistent
+ *                    kernel, output offsets by decoupled look-back over
+ *                    super-tiles (sel_ctx_set_pushdown_super_rows), or the
+ *                    one-CTA-per-tile kernel for tile sizes the persistent
+ *                    kernel does not take (sel_ctx_set_scan_shape).
+ * Any other value: SEL_ERR_INVALID_ARG. */
+enum { SEL_PD_AUTO = 0, SEL_PD_TWO_PASS = 1, SEL_PD_ONE_PASS = 2 };
+sel_status sel_ctx_set_pushdown_method(sel_ctx* ctx, int32_t method);
+
+/* Test hook for the bounded waits of the push-down look-back (SEL_PD_ONE_PASS): look-back unit
  * skip_tile (a super-tile of the persistent kernel -- see
  * sel_ctx_set_pushdown_super_rows --, a tile of the one-CTA-per-tile kernel;
  * -1: none) never publishes its prefix, and a waiting tile gives up after

@@ -32,6 +32,7 @@ TORCH_TYPES = {"i32": torch.int32, "i64": torch.int64, "f32": torch.float32, "da
                "dict": torch.int32}
 N_CMP, N_BETWEEN, N_IN, N_LIKE, N_AND, N_OR, N_NOT, N_TRUE, N_FALSE = range(1, 10)
 OPS = {"=": 0, "<>": 1, "<": 2, "<=": 3, ">": 4, ">=": 5}
+SEL_PD_AUTO, SEL_PD_TWO_PASS, SEL_PD_ONE_PASS = 0, 1, 2
 
 
 class sel_column(C.Structure):
@@ -116,6 +117,7 @@ def _load():
         "sel_ctx_launch_count": (C.c_uint64, [V]),
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
         "sel_ctx_set_pushdown_super_rows": (C.c_int, [V, C.c_int32]),
+        "sel_ctx_set_pushdown_method": (C.c_int, [V, C.c_int32]),
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
         "sel_count_distinct": (C.c_int, [V, P(sel_table), C.c_int32, V, P(C.c_uint64), P(C.c_uint64)]),
         "sel_join_size_estimate": (C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]),
@@ -356,6 +358,10 @@ class Context:
     def set_pushdown_super_rows(self, rows: int):
         """Super-tile target of the persistent push-down (0: from the table size)."""
         _check(lib.sel_ctx_set_pushdown_super_rows(self.h, rows), "sel_ctx_set_pushdown_super_rows")
+
+    def set_pushdown_method(self, method: int):
+        """SEL_PD_AUTO (two passes), SEL_PD_TWO_PASS or SEL_PD_ONE_PASS."""
+        _check(lib.sel_ctx_set_pushdown_method(self.h, int(method)), "sel_ctx_set_pushdown_method")
 
     def debug_pushdown_fault(self, skip_tile: int, wait_ns: int = 0):
         _check(lib.sel_ctx_debug_pushdown_fault(self.h, skip_tile, wait_ns), "sel_ctx_debug_pushdown_fault")

@@ -109,6 +109,7 @@ struct sel_ctx {
     DevBuf counts;            // sel_count / batch staging
     DevBuf err;               // 4 bytes: error flag of the last launches
     DevBuf pd_scratch;        // push-down: tile status | tile counter | total
+    DevBuf pd_mask;           // two-pass push-down: row masks | chunk counts | segment counts | group offsets
     DevBuf distinct_vals;     // sel_count_distinct: the selected values
     DevBuf distinct_table;    // sel_count_distinct: hash set | new-key counter | flags
     DevBuf join_vals;         // sel_join_count: the second side's selected keys
@@ -121,6 +122,7 @@ struct sel_ctx {
     long long debug_skip_tile = -1;
     unsigned long long debug_wait_ns = kWaitNs;
     uint32_t pd_super_rows = 0;   // push-down super-tile target (0: chosen from the table size)
+    int pd_method = SEL_PD_AUTO;  // push-down method
 };
 
 struct sel_batch_plan {
@@ -270,9 +272,13 @@ static sel_status resolve_shape(sel_ctx* ctx, uint32_t blob_bytes, uint32_t n_pr
 
 // Fills shape-dependent fields and launches (several launches when the
 // tables do not fit in one).
+// mask / seg_cnt / seg_nz: the two-pass push-down's first pass (one program
+// on one table: the row masks and segment counts of ScanArgs), else null.
 static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_bytes, uint32_t instr_off,
                            uint32_t pool_off, uint32_t n_progs, std::vector<TableArg> tables,
-                           unsigned long long* d_counts, const Shape& sh_in, int* n_launches) {
+                           unsigned long long* d_counts, const Shape& sh_in, int* n_launches,
+                           uint8_t* mask = nullptr, uint32_t* seg_cnt = nullptr,
+                           unsigned long long* seg_nz = nullptr) {
     int launches = 0;
     Shape sh;
     {
@@ -291,6 +297,9 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
         a.stages = (uint32_t)sh.stages;
         a.counts = d_counts;
         a.err = static_cast<unsigned int*>(ctx->err.p);
+        a.mask = mask;
+        a.seg_cnt = seg_cnt;
+        a.seg_nz = seg_nz;
         const size_t t1 = std::min(tables.size(), t0 + kMaxTables);
         a.n_tables = (uint32_t)(t1 - t0);
         uint32_t max_rb = 0;
@@ -570,6 +579,15 @@ extern "C" sel_status sel_ctx_set_pushdown_super_rows(sel_ctx* c, int32_t rows) 
     return SEL_OK;
 }
 
+extern "C" sel_status sel_ctx_set_pushdown_method(sel_ctx* c, int32_t method) {
+    if (!c || method < SEL_PD_AUTO || method > SEL_PD_ONE_PASS) {
+        set_error("sel_ctx_set_pushdown_method: method must be SEL_PD_AUTO, SEL_PD_TWO_PASS or SEL_PD_ONE_PASS");
+        return SEL_ERR_INVALID_ARG;
+    }
+    c->pd_method = method;
+    return SEL_OK;
+}
+
 extern "C" sel_status sel_ctx_debug_pushdown_fault(sel_ctx* c, int64_t skip_tile, uint64_t wait_ns) {
     if (!c) {
         set_error("sel_ctx_debug_pushdown_fault: ctx is NULL");
@@ -628,6 +646,66 @@ extern "C" sel_status sel_count(sel_ctx* ctx, const sel_pred* pred, const sel_ta
     return SEL_OK;
 }
 
+static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// The two-pass push-down: the count scan with the mask output (d_total gets
+// the exact count), the group offsets, and the scatter of the selected rows
+// (skipped when nothing is to be written).  `a` holds the projection.
+static sel_status pushdown_two_pass(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
+                                    const PushdownArgs& a, int64_t* dev_out_rowids, uint64_t max_rows,
+                                    unsigned long long* d_total) {
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(d_total, 0, 8, ctx->stream));
+    const int64_t n = table->n_rows;
+    if (n == 0) return SEL_OK;
+    const int64_t n_chunks = (n + kChunkRows - 1) / kChunkRows;
+    const int64_t n_seg = (n_chunks + kSegChunks - 1) / kSegChunks;
+    const int64_t n_grp = (n_seg + kGrpSegs - 1) / kGrpSegs;
+    // scratch: segment counts | segment bitmaps (zeroed together) | group offsets | row masks
+    const size_t seg_bytes = align256((size_t)n_grp * kGrpSegs * 4);
+    const size_t nz_bytes = align256((size_t)n_seg * 8);
+    const size_t off_bytes = align256((size_t)n_grp * 8);
+    const size_t mask_bytes = align256((size_t)n_chunks * 32);
+    sel_status s = ctx->pd_mask.ensure(seg_bytes + nz_bytes + off_bytes + mask_bytes, "push-down masks");
+    if (s != SEL_OK) return s;
+    uint8_t* base = static_cast<uint8_t*>(ctx->pd_mask.p);
+    uint32_t* seg_cnt = reinterpret_cast<uint32_t*>(base);
+    unsigned long long* seg_nz = reinterpret_cast<unsigned long long*>(base + seg_bytes);
+    unsigned long long* grp_off = reinterpret_cast<unsigned long long*>(base + seg_bytes + nz_bytes);
+    uint8_t* mask = base + seg_bytes + nz_bytes + off_bytes;
+    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(base, 0, seg_bytes + nz_bytes, ctx->stream));
+    TableArg ta;
+    fill_table_arg(ta, pred->prog.slot_col, table);
+    ta.prog_begin = 0;
+    ta.prog_end = 1;
+    const Shape sh = single_shape(ctx, ta.row_bytes);
+    s = run_scan(ctx, static_cast<const uint8_t*>(pred->d_blob), pred->blob_bytes, pred->instr_off, pred->pool_off,
+                 1, {ta}, d_total, sh, nullptr, mask, seg_cnt, seg_nz);
+    if (s != SEL_OK) return s;
+    if (max_rows == 0 || (a.n_proj == 0 && !dev_out_rowids)) return SEL_OK;
+    cudaError_t e = launch_seg_scan(seg_cnt, grp_off, n_grp, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail("push-down offsets launch", e);
+    ScatterArgs sa;
+    std::memset(&sa, 0, sizeof(sa));
+    sa.mask = mask;
+    sa.seg_cnt = seg_cnt;
+    sa.seg_nz = seg_nz;
+    sa.grp_off = grp_off;
+    sa.n_rows = n;
+    sa.n_seg = n_seg;
+    sa.n_proj = a.n_proj;
+    for (uint32_t j = 0; j < a.n_proj; ++j) {
+        sa.src[j] = a.proj_src[j];
+        sa.dst[j] = a.proj_dst[j];
+        sa.width[j] = a.proj_width[j];
+    }
+    sa.rowids = reinterpret_cast<long long*>(dev_out_rowids);
+    sa.max_rows = max_rows;
+    e = launch_pushdown_scatter(sa, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail("push-down scatter launch", e);
+    ctx->launches += 2;
+    return SEL_OK;
+}
+
 // Enqueues the push-down; the exact count lands in d_total (device).
 static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
                                    const int32_t* proj_cols, int32_t n_proj, void* const* dev_out_cols,
@@ -672,6 +750,9 @@ static sel_status pushdown_enqueue(sel_ctx* ctx, const sel_pred* pred, const sel
     }
     s = pred_upload(pred);
     if (s != SEL_OK) return s;
+    a.n_proj = (uint32_t)n_proj;
+    if (ctx->pd_method != SEL_PD_ONE_PASS)
+        return pushdown_two_pass(ctx, pred, table, a, dev_out_rowids, max_rows, d_total);
     TableArg ta;
     fill_table_arg(ta, pred->prog.slot_col, table);
     a.blob = static_cast<const uint8_t*>(pred->d_blob);

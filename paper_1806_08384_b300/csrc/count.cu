@@ -27,7 +27,12 @@ namespace sel {
 // tile's table.  blob is the program blob (shared or global memory); the
 // kernel calls this with a pointer the compiler can trace to shared memory
 // when the blob is staged there, so instruction and pool reads are shared loads.
-template <int W, int G>
+// MASK (one program on one table, the first pass of the two-pass push-down):
+// a chunk with selected rows stores its lane bytes (mask: byte l of chunk c
+// is lane l's 8-bit mask, bit i < 4 row 4l + i, bit 4 + i row 128 + 4l + i of
+// the chunk), adds its count to its segment's (seg_cnt) and sets its bit in
+// the segment's bitmap (seg_nz); an empty chunk stores nothing.
+template <int W, int G, bool MASK>
 __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* blob, uint64_t* full, uint64_t* empty,
                                               unsigned long long* cnt, uint8_t* stages,
                                               const uint32_t (&s_off)[kMaxTables][kMaxSlots], uint32_t* s_fail,
@@ -75,11 +80,39 @@ __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* 
             for (uint32_t p = T.prog_begin; p < T.prog_end; ++p) {
                 uint32_t m[G];
                 eval_program_g<G>(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane, m);
-                uint32_t pc = 0;
+                if constexpr (MASK) {
+                    const int64_t chunk0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows / kChunkRows) +
+                                           grp * G;
+                    uint32_t c = 0;
 #pragma unroll
-                for (int q = 0; q < G; ++q) pc += __popc(m[q] & vm[q]);
-                const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
-                if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
+                    for (int q0 = 0; q0 < G; q0 += 2) {   // two chunk counts per reduction
+                        const int q1 = q0 + 1 < G ? q0 + 1 : q0;   // G odd: the last pair has one chunk
+                        const uint32_t m0 = m[q0] & vm[q0];
+                        const uint32_t m1 = q0 + 1 < G ? m[q1] & vm[q1] : 0u;
+                        const uint32_t both = __reduce_add_sync(0xFFFFFFFFu, __popc(m0) | (__popc(m1) << 16));
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (q0 + h >= G) break;
+                            const uint32_t cq = h ? both >> 16 : both & 0xFFFFu;
+                            if (cq) {   // warp-uniform; a missing chunk of the last group has cq = 0
+                                const int64_t gc = chunk0 + q0 + h;
+                                a.mask[gc * 32 + lane] = static_cast<uint8_t>(h ? m1 : m0);
+                                if (lane == 0) {
+                                    atomicAdd(&a.seg_cnt[gc / kSegChunks], cq);
+                                    atomicOr(&a.seg_nz[gc / kSegChunks], 1ull << (gc % kSegChunks));
+                                }
+                            }
+                            c += cq;
+                        }
+                    }
+                    if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
+                } else {
+                    uint32_t pc = 0;
+#pragma unroll
+                    for (int q = 0; q < G; ++q) pc += __popc(m[q] & vm[q]);
+                    const uint32_t c = __reduce_add_sync(0xFFFFFFFFu, pc);
+                    if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
+                }
             }
         }
         rot += n_groups;
@@ -95,7 +128,7 @@ __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* 
 // W consumer warps (+1 producer warp); each consumer pass evaluates the
 // programs on G chunks at once (G independent mask stacks share one
 // instruction stream, which hides the interpreter's latency).
-template <int W, int G>
+template <int W, int G, bool MASK>
 __global__ void __launch_bounds__((W + 1) * 32, (W == 8 && G < 4) ? 2 : 1) scan_count_kernel(const __grid_constant__ ScanArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint32_t s_off[kMaxTables][kMaxSlots];
@@ -154,9 +187,9 @@ __global__ void __launch_bounds__((W + 1) * 32, (W == 8 && G < 4) ? 2 : 1) scan_
         }
     } else if (a.prog_in_smem) {
         // the program's address space is visible to the compiler: shared loads
-        consume_tiles<W, G>(a, smem + a.prog_off, full, empty, cnt, stages, s_off, &s_fail, warp, lane);
+        consume_tiles<W, G, MASK>(a, smem + a.prog_off, full, empty, cnt, stages, s_off, &s_fail, warp, lane);
     } else {
-        consume_tiles<W, G>(a, a.blob, full, empty, cnt, stages, s_off, &s_fail, warp, lane);
+        consume_tiles<W, G, MASK>(a, a.blob, full, empty, cnt, stages, s_off, &s_fail, warp, lane);
     }
     __syncthreads();
     if (s_fail) return;   // counts are invalid; the error flag is set
@@ -175,14 +208,20 @@ size_t scan_layout(ScanArgs& a) {
     return static_cast<size_t>(a.stage_off) + static_cast<size_t>(a.stages) * a.stage_bytes;
 }
 
-template <int W, int G>
-static cudaError_t set_smem_limit(int optin, int* dyn_max) {
+template <int W, int G, bool MASK>
+static cudaError_t set_smem_limit_1(int optin, int* dyn_max) {
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, scan_count_kernel<W, G>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, scan_count_kernel<W, G, MASK>);
     if (e != cudaSuccess) return e;
     const int lim = optin - static_cast<int>(fa.sharedSizeBytes);
     *dyn_max = *dyn_max < 0 ? lim : std::min(*dyn_max, lim);
-    return cudaFuncSetAttribute(scan_count_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return cudaFuncSetAttribute(scan_count_kernel<W, G, MASK>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+template <int W, int G>
+static cudaError_t set_smem_limit(int optin, int* dyn_max) {
+    cudaError_t e = set_smem_limit_1<W, G, false>(optin, dyn_max);
+    return e == cudaSuccess ? set_smem_limit_1<W, G, true>(optin, dyn_max) : e;
 }
 
 cudaError_t scan_kernel_max_smem(int optin, int* dyn_max) {
@@ -199,21 +238,32 @@ bool scan_variant_ok(int warps, int group) {
     return ((warps == 8 || warps == 16) && (group == 1 || group == 2)) || (warps == 8 && group == 4);
 }
 
-cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group) {
+template <bool MASK>
+static cudaError_t launch_scan_count_1(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps,
+                                       int group) {
     if (warps == 8 && group == 1)
-        scan_count_kernel<8, 1><<<grid, 9 * 32, smem, st>>>(a);
+        scan_count_kernel<8, 1, MASK><<<grid, 9 * 32, smem, st>>>(a);
     else if (warps == 8 && group == 2)
-        scan_count_kernel<8, 2><<<grid, 9 * 32, smem, st>>>(a);
+        scan_count_kernel<8, 2, MASK><<<grid, 9 * 32, smem, st>>>(a);
     else if (warps == 16 && group == 1)
-        scan_count_kernel<16, 1><<<grid, 17 * 32, smem, st>>>(a);
+        scan_count_kernel<16, 1, MASK><<<grid, 17 * 32, smem, st>>>(a);
     else if (warps == 16 && group == 2)
-        scan_count_kernel<16, 2><<<grid, 17 * 32, smem, st>>>(a);
+        scan_count_kernel<16, 2, MASK><<<grid, 17 * 32, smem, st>>>(a);
     else if (warps == 8 && group == 4)
-        scan_count_kernel<8, 4><<<grid, 9 * 32, smem, st>>>(a);
-
+        scan_count_kernel<8, 4, MASK><<<grid, 9 * 32, smem, st>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
+}
+
+cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group) {
+    if (a.mask) {   // one program on one table
+        if (a.n_tables != 1 || a.n_progs != 1 || a.tile_rows % kChunkRows != 0 || a.tile_rows > kMaxTileRows ||
+            !a.seg_cnt || !a.seg_nz)
+            return cudaErrorInvalidValue;
+        return launch_scan_count_1<true>(a, grid, smem, st, warps, group);
+    }
+    return launch_scan_count_1<false>(a, grid, smem, st, warps, group);
 }
 
 }  // namespace sel

@@ -41,6 +41,12 @@ struct ScanArgs {
     int64_t total_tiles;
     unsigned long long* counts;      // n_progs, zeroed before the launch
     unsigned int* err;               // bit 0: a bounded wait timed out
+    // Mask output of the two-pass push-down (one program on one table; null
+    // otherwise): the lane bytes of every chunk that has selected rows, and,
+    // atomically, each segment's count and bitmap of chunks with rows.
+    uint8_t* mask;                   // [chunks][32]
+    uint32_t* seg_cnt;               // [segments], zeroed before the launch
+    unsigned long long* seg_nz;      // [segments], zeroed before the launch
     TableArg t[kMaxTables];
 };
 
@@ -101,6 +107,32 @@ struct PushdownArgs {
 };
 
 size_t pushdown_layout(PushdownArgs& a);
+
+// ---------------------------------------------------------------------------
+// two-pass push-down: the count scan stores the row masks (ScanArgs.mask),
+// a one-CTA kernel turns the segment counts into output offsets, and the
+// scatter kernel writes the selected rows
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSegChunks = 64;   // a segment: 64 chunks (16384 rows), one scatter warp
+constexpr uint32_t kGrpSegs = 64;     // an offset group: 64 segments
+
+struct ScatterArgs {
+    const uint8_t* mask;                 // [chunks][32] lane bytes (written for chunks with rows)
+    const uint32_t* seg_cnt;             // [n_grp * kGrpSegs] selected rows per segment (zero past the table)
+    const unsigned long long* seg_nz;    // [n_seg] bit c: chunk c of the segment has selected rows
+    const unsigned long long* grp_off;   // [n_grp] output offset of each group's first row
+    int64_t n_rows, n_seg;
+    uint32_t n_proj, pad;
+    const uint8_t* src[kPdMaxProj];
+    uint8_t* dst[kPdMaxProj];
+    uint32_t width[kPdMaxProj];          // 4 or 8
+    long long* rowids;                   // may be null
+    unsigned long long max_rows;
+};
+
+// grp_off[g] = sum of seg_cnt over the groups before g (n_grp groups).
+cudaError_t launch_seg_scan(const uint32_t* seg_cnt, unsigned long long* grp_off, int64_t n_grp, cudaStream_t st);
+cudaError_t launch_pushdown_scatter(const ScatterArgs& a, cudaStream_t st);
 cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
 
 // Persistent push-down: one CTA per SM with W consumer warps (8, 12 or 16)

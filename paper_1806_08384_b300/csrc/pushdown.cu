@@ -18,6 +18,7 @@
 // positions >= max_rows are not written; the count stays exact.
 #include "kernels.h"
 #include "lookback.cuh"
+#include "rowmask.cuh"
 #include "scan.cuh"
 
 namespace sel {
@@ -365,41 +366,8 @@ __device__ __forceinline__ void fail_flag(const PushdownArgs& a, uint32_t* s_fai
 __device__ __forceinline__ bool volatile_flag(const uint32_t* f) { return *reinterpret_cast<const volatile uint32_t*>(f) != 0; }
 
 // A chunk's row masks are first stored by the consumers as one byte per lane
-// (byte l: bit i < 4 is row 4*l + i, bit 4 + i is row 128 + 4*l + i: the
-// lane's 8-bit mask as the interpreter produces it) and turned into 8
-// row-order words (word k holds rows 32k .. 32k + 31) by the look-back warp
-// before the writers read them.
-// The low nibbles of the 4 bytes of x, packed into 16 bits.
-__device__ __forceinline__ uint32_t pack_nibbles(uint32_t x) {
-    x &= 0x0F0F0F0Fu;
-    x = (x | (x >> 4)) & 0x00FF00FFu;
-    return (x | (x >> 8)) & 0x0000FFFFu;
-}
-
-// Rewrites one chunk's 32 lane bytes (two uint4: x holds lanes 0..15, y lanes
-// 16..31) as its 8 row-order words.
-__device__ __forceinline__ void lane_bytes_to_rows(uint4* w4, const uint4& x, const uint4& y) {
-    const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};   // w[i]: lanes 4i .. 4i + 3
-    uint32_t r[8];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        r[k] = pack_nibbles(w[2 * k]) | (pack_nibbles(w[2 * k + 1]) << 16);
-        r[4 + k] = pack_nibbles(w[2 * k] >> 4) | (pack_nibbles(w[2 * k + 1] >> 4) << 16);
-    }
-    w4[0] = make_uint4(r[0], r[1], r[2], r[3]);
-    w4[1] = make_uint4(r[4], r[5], r[6], r[7]);
-}
-
-// Position of the (o+1)-th set bit of w (o < popc(w)).
-__device__ __forceinline__ uint32_t select_bit(uint32_t w, uint32_t o) {
-    uint32_t pos = 0, c;
-    c = __popc(w & 0xFFFFu); if (o >= c) { o -= c; pos += 16; w >>= 16; }
-    c = __popc(w & 0xFFu);   if (o >= c) { o -= c; pos += 8;  w >>= 8; }
-    c = __popc(w & 0xFu);    if (o >= c) { o -= c; pos += 4;  w >>= 4; }
-    c = __popc(w & 0x3u);    if (o >= c) { o -= c; pos += 2;  w >>= 2; }
-    if (o >= (w & 1u)) pos += 1;
-    return pos;
-}
+// and turned into 8 row-order words by the look-back warp before the writers
+// read them (rowmask.cuh).
 
 // Row of rank r among the selected rows of the super-tile in buffer b.  lo:
 // on entry a chunk whose prefix is <= r (0 always is), on return r's chunk,

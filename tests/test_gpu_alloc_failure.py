@@ -55,7 +55,7 @@ def test_count_pushdown_and_plans(small):
     proj = [t.index(c) for c in dg.CONFIG2_PROJECTION]
     fresh = sel.Context()
     fresh.count(p, T)
-    sel.debug_fail_allocation(1)                    # the push-down's look-back scratch
+    sel.debug_fail_allocation(1)                    # the push-down's scratch (row masks and counts)
     _oom(lambda: fresh.pushdown(p, T, proj, want[0]))
     st, n, cols, ids = fresh.pushdown(p, T, proj, want[0])
     assert st == sel.SEL_OK and n == want[0]

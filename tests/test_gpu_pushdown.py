@@ -32,8 +32,20 @@ def check_pushdown(ctx, T, ot, tree, proj, max_rows=None, rowids=True):
     return n
 
 
+@pytest.fixture(params=[sel.SEL_PD_TWO_PASS, sel.SEL_PD_ONE_PASS], ids=["two_pass", "one_pass"])
+def method(request, ctx):
+    """Runs the test with each push-down method (the context is the test's own)."""
+    ctx.set_pushdown_method(request.param)
+    return request.param
+
+
+@pytest.fixture()
+def one_pass(ctx):
+    ctx.set_pushdown_method(sel.SEL_PD_ONE_PASS)
+
+
 @pytest.mark.parametrize("n", [0, 1, 3, 33, 255, 256, 257, 1023, 1025, 4097, 20_000, 32768, 32769, 70_001])
-def test_random_trees_tiny(ctx, dev, n):
+def test_random_trees_tiny(ctx, dev, method, n):
     t = dg.tiny_table(n, seed=n + 7)
     ot = oracle.OTable.from_table(t)
     T = sel.Table(t.to(dev).columns)
@@ -59,7 +71,7 @@ def proj_cfg2(t):
 # 512 rows only (1024, 2048, 2560, 3584, 4096, 8192); 256 and 1280 are neither
 # and run on the one-CTA-per-tile kernel.
 @pytest.mark.parametrize("tile_rows", [0, 256, 768, 1024, 1280, 1536, 2048, 2304, 2560, 3584, 4096, 8192])
-def test_config2_selectivities(ctx, medium, tile_rows):
+def test_config2_selectivities(ctx, medium, method, tile_rows):
     t, ot, T = medium
     ctx.set_scan_shape(tile_rows, 0, 0)
     for s in dg.CONFIG2_TARGETS:
@@ -67,7 +79,7 @@ def test_config2_selectivities(ctx, medium, tile_rows):
 
 
 @pytest.mark.parametrize("variant", [(12, 3), (12, 2), (12, 1), (16, 2), (16, 1), (8, 2), (8, 1)])
-def test_persistent_variants(ctx, dev, medium, variant):
+def test_persistent_variants(ctx, dev, medium, one_pass, variant):
     """Every persistent push-down variant (consumer warps x chunks per warp), on
     the 1,000,003-row table (ragged last super-tile and sub-tile) and on sizes at
     super-tile boundaries."""
@@ -89,7 +101,7 @@ def test_persistent_variants(ctx, dev, medium, variant):
 
 
 @pytest.mark.parametrize("super_rows", [65536, 131072, 99_840, 256])
-def test_super_tile_sizes(ctx, dev, medium, super_rows):
+def test_super_tile_sizes(ctx, dev, medium, one_pass, super_rows):
     """Super-tiles above the default 32768 rows (the masks and chunk prefixes
     of up to 512 chunks per buffer), one that is no multiple of the sub-tile
     and one smaller than the sub-tile (one sub-tile per super-tile), on the
@@ -110,7 +122,7 @@ def test_super_tile_sizes(ctx, dev, medium, super_rows):
 
 
 @pytest.mark.parametrize("super_rows", [0, 65536])
-def test_four_byte_projections(ctx, dev, medium, super_rows):
+def test_four_byte_projections(ctx, dev, medium, method, super_rows):
     """Projections of 4-byte columns only: 6 such columns (two rounds of 4
     loads a write batch), 1 column, and no column with row ids only, at
     selectivities from 1e-4 to 0.5."""
@@ -145,14 +157,14 @@ def test_bad_super_rows_are_rejected(ctx):
             ctx.set_pushdown_super_rows(r)
 
 
-def test_projection_of_non_predicate_columns_and_no_rowids(ctx, medium):
+def test_projection_of_non_predicate_columns_and_no_rowids(ctx, medium, method):
     t, ot, T = medium
     tree = dg.p_between(t.index("f0"), 100.0, 2000.0)
     check_pushdown(ctx, T, ot, tree, [t.index("k2"), t.index("s1"), t.index("f0")], rowids=False)
     check_pushdown(ctx, T, ot, tree, [], rowids=True)
 
 
-def test_max_rows_contract(ctx, medium):
+def test_max_rows_contract(ctx, medium, method):
     t, ot, T = medium
     tree = dg.config2_predicate(1e-2, seed=12)
     n = oracle.count(ot, tree, threads=THREADS)
@@ -194,7 +206,7 @@ def test_max_rows_contract(ctx, medium):
         assert bool((o[m:] == 7).all())
 
 
-def test_unaligned_columns(ctx, medium):
+def test_unaligned_columns(ctx, medium, method):
     t, ot, _ = medium
     cols = [dg.Column(c.spec, c.data[3:], c.dictionary) for c in t.columns]
     T = sel.Table(cols)
@@ -204,7 +216,7 @@ def test_unaligned_columns(ctx, medium):
 
 
 @pytest.mark.parametrize("tile_rows", [1024, 2048, 3584, 4096, 1280, -65536])
-def test_lookback_wait_times_out_and_context_recovers(ctx, dev, tile_rows):
+def test_lookback_wait_times_out_and_context_recovers(ctx, dev, one_pass, tile_rows):
     """A tile that never publishes makes its successors' bounded waits run out:
     the call returns SEL_ERR_TIMEOUT, and the context works afterwards (the
     persistent kernel, whose look-back unit is a super-tile of up to 32768
@@ -227,6 +239,42 @@ def test_lookback_wait_times_out_and_context_recovers(ctx, dev, tile_rows):
     check_pushdown(ctx, T, ot, tree, [0, 1, 2])
     assert ctx.count(p, T) == oracle.count(ot, tree)
     ctx.set_pushdown_super_rows(0)
+
+
+def test_bad_method_is_rejected(ctx):
+    for m in (-1, 3, 100):
+        with pytest.raises(sel.SelError):
+            ctx.set_pushdown_method(m)
+
+
+@pytest.mark.parametrize("variant", [(16, 2), (16, 1), (8, 2), (8, 1), (8, 4)])
+def test_two_pass_count_variants(ctx, dev, medium, variant):
+    """The two-pass method's first pass is the count scan: every variant of it
+    leaves the same masks and counts."""
+    t, ot, T = medium
+    ctx.set_pushdown_method(sel.SEL_PD_TWO_PASS)
+    ctx.set_scan_variant(*variant)
+    for s in (1e-3, 0.1):
+        check_pushdown(ctx, T, ot, dg.config2_predicate(s, seed=24), proj_cfg2(t))
+    ctx.set_scan_shape(1792, 0, 0)   # 7 chunks a tile: chunk groups that straddle a segment
+    check_pushdown(ctx, T, ot, dg.config2_predicate(0.5, seed=25), proj_cfg2(t))
+
+
+# Sizes at the two-pass method's boundaries: 16384-row segments (one scatter
+# warp each) and groups of 64 segments (1,048,576 rows, one offset each).
+@pytest.mark.parametrize("n", [16383, 16384, 16385, 16384 * 64, 16384 * 64 + 1, 2 * 16384 * 64 + 16384 * 3 + 99])
+def test_two_pass_segment_boundaries(ctx, dev, n):
+    t = dg.tiny_table(n, seed=n % 1000 + 3)
+    ot = oracle.OTable.from_table(t)
+    T = sel.Table(t.to(dev).columns)
+    ctx.set_pushdown_method(sel.SEL_PD_TWO_PASS)
+    rng = np.random.default_rng(n)
+    for _ in range(6):
+        check_pushdown(ctx, T, ot, dg.random_tree(t, rng, depth=4), [0, 1, 2, 3, 4])
+    # every row, and every row but the limit
+    check_pushdown(ctx, T, ot, dg.P_TRUE, [0, 1, 2, 3, 4])
+    st, cnt, _, ids = ctx.pushdown(sel.Predicate(T, dg.P_TRUE), T, [0], n - 5)
+    assert st == sel.SEL_ERR_TOO_LARGE and cnt == n
 
 
 @pytest.mark.slow
