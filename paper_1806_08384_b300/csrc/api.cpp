@@ -272,13 +272,12 @@ static sel_status resolve_shape(sel_ctx* ctx, uint32_t blob_bytes, uint32_t n_pr
 
 // Fills shape-dependent fields and launches (several launches when the
 // tables do not fit in one).
-// mask / seg_cnt / seg_nz: the two-pass push-down's first pass (one program
-// on one table: the row masks and segment counts of ScanArgs), else null.
+// mask / ccnt: the two-pass push-down's first pass (one program on one
+// table: the row masks and chunk counts of ScanArgs), else null.
 static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_bytes, uint32_t instr_off,
                            uint32_t pool_off, uint32_t n_progs, std::vector<TableArg> tables,
                            unsigned long long* d_counts, const Shape& sh_in, int* n_launches,
-                           uint8_t* mask = nullptr, uint32_t* seg_cnt = nullptr,
-                           unsigned long long* seg_nz = nullptr) {
+                           uint8_t* mask = nullptr, uint16_t* ccnt = nullptr) {
     int launches = 0;
     Shape sh;
     {
@@ -298,8 +297,7 @@ static sel_status run_scan(sel_ctx* ctx, const uint8_t* d_blob, uint32_t blob_by
         a.counts = d_counts;
         a.err = static_cast<unsigned int*>(ctx->err.p);
         a.mask = mask;
-        a.seg_cnt = seg_cnt;
-        a.seg_nz = seg_nz;
+        a.ccnt = ccnt;
         const size_t t1 = std::min(tables.size(), t0 + kMaxTables);
         a.n_tables = (uint32_t)(t1 - t0);
         uint32_t max_rb = 0;
@@ -648,47 +646,51 @@ extern "C" sel_status sel_count(sel_ctx* ctx, const sel_pred* pred, const sel_ta
 
 static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// The two-pass push-down: the count scan with the mask output (d_total gets
-// the exact count), the group offsets, and the scatter of the selected rows
-// (skipped when nothing is to be written).  `a` holds the projection.
+// The two-pass push-down: the count scan with the mask output (chunk masks
+// and counts), the segment counts, the group offsets and the exact count
+// (d_total), and the scatter of the selected rows (skipped when nothing is to
+// be written).  `a` holds the projection.
 static sel_status pushdown_two_pass(sel_ctx* ctx, const sel_pred* pred, const sel_table* table,
                                     const PushdownArgs& a, int64_t* dev_out_rowids, uint64_t max_rows,
                                     unsigned long long* d_total) {
-    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(d_total, 0, 8, ctx->stream));
     const int64_t n = table->n_rows;
-    if (n == 0) return SEL_OK;
+    if (n == 0) {
+        SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(d_total, 0, 8, ctx->stream));
+        return SEL_OK;
+    }
     const int64_t n_chunks = (n + kChunkRows - 1) / kChunkRows;
     const int64_t n_seg = (n_chunks + kSegChunks - 1) / kSegChunks;
     const int64_t n_grp = (n_seg + kGrpSegs - 1) / kGrpSegs;
-    // scratch: segment counts | segment bitmaps (zeroed together) | group offsets | row masks
+    // scratch: segment counts | group offsets | chunk counts | row masks (every entry written before it is read)
     const size_t seg_bytes = align256((size_t)n_grp * kGrpSegs * 4);
-    const size_t nz_bytes = align256((size_t)n_seg * 8);
     const size_t off_bytes = align256((size_t)n_grp * 8);
+    const size_t ccnt_bytes = align256((size_t)n_chunks * 2);
     const size_t mask_bytes = align256((size_t)n_chunks * 32);
-    sel_status s = ctx->pd_mask.ensure(seg_bytes + nz_bytes + off_bytes + mask_bytes, "push-down masks");
+    sel_status s = ctx->pd_mask.ensure(seg_bytes + off_bytes + ccnt_bytes + mask_bytes, "push-down masks");
     if (s != SEL_OK) return s;
     uint8_t* base = static_cast<uint8_t*>(ctx->pd_mask.p);
     uint32_t* seg_cnt = reinterpret_cast<uint32_t*>(base);
-    unsigned long long* seg_nz = reinterpret_cast<unsigned long long*>(base + seg_bytes);
-    unsigned long long* grp_off = reinterpret_cast<unsigned long long*>(base + seg_bytes + nz_bytes);
-    uint8_t* mask = base + seg_bytes + nz_bytes + off_bytes;
-    SEL_CUDA("cudaMemsetAsync", cudaMemsetAsync(base, 0, seg_bytes + nz_bytes, ctx->stream));
+    unsigned long long* grp_off = reinterpret_cast<unsigned long long*>(base + seg_bytes);
+    uint16_t* ccnt = reinterpret_cast<uint16_t*>(base + seg_bytes + off_bytes);
+    uint8_t* mask = base + seg_bytes + off_bytes + ccnt_bytes;
     TableArg ta;
     fill_table_arg(ta, pred->prog.slot_col, table);
     ta.prog_begin = 0;
     ta.prog_end = 1;
     const Shape sh = single_shape(ctx, ta.row_bytes);
     s = run_scan(ctx, static_cast<const uint8_t*>(pred->d_blob), pred->blob_bytes, pred->instr_off, pred->pool_off,
-                 1, {ta}, d_total, sh, nullptr, mask, seg_cnt, seg_nz);
+                 1, {ta}, d_total, sh, nullptr, mask, ccnt);
     if (s != SEL_OK) return s;
-    if (max_rows == 0 || (a.n_proj == 0 && !dev_out_rowids)) return SEL_OK;
-    cudaError_t e = launch_seg_scan(seg_cnt, grp_off, n_grp, ctx->stream);
+    cudaError_t e = launch_seg_sum(ccnt, n_chunks, seg_cnt, n_grp, ctx->stream);
+    if (e == cudaSuccess) e = launch_seg_scan(seg_cnt, grp_off, n_grp, d_total, ctx->stream);
     if (e != cudaSuccess) return cuda_fail("push-down offsets launch", e);
+    ctx->launches += 2;
+    if (max_rows == 0 || (a.n_proj == 0 && !dev_out_rowids)) return SEL_OK;
     ScatterArgs sa;
     std::memset(&sa, 0, sizeof(sa));
     sa.mask = mask;
+    sa.ccnt = ccnt;
     sa.seg_cnt = seg_cnt;
-    sa.seg_nz = seg_nz;
     sa.grp_off = grp_off;
     sa.n_rows = n;
     sa.n_seg = n_seg;
@@ -702,7 +704,7 @@ static sel_status pushdown_two_pass(sel_ctx* ctx, const sel_pred* pred, const se
     sa.max_rows = max_rows;
     e = launch_pushdown_scatter(sa, ctx->stream);
     if (e != cudaSuccess) return cuda_fail("push-down scatter launch", e);
-    ctx->launches += 2;
+    ctx->launches++;
     return SEL_OK;
 }
 

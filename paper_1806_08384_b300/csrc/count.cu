@@ -28,10 +28,10 @@ namespace sel {
 // kernel calls this with a pointer the compiler can trace to shared memory
 // when the blob is staged there, so instruction and pool reads are shared loads.
 // MASK (one program on one table, the first pass of the two-pass push-down):
-// a chunk with selected rows stores its lane bytes (mask: byte l of chunk c
-// is lane l's 8-bit mask, bit i < 4 row 4l + i, bit 4 + i row 128 + 4l + i of
-// the chunk), adds its count to its segment's (seg_cnt) and sets its bit in
-// the segment's bitmap (seg_nz); an empty chunk stores nothing.
+// every chunk stores its lane bytes (mask: byte l of chunk c is lane l's
+// 8-bit mask, bit i < 4 row 4l + i, bit 4 + i row 128 + 4l + i of the chunk)
+// and its number of selected rows (ccnt), with no branch and no atomic; the
+// total is left to the kernels that sum the chunk counts.
 template <int W, int G, bool MASK>
 __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* blob, uint64_t* full, uint64_t* empty,
                                               unsigned long long* cnt, uint8_t* stages,
@@ -83,29 +83,23 @@ __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* 
                 if constexpr (MASK) {
                     const int64_t chunk0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows / kChunkRows) +
                                            grp * G;
-                    uint32_t c = 0;
 #pragma unroll
                     for (int q0 = 0; q0 < G; q0 += 2) {   // two chunk counts per reduction
                         const int q1 = q0 + 1 < G ? q0 + 1 : q0;   // G odd: the last pair has one chunk
                         const uint32_t m0 = m[q0] & vm[q0];
                         const uint32_t m1 = q0 + 1 < G ? m[q1] & vm[q1] : 0u;
                         const uint32_t both = __reduce_add_sync(0xFFFFFFFFu, __popc(m0) | (__popc(m1) << 16));
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            if (q0 + h >= G) break;
-                            const uint32_t cq = h ? both >> 16 : both & 0xFFFFu;
-                            if (cq) {   // warp-uniform; a missing chunk of the last group has cq = 0
-                                const int64_t gc = chunk0 + q0 + h;
-                                a.mask[gc * 32 + lane] = static_cast<uint8_t>(h ? m1 : m0);
-                                if (lane == 0) {
-                                    atomicAdd(&a.seg_cnt[gc / kSegChunks], cq);
-                                    atomicOr(&a.seg_nz[gc / kSegChunks], 1ull << (gc % kSegChunks));
-                                }
-                            }
-                            c += cq;
+                        // no branch around the stores: a missing chunk of a tile's last group stores nothing
+                        const bool has0 = grp * G + q0 < n_chunks;
+                        const bool has1 = q0 + 1 < G && grp * G + q0 + 1 < n_chunks;
+                        uint8_t* mp = a.mask + (chunk0 + q0) * 32 + lane;
+                        if (has0) mp[0] = static_cast<uint8_t>(m0);
+                        if (has1) mp[32] = static_cast<uint8_t>(m1);
+                        if (lane == 0) {
+                            if (has0) a.ccnt[chunk0 + q0] = static_cast<uint16_t>(both & 0xFFFFu);
+                            if (has1) a.ccnt[chunk0 + q0 + 1] = static_cast<uint16_t>(both >> 16);
                         }
                     }
-                    if (lane == 0 && c) atomicAdd(&cnt[p], static_cast<unsigned long long>(c));
                 } else {
                     uint32_t pc = 0;
 #pragma unroll
@@ -193,6 +187,7 @@ __global__ void __launch_bounds__((W + 1) * 32, (W == 8 && G < 4) ? 2 : 1) scan_
     }
     __syncthreads();
     if (s_fail) return;   // counts are invalid; the error flag is set
+    if constexpr (MASK) return;   // the chunk counts are the result
     const ProgDesc* pd = reinterpret_cast<const ProgDesc*>(blob);
     for (uint32_t p = tid; p < a.n_progs; p += blockDim.x)
         if (cnt[p]) atomicAdd(&a.counts[pd[p].out], cnt[p]);
@@ -259,7 +254,7 @@ static cudaError_t launch_scan_count_1(const ScanArgs& a, int grid, size_t smem,
 cudaError_t launch_scan_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group) {
     if (a.mask) {   // one program on one table
         if (a.n_tables != 1 || a.n_progs != 1 || a.tile_rows % kChunkRows != 0 || a.tile_rows > kMaxTileRows ||
-            !a.seg_cnt || !a.seg_nz)
+            !a.ccnt)
             return cudaErrorInvalidValue;
         return launch_scan_count_1<true>(a, grid, smem, st, warps, group);
     }

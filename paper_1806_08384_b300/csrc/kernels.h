@@ -42,11 +42,10 @@ struct ScanArgs {
     unsigned long long* counts;      // n_progs, zeroed before the launch
     unsigned int* err;               // bit 0: a bounded wait timed out
     // Mask output of the two-pass push-down (one program on one table; null
-    // otherwise): the lane bytes of every chunk that has selected rows, and,
-    // atomically, each segment's count and bitmap of chunks with rows.
+    // otherwise): every chunk's lane bytes and selected-row count; counts is
+    // then not written.
     uint8_t* mask;                   // [chunks][32]
-    uint32_t* seg_cnt;               // [segments], zeroed before the launch
-    unsigned long long* seg_nz;      // [segments], zeroed before the launch
+    uint16_t* ccnt;                  // [chunks]
     TableArg t[kMaxTables];
 };
 
@@ -117,9 +116,9 @@ constexpr uint32_t kSegChunks = 64;   // a segment: 64 chunks (16384 rows), one 
 constexpr uint32_t kGrpSegs = 64;     // an offset group: 64 segments
 
 struct ScatterArgs {
-    const uint8_t* mask;                 // [chunks][32] lane bytes (written for chunks with rows)
+    const uint8_t* mask;                 // [chunks][32] lane bytes
+    const uint16_t* ccnt;                // [chunks] selected rows per chunk
     const uint32_t* seg_cnt;             // [n_grp * kGrpSegs] selected rows per segment (zero past the table)
-    const unsigned long long* seg_nz;    // [n_seg] bit c: chunk c of the segment has selected rows
     const unsigned long long* grp_off;   // [n_grp] output offset of each group's first row
     int64_t n_rows, n_seg;
     uint32_t n_proj, pad;
@@ -130,8 +129,13 @@ struct ScatterArgs {
     unsigned long long max_rows;
 };
 
-// grp_off[g] = sum of seg_cnt over the groups before g (n_grp groups).
-cudaError_t launch_seg_scan(const uint32_t* seg_cnt, unsigned long long* grp_off, int64_t n_grp, cudaStream_t st);
+// seg_cnt[s] = the sum of segment s's chunk counts, for all n_grp * kGrpSegs
+// segments (0 past the table's n_chunks chunks).
+cudaError_t launch_seg_sum(const uint16_t* ccnt, int64_t n_chunks, uint32_t* seg_cnt, int64_t n_grp, cudaStream_t st);
+// grp_off[g] = sum of seg_cnt over the groups before g (n_grp groups);
+// *total = the sum over all groups.
+cudaError_t launch_seg_scan(const uint32_t* seg_cnt, unsigned long long* grp_off, int64_t n_grp,
+                            unsigned long long* total, cudaStream_t st);
 cudaError_t launch_pushdown_scatter(const ScatterArgs& a, cudaStream_t st);
 cudaError_t launch_pushdown(const PushdownArgs& a, cudaStream_t st);
 
