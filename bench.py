@@ -173,6 +173,19 @@ def algorithmic_bytes(types, n, trees, counts, accepted, proj):
     return batch, pds
 
 
+def pushdown_pass_bytes(types, n, trees, counts, accepted, proj):
+    """Per push-down, the algorithmic bytes of its two passes: the count pass
+    reads the predicate columns; the scatter reads every projected value of
+    the selected rows (predicate columns included: the count pass keeps only
+    the row masks) and writes them with their int64 row ids."""
+    out = []
+    for i in accepted:
+        pc = dg.tree_columns(trees[i])
+        pw = sum(WIDTH[types[c]] for c in proj)
+        out.append((sum(WIDTH[types[c]] for c in set(pc)) * n, counts[i] * (2 * pw + 8)))
+    return out
+
+
 class Workload:
     """Config 5: 1.2B rows x 6 columns, 256 probes, push-down of 3 columns."""
 
@@ -199,7 +212,7 @@ class OurStep:
         cap = max(1, w.max_rows)
         self.out_cols = [torch.empty(cap, dtype=w.table.columns[c].data.dtype, device=dev) for c in w.proj]
         self.out_ids = torch.empty(cap, dtype=torch.int64, device=dev)
-        self.events = []            # (kind, start, end) of the timed steps
+        self.events = []            # (kind, start, end[, split]) of the timed steps
         self.host_out = None
         # the batch plan (autotuned, graph-captured) is created and cached by the first call
         preds = [sel.Predicate(self.T, t) for t in w.trees]
@@ -234,12 +247,17 @@ class OurStep:
                 ctx.stream.wait_event(self.copy_done[k % 2])                    # the set's last copy has read it
             if record:
                 a.record()
+                # the library records `mid` between the push-down's count pass and its scatter
+                mid = ev()
+                mid.record()
+                ctx.set_pushdown_split_event(mid)
             torch.cuda.nvtx.range_push("a4_pushdown")
             ctx.pushdown_async(preds[i], T, w.proj, w.max_rows, outs, ids, self.pd_counts[i:i + 1])
             torch.cuda.nvtx.range_pop()
             if record:
+                ctx.set_pushdown_split_event(None)
                 b.record()
-                self.events.append(("pushdown", a, b))
+                self.events.append(("pushdown", a, b, mid))
             if e2e:
                 done = torch.cuda.Event()
                 done.record(ctx.stream)
@@ -559,8 +577,8 @@ def config5_gated(step: "OurStep", n_train=100_000, n_val=10_000, reps=3):
         "featurizable_fraction": round(float(okt.mean()), 3),
         "answered_by_network": int(acc.sum()), "exact_fallbacks": int(used.sum()),
         "gated_ms": round(gated_ms, 3), "gated_ms_per_estimate": round(gated_ms / len(wl), 4),
-        "exact_batched_ms_per_estimate": round(statistics.mean(a.elapsed_time(b) for k, a, b in step.events
-                                                               if k == "count") / len(wl), 4),
+        "exact_batched_ms_per_estimate": round(statistics.mean(e[1].elapsed_time(e[2]) for e in step.events
+                                                               if e[0] == "count") / len(wl), 4),
         "q_error_p50": round(float(np.median(q)), 3), "q_error_p95": round(float(np.percentile(q, 95)), 3),
         "accepted_q_error_p95": round(float(np.percentile(q[acc], 95)), 3) if acc.any() else None,
         "network_q_error_p50_featurizable": quality["q_error_p50"],
@@ -797,7 +815,9 @@ def cpu_rate(ot, types, trees, proj, threads, reps=1):
 KERNEL_SOURCES = {
     "bucket_count_kernel": ("scan.cuh", "program.h", "kernels.h", "bucket.h", "bucket_count.cu"),
     "scan_count_kernel": ("scan.cuh", "program.h", "kernels.h", "count.cu"),
-    "pushdown_persistent_kernel": ("scan.cuh", "program.h", "kernels.h", "lookback.cuh", "pushdown.cu"),
+    "pushdown_persistent_kernel": ("scan.cuh", "program.h", "kernels.h", "lookback.cuh", "rowmask.cuh", "pushdown.cu"),
+    "scan_count_kernel_mask": ("scan.cuh", "program.h", "kernels.h", "count.cu"),
+    "pushdown_scatter_kernel": ("program.h", "kernels.h", "rowmask.cuh", "scatter.cu"),
 }
 
 
@@ -954,19 +974,32 @@ def main():
     launches = step.ctx.launches + (sur.ctx.launches if sur else 0) - launches0
     elapsed_ms, value = replica_throughput(t0.elapsed_time(t1), step_bytes, args.steps, world, dev)
 
-    # per-kernel durations inside the timed region
-    dur = {"count": [], "pushdown": []}
-    for kind, a, b in step.events:
-        dur[kind].append(a.elapsed_time(b))
+    # per-kernel durations inside the timed region: the batched count, and each
+    # push-down's count pass (start -> the library's split event) and the rest
+    # (segment sums, group offsets, scatter)
+    dur = {"count": [], "pushdown": [], "pass1": [], "scatter": []}
+    for e in step.events:
+        if e[0] == "count":
+            dur["count"].append(e[1].elapsed_time(e[2]))
+        else:
+            _, a, b, m = e
+            dur["pushdown"].append(a.elapsed_time(b))
+            dur["pass1"].append(a.elapsed_time(m))
+            dur["scatter"].append(m.elapsed_time(b))
     count_ms = statistics.mean(dur["count"])
-    pd_ms = statistics.mean(dur["pushdown"]) if dur["pushdown"] else 0.0
+    mean = lambda xs: statistics.mean(xs) if xs else 0.0
+    split = pushdown_pass_bytes(w.types, w.n, w.trees, counts, accepted, w.proj)
     peak, peak_kind = load_peaks()
     count_kernel = "bucket_count_kernel"
     kernels = {
         "count": {"name": count_kernel, "ms": count_ms, "bytes": b_batch, "launches": len(dur["count"]),
                   "total_ms": sum(dur["count"])},
-        "pushdown": {"name": "pushdown_persistent_kernel", "ms": pd_ms,
-                     "bytes": (sum(b_pds) / len(b_pds)) if b_pds else 0,
+        "pass1": {"name": "scan_count_kernel_mask", "ms": mean(dur["pass1"]), "bytes": mean([p for p, _ in split]),
+                  "launches": len(dur["pass1"]), "total_ms": sum(dur["pass1"])},
+        "scatter": {"name": "pushdown_scatter_kernel", "ms": mean(dur["scatter"]),
+                    "bytes": mean([q for _, q in split]), "launches": len(dur["scatter"]),
+                    "total_ms": sum(dur["scatter"])},
+        "pushdown": {"name": "push-down (all its kernels)", "ms": mean(dur["pushdown"]), "bytes": mean(b_pds),
                      "launches": len(dur["pushdown"]), "total_ms": sum(dur["pushdown"])},
     }
 
@@ -978,8 +1011,8 @@ def main():
                 "traffic": traffic_for(kk["name"], kk["bytes"]), "kernel": kk["name"],
                 "algorithmic_bytes_per_launch": int(kk["bytes"]), "avg_launch_ms": round(kk["ms"], 4),
                 "launches_timed": kk["launches"], "total_ms_timed": round(kk["total_ms"], 3)}
-    dominant = max(kernels, key=lambda k: kernels[k]["total_ms"])
-    other = "count" if dominant == "pushdown" else "pushdown"
+    dominant = max(("count", "pass1", "scatter"), key=lambda k: kernels[k]["total_ms"])
+    other = "count" if dominant != "count" else "pass1"
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -991,6 +1024,11 @@ def main():
         "ms_per_estimate_note": "the batched count's device time over its 256 probes",
         "roofline": roof(dominant),
         "roofline_other": roof(other),
+        "roofline_scatter": dict(roof("scatter"), note="the events between the count pass and the call's end also "
+                                 "hold the segment-sum and group-scan kernels (about 20 us a push-down)"),
+        "pushdown_call": dict(roof("pushdown"), note="the whole push-down call (its count pass, offsets and "
+                              "scatter) against the step's algorithmic bytes of that push-down: predicate columns, "
+                              "projected values of the selected rows that are not predicate columns, written rows"),
         "roofline_issue": issue_roofline(count_kernel, w.n, count_ms, float((clk or {}).get("sm_max_mhz") or 2032.0)),
         "roofline_smem": smem_roofline(count_kernel, w.n, count_ms, float((clk or {}).get("sm_max_mhz") or 2032.0)),
         "gpu_launches": int(launches),

@@ -122,7 +122,12 @@ const char* sel_status_str(sel_status s);
 /* Create a context bound to a CUDA stream (a cudaStream_t; NULL = the legacy
  * default stream) on the current device.  The context owns small device
  * scratch (result counters, error flag, tile status of the push-down scan,
- * grown on demand) and pinned host buffers for results. */
+ * row masks of the two-pass push-down, grown on demand) and pinned host
+ * buffers for results.  It also sets the calling process's L2 fetch
+ * granularity hint on the device (cudaLimitMaxL2FetchGranularity) to 32
+ * bytes: the push-down's gathers of single values then read a quarter of the
+ * DRAM bytes.  The hint belongs to the process's CUDA context, ends with it,
+ * and can be changed back with cudaDeviceSetLimit. */
 sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out);
 void sel_ctx_destroy(sel_ctx* ctx);
 
@@ -321,6 +326,15 @@ sel_status sel_ctx_set_pushdown_super_rows(sel_ctx* ctx, int32_t rows);
  * Any other value: SEL_ERR_INVALID_ARG. */
 enum { SEL_PD_AUTO = 0, SEL_PD_TWO_PASS = 1, SEL_PD_ONE_PASS = 2 };
 sel_status sel_ctx_set_pushdown_method(sel_ctx* ctx, int32_t method);
+
+/* Timing hook: when cuda_event (a cudaEvent_t of the context's device) is
+ * not NULL, every two-pass push-down enqueued on this context records it on
+ * the context's stream between its count pass and the rest (offsets and
+ * scatter), so that the caller can time the passes separately with events of
+ * its own before and after the call.  The event is recorded when the call
+ * enqueues its work; NULL (the default) turns the hook off.  The caller owns
+ * the event and clears the hook before destroying it. */
+sel_status sel_ctx_set_pushdown_split_event(sel_ctx* ctx, void* cuda_event);
 
 /* Test hook for the bounded waits of the push-down look-back (SEL_PD_ONE_PASS): look-back unit
  * skip_tile (a super-tile of the persistent kernel -- see

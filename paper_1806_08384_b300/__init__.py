@@ -118,6 +118,7 @@ def _load():
         "sel_ctx_debug_pushdown_fault": (C.c_int, [V, C.c_int64, C.c_uint64]),
         "sel_ctx_set_pushdown_super_rows": (C.c_int, [V, C.c_int32]),
         "sel_ctx_set_pushdown_method": (C.c_int, [V, C.c_int32]),
+        "sel_ctx_set_pushdown_split_event": (C.c_int, [V, V]),
         "sel_debug_gemm_bf16": (C.c_int, [V, V, V, C.c_int32, C.c_int32, C.c_int32, V, C.c_int32, V]),
         "sel_count_distinct": (C.c_int, [V, P(sel_table), C.c_int32, V, P(C.c_uint64), P(C.c_uint64)]),
         "sel_join_size_estimate": (C.c_double, [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]),
@@ -362,6 +363,12 @@ class Context:
     def set_pushdown_method(self, method: int):
         """SEL_PD_AUTO (two passes), SEL_PD_TWO_PASS or SEL_PD_ONE_PASS."""
         _check(lib.sel_ctx_set_pushdown_method(self.h, int(method)), "sel_ctx_set_pushdown_method")
+
+    def set_pushdown_split_event(self, event: Optional[torch.cuda.Event]):
+        """Record `event` between the two passes of each later push-down (None: off).
+        The event must have been recorded once (torch creates it lazily)."""
+        h = C.c_void_p(event.cuda_event if event is not None else None)
+        _check(lib.sel_ctx_set_pushdown_split_event(self.h, h), "sel_ctx_set_pushdown_split_event")
 
     def debug_pushdown_fault(self, skip_tile: int, wait_ns: int = 0):
         _check(lib.sel_ctx_debug_pushdown_fault(self.h, skip_tile, wait_ns), "sel_ctx_debug_pushdown_fault")

@@ -123,6 +123,7 @@ struct sel_ctx {
     unsigned long long debug_wait_ns = kWaitNs;
     uint32_t pd_super_rows = 0;   // push-down super-tile target (0: chosen from the table size)
     int pd_method = SEL_PD_AUTO;  // push-down method
+    cudaEvent_t pd_split_event = nullptr;   // recorded between the two passes of a push-down (timing)
 };
 
 struct sel_batch_plan {
@@ -499,6 +500,11 @@ extern "C" sel_status sel_ctx_create(void* cuda_stream, sel_ctx** out) {
     SEL_CUDA("scan smem attribute", scan_kernel_max_smem(c->max_smem, &c->max_smem_scan));
     SEL_CUDA("push-down smem attribute", pushdown_persistent_max_smem(c->max_smem, &c->max_smem_pdp));
     SEL_CUDA("bucket smem attribute", bucket_kernel_max_smem(c->max_smem, &c->max_smem_bucket));
+    // The push-down's gathers read one 4- or 8-byte value per selected row:
+    // with the L2 fetching 32 bytes per miss instead of a whole line they move
+    // a quarter of the DRAM bytes (the scans and their bulk copies read whole
+    // lines either way).  A hint of this process's context on the device.
+    SEL_CUDA("cudaDeviceSetLimit", cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, 32));
     sel_status s = c->err.ensure(256, "error flag");
     if (s != SEL_OK) return s;
     SEL_CUDA("cudaMemset", cudaMemset(c->err.p, 0, 256));
@@ -583,6 +589,15 @@ extern "C" sel_status sel_ctx_set_pushdown_method(sel_ctx* c, int32_t method) {
         return SEL_ERR_INVALID_ARG;
     }
     c->pd_method = method;
+    return SEL_OK;
+}
+
+extern "C" sel_status sel_ctx_set_pushdown_split_event(sel_ctx* c, void* cuda_event) {
+    if (!c) {
+        set_error("sel_ctx_set_pushdown_split_event: ctx is NULL");
+        return SEL_ERR_INVALID_ARG;
+    }
+    c->pd_split_event = static_cast<cudaEvent_t>(cuda_event);
     return SEL_OK;
 }
 
@@ -681,6 +696,7 @@ static sel_status pushdown_two_pass(sel_ctx* ctx, const sel_pred* pred, const se
     s = run_scan(ctx, static_cast<const uint8_t*>(pred->d_blob), pred->blob_bytes, pred->instr_off, pred->pool_off,
                  1, {ta}, d_total, sh, nullptr, mask, ccnt);
     if (s != SEL_OK) return s;
+    if (ctx->pd_split_event) SEL_CUDA("cudaEventRecord", cudaEventRecord(ctx->pd_split_event, ctx->stream));
     cudaError_t e = launch_seg_sum(ccnt, n_chunks, seg_cnt, n_grp, ctx->stream);
     if (e == cudaSuccess) e = launch_seg_scan(seg_cnt, grp_off, n_grp, d_total, ctx->stream);
     if (e != cudaSuccess) return cuda_fail("push-down offsets launch", e);

@@ -284,3 +284,13 @@ def test_config2_full_size(ctx, dev):
     ot = oracle.OTable.from_table(t)
     for s in (1e-4, 1e-2, 0.5):
         check_pushdown(ctx, T, ot, dg.config2_predicate(s), proj_cfg2(t))
+
+
+def test_context_sets_the_l2_fetch_granularity_hint(ctx):
+    """sel_ctx_create leaves the process's L2 fetch granularity hint at 32
+    bytes (the push-down's gathers read single values)."""
+    import ctypes
+    rt = ctypes.CDLL("libcudart.so.13")   # the runtime the library loaded
+    v = ctypes.c_size_t(0)
+    assert rt.cudaDeviceGetLimit(ctypes.byref(v), 5) == 0   # cudaLimitMaxL2FetchGranularity
+    assert v.value == 32
