@@ -28,9 +28,9 @@ namespace sel {
 // kernel calls this with a pointer the compiler can trace to shared memory
 // when the blob is staged there, so instruction and pool reads are shared loads.
 // MASK (one program on one table, the first pass of the two-pass push-down):
-// every chunk stores its lane bytes (mask: byte l of chunk c is lane l's
-// 8-bit mask, bit i < 4 row 4l + i, bit 4 + i row 128 + 4l + i of the chunk)
-// and its number of selected rows (ccnt), with no branch and no atomic; the
+// every chunk stores its number of selected rows (ccnt) and, if it has some,
+// its lane bytes (mask: byte l of chunk c is lane l's 8-bit mask, bit i < 4
+// row 4l + i, bit 4 + i row 128 + 4l + i of the chunk), with no atomic; the
 // total is left to the kernels that sum the chunk counts.
 template <int W, int G, bool MASK>
 __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* blob, uint64_t* full, uint64_t* empty,
@@ -66,6 +66,14 @@ __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* 
         }
         if (*reinterpret_cast<volatile uint32_t*>(s_fail)) break;
         const uint32_t st_addr = smem_u32(stages + static_cast<size_t>(s) * a.stage_bytes);
+        // MASK: the tile's first chunk's mask byte of this lane, and its count
+        [[maybe_unused]] uint8_t* tile_mask = nullptr;
+        [[maybe_unused]] uint16_t* tile_ccnt = nullptr;
+        if constexpr (MASK) {
+            const int64_t tc0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows / kChunkRows);
+            tile_mask = a.mask + tc0 * 32 + lane;
+            tile_ccnt = a.ccnt + tc0;
+        }
         for (uint32_t grp = first; grp < n_groups; grp += W) {
             uint32_t c0[G], vm[G];
 #pragma unroll
@@ -81,23 +89,23 @@ __device__ __forceinline__ void consume_tiles(const ScanArgs& a, const uint8_t* 
                 uint32_t m[G];
                 eval_program_g<G>(ins + pd[p].instr_begin, pd[p].n_instr, pool, st_addr, s_off[ti], c0, lane, m);
                 if constexpr (MASK) {
-                    const int64_t chunk0 = (g - T.tile_begin) * static_cast<int64_t>(a.tile_rows / kChunkRows) +
-                                           grp * G;
+                    const uint32_t chunk0 = grp * G;   // in the tile
 #pragma unroll
                     for (int q0 = 0; q0 < G; q0 += 2) {   // two chunk counts per reduction
                         const int q1 = q0 + 1 < G ? q0 + 1 : q0;   // G odd: the last pair has one chunk
                         const uint32_t m0 = m[q0] & vm[q0];
                         const uint32_t m1 = q0 + 1 < G ? m[q1] & vm[q1] : 0u;
                         const uint32_t both = __reduce_add_sync(0xFFFFFFFFu, __popc(m0) | (__popc(m1) << 16));
-                        // no branch around the stores: a missing chunk of a tile's last group stores nothing
-                        const bool has0 = grp * G + q0 < n_chunks;
-                        const bool has1 = q0 + 1 < G && grp * G + q0 + 1 < n_chunks;
-                        uint8_t* mp = a.mask + (chunk0 + q0) * 32 + lane;
-                        if (has0) mp[0] = static_cast<uint8_t>(m0);
-                        if (has1) mp[32] = static_cast<uint8_t>(m1);
+                        // predicated stores: a chunk without selected rows stores no mask, a
+                        // missing chunk of a tile's last group nothing
+                        const bool has0 = chunk0 + q0 < n_chunks;
+                        const bool has1 = q0 + 1 < G && chunk0 + q0 + 1 < n_chunks;
+                        uint8_t* mp = tile_mask + (chunk0 + q0) * 32u;
+                        if (has0 && (both & 0xFFFFu)) mp[0] = static_cast<uint8_t>(m0);
+                        if (has1 && (both >> 16)) mp[32] = static_cast<uint8_t>(m1);
                         if (lane == 0) {
-                            if (has0) a.ccnt[chunk0 + q0] = static_cast<uint16_t>(both & 0xFFFFu);
-                            if (has1) a.ccnt[chunk0 + q0 + 1] = static_cast<uint16_t>(both >> 16);
+                            if (has0) tile_ccnt[chunk0 + q0] = static_cast<uint16_t>(both & 0xFFFFu);
+                            if (has1) tile_ccnt[chunk0 + q0 + 1] = static_cast<uint16_t>(both >> 16);
                         }
                     }
                 } else {

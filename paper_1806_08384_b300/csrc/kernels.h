@@ -42,8 +42,8 @@ struct ScanArgs {
     unsigned long long* counts;      // n_progs, zeroed before the launch
     unsigned int* err;               // bit 0: a bounded wait timed out
     // Mask output of the two-pass push-down (one program on one table; null
-    // otherwise): every chunk's lane bytes and selected-row count; counts is
-    // then not written.
+    // otherwise): every chunk's selected-row count and the lane bytes of the
+    // chunks that have some; counts is then not written.
     uint8_t* mask;                   // [chunks][32]
     uint16_t* ccnt;                  // [chunks]
     TableArg t[kMaxTables];
@@ -116,7 +116,7 @@ constexpr uint32_t kSegChunks = 64;   // a segment: 64 chunks (16384 rows), one 
 constexpr uint32_t kGrpSegs = 64;     // an offset group: 64 segments
 
 struct ScatterArgs {
-    const uint8_t* mask;                 // [chunks][32] lane bytes
+    const uint8_t* mask;                 // [chunks][32] lane bytes (of the chunks with selected rows)
     const uint16_t* ccnt;                // [chunks] selected rows per chunk
     const uint32_t* seg_cnt;             // [n_grp * kGrpSegs] selected rows per segment (zero past the table)
     const unsigned long long* grp_off;   // [n_grp] output offset of each group's first row

@@ -2,8 +2,9 @@
 // "Materialization"; Algorithm 1, Execute with isSPD = true).
 //
 // The first pass is the COUNT scan itself (count.cu with a mask output): it
-// evaluates the predicate once and leaves, for every 256-row chunk, its 32
-// lane bytes (rowmask.cuh) and its number of selected rows.
+// evaluates the predicate once and leaves, for every 256-row chunk, its
+// number of selected rows and, if it has some, its 32 lane bytes
+// (rowmask.cuh).
 //
 // seg_sum_kernel           a warp per segment of kSegChunks chunks: its
 //                          number of selected rows.
