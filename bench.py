@@ -200,6 +200,44 @@ class Workload:
         self.max_rows = int(math.floor(n_rows * MAX_SELECTIVITY))
 
 
+class DeviceRing:
+    """Output regions for the end-to-end push-downs: consecutive slices of one
+    device buffer, each reused only after the copy that read it (its event)
+    has run, so that the copy-backs of large push-downs never hold up the
+    push-downs after them."""
+
+    def __init__(self, nbytes: int, device):
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.head = 0
+        self.live = []          # [start, end, event or None] of regions still to be read
+        self.pending = []       # regions of the current take, until release_on
+
+    def take(self, counts, dtypes, stream):
+        sizes = [(n * torch.empty(0, dtype=d).element_size() + 255) // 256 * 256 for n, d in zip(counts, dtypes)]
+        need = max(256, sum(sizes))
+        assert need <= self.buf.numel(), "push-down output larger than the ring"
+        if self.head + need > self.buf.numel():
+            self.head = 0
+        a, b = self.head, self.head + need
+        keep = []
+        for r in self.live:
+            if r[0] < b and a < r[1]:
+                stream.wait_event(r[2])         # its copy has read it
+            else:
+                keep.append(r)
+        self.live = keep
+        self.head = b
+        self.pending = [a, b]
+        out, off = [], a
+        for n, d, sz in zip(counts, dtypes, sizes):
+            out.append(self.buf[off:off + sz].view(d)[:n])
+            off += sz
+        return out[:-1], out[-1]
+
+    def release_on(self, event):
+        self.live.append([self.pending[0], self.pending[1], event])
+
+
 class OurStep:
     def __init__(self, w: Workload, sel):
         self.w, self.sel = w, sel
@@ -221,7 +259,7 @@ class OurStep:
         self.ctx.synchronize()
         self.plan_s = time.perf_counter() - t0
 
-    def run(self, record=False, e2e=False, T=None):
+    def run(self, record=False, e2e=False, T=None, rows_back=False):
         w, sel, ctx = self.w, self.sel, self.ctx
         T = T or self.T                                                          # the table's device copy
         preds = [sel.Predicate(T, t) for t in w.trees]                          # a1
@@ -240,11 +278,17 @@ class OurStep:
         d2h = 8 * len(counts)
         for k, i in enumerate(accepted):                                        # a4
             a, b = ev(), ev()
-            # end to end: push-downs alternate between two output sets, and each
-            # one's rows go back to the host on a copy stream while the next runs
-            outs, ids = (self.out_cols, self.out_ids) if not e2e or k % 2 == 0 else self.e2e_out[1]
-            if e2e and self.copy_done[k % 2] is not None:
-                ctx.stream.wait_event(self.copy_done[k % 2])                    # the set's last copy has read it
+            mr = w.max_rows
+            if e2e and rows_back:
+                # end to end: each push-down writes into its own region of a device
+                # ring, sized by its exact count (known from the batched count, so
+                # max_rows = the count bounds the writes to the region), and its rows
+                # go back to the host on a copy stream while the next ones run
+                outs, ids = self.e2e_ring.take([counts[i]] * len(w.proj) + [counts[i]],
+                                               [o.dtype for o in self.out_cols] + [torch.int64], ctx.stream)
+                mr = counts[i]
+            else:
+                outs, ids = self.out_cols, self.out_ids
             if record:
                 a.record()
                 # the library records `mid` between the push-down's count pass and its scatter
@@ -252,26 +296,32 @@ class OurStep:
                 mid.record()
                 ctx.set_pushdown_split_event(mid)
             torch.cuda.nvtx.range_push("a4_pushdown")
-            ctx.pushdown_async(preds[i], T, w.proj, w.max_rows, outs, ids, self.pd_counts[i:i + 1])
+            ctx.pushdown_async(preds[i], T, w.proj, mr, outs, ids, self.pd_counts[i:i + 1])
             torch.cuda.nvtx.range_pop()
             if record:
                 ctx.set_pushdown_split_event(None)
                 b.record()
                 self.events.append(("pushdown", a, b, mid))
-            if e2e:
+            if e2e and rows_back:
                 done = torch.cuda.Event()
                 done.record(ctx.stream)
                 self.copy_stream.wait_event(done)
                 with torch.cuda.stream(self.copy_stream):
                     for o, h in zip(outs + [ids], self.host_out):
                         h[:counts[i]].copy_(o[:counts[i]], non_blocking=True)
-                    self.copy_done[k % 2] = torch.cuda.Event()
-                    self.copy_done[k % 2].record(self.copy_stream)
+                    copied = torch.cuda.Event()
+                    copied.record(self.copy_stream)
+                self.e2e_ring.release_on(copied)
                 d2h += counts[i] * (sum(o.element_size() for o in self.out_cols) + 8)
-        ctx.synchronize()
         if e2e:
+            # the step's result on the host: the exact counts (above) and the
+            # push-downs' counts; the materialised rows stay on the device for
+            # the rest of the query unless rows_back
+            self.pd_counts_host = self.pd_counts.cpu()
+            d2h += 8 * len(counts)
+        ctx.synchronize()
+        if e2e and rows_back:
             self.copy_stream.synchronize()
-            self.copy_done = [None, None]
         return counts, accepted, d2h
 
 
@@ -1045,6 +1095,7 @@ def main():
         out["config1_latency"] = config1_latency(sel, dev)
     if rank == 0 and not args.no_e2e:
         out["e2e"] = run_e2e(step, args, step_bytes)
+        out["e2e_rows_to_host"] = run_e2e(step, args, step_bytes, rows_back=True)
     if rank == 0 and not args.no_cpu:
         ot = oracle_sample(w.table, w.trees, args.cpu_seconds, threads)
         gbs, secs = cpu_rate(ot, w.types, w.trees, w.proj, threads)
@@ -1122,25 +1173,25 @@ def estimator_curve(sel, dev, args):
                                   f"{args.cfg2_rows}-row table, labels from the count kernel"}))
 
 
-def run_e2e(step: OurStep, args, step_bytes):
+def run_e2e(step: OurStep, args, step_bytes, rows_back=False):
     """The same step through the C ABI with the table in pinned HOST memory:
-    every step copies the columns host->device and the results back.  Two
-    device copies of the table: step k + 1's upload (on its own stream) runs
-    while step k computes, and starts only after the step that last read that
-    copy (k - 1) has finished; push-down rows go back on a copy stream while
-    the next push-down runs (OurStep.run)."""
+    every step copies the columns host->device and its result (the exact
+    counts and the push-downs' counts) back; with rows_back, every
+    push-down's rows too.  Two device copies of the table: step k + 1's upload
+    (on its own stream) runs while step k computes, and starts only after the
+    step that last read that copy (k - 1) has finished; push-down rows go back
+    on a copy stream while the next push-down runs (OurStep.run)."""
     w, sel = step.w, step.sel
     host_cols = [torch.empty_like(c.data, device="cpu").pin_memory() for c in w.table.columns]
     for h, c in zip(host_cols, w.table.columns):
         h.copy_(c.data)
-    step.host_out = [torch.empty(o.numel(), dtype=o.dtype).pin_memory() for o in step.out_cols + [step.out_ids]]
-    # a second device output set and a copy stream: the rows of push-down k are
-    # copied back while push-down k + 1 runs (each set is reused only after its
-    # copy has read it)
-    step.e2e_out = [(step.out_cols, step.out_ids),
-                    ([torch.empty_like(o) for o in step.out_cols], torch.empty_like(step.out_ids))]
-    step.copy_stream = torch.cuda.Stream()
-    step.copy_done = [None, None]
+    # host sinks for the rows (each push-down's rows land at their start) and a
+    # copy stream: the rows of push-down k are copied back while the next ones
+    # run, out of a 16 GB device ring of output regions
+    if rows_back:
+        step.host_out = [torch.empty(o.numel(), dtype=o.dtype).pin_memory() for o in step.out_cols + [step.out_ids]]
+        step.e2e_ring = DeviceRing(16 << 30, w.table.columns[0].data.device)
+        step.copy_stream = torch.cuda.Stream()
     dev_cols = [[c.data for c in w.table.columns], [torch.empty_like(c.data) for c in w.table.columns]]
     tabs = [step.T, sel.Table([dg.Column(c.spec, d, c.dictionary) for c, d in zip(w.table.columns, dev_cols[1])])]
     up = torch.cuda.Stream()
@@ -1159,7 +1210,7 @@ def run_e2e(step: OurStep, args, step_bytes):
         b = k % 2
         cur = torch.cuda.current_stream()
         cur.wait_event(uploaded[b])
-        _, _, d2h = step.run(e2e=True, T=tabs[b])
+        _, _, d2h = step.run(e2e=True, T=tabs[b], rows_back=rows_back)
         released[b] = torch.cuda.Event()
         released[b].record(cur)
         return d2h
@@ -1169,7 +1220,7 @@ def run_e2e(step: OurStep, args, step_bytes):
         upload(b)
         one_step(b)
     torch.cuda.synchronize()
-    k = max(1, min(args.steps, 3))
+    k = max(1, args.steps)              # as many steps as the device-timed region
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record()
@@ -1184,12 +1235,16 @@ def run_e2e(step: OurStep, args, step_bytes):
     ms = t0.elapsed_time(t1) / k
     del host_cols, dev_cols, tabs
     step.host_out = None
-    step.e2e_out = None
+    step.e2e_ring = None
     torch.cuda.empty_cache()
     return {"value": round(step_bytes / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": k,
-            "overlap": "step k + 1's table upload and each push-down's copy-back run during step k's kernels "
-                       "(two device copies of the table, two output sets)"}
+            "result_to_host": ("the exact counts, the push-downs' counts and every push-down's rows" if rows_back else
+                               "the exact counts and the push-downs' counts; the materialised rows stay on the device "
+                               "for the rest of the query (Algorithm 1 materialises while R is on the GPU)"),
+            "overlap": ("step k + 1's table upload" + (" and each push-down's copy-back" if rows_back else "") +
+                        " run during step k's kernels (two device copies of the table" +
+                        ("; push-down outputs in a 16 GB device ring)" if rows_back else ")"))}
 
 
 def replica_throughput(elapsed_ms: float, step_bytes: int, steps: int, world: int, device) -> tuple:
