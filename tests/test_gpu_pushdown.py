@@ -294,3 +294,41 @@ def test_context_sets_the_l2_fetch_granularity_hint(ctx):
     v = ctypes.c_size_t(0)
     assert rt.cudaDeviceGetLimit(ctypes.byref(v), 5) == 0   # cudaLimitMaxL2FetchGranularity
     assert v.value == 32
+
+
+def test_split_event_marks_the_end_of_the_count_pass(ctx, medium):
+    """sel_ctx_set_pushdown_split_event: the event is recorded between a
+    two-pass push-down's count pass and its scatter, so start <= split <= end;
+    the one-pass method does not record it; NULL turns the hook off."""
+    t, ot, T = medium
+    tree = dg.config2_predicate(0.1, seed=41)
+    p = sel.Predicate(T, tree)
+    proj = proj_cfg2(t)
+    n = oracle.count(ot, tree, threads=THREADS)
+    outs = [torch.empty(n, dtype=t.columns[j].data.dtype, device="cuda") for j in proj]
+    ids = torch.empty(n, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    a, m, b = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    ctx.set_pushdown_method(sel.SEL_PD_TWO_PASS)
+    m.record()
+    torch.cuda.synchronize()
+    a.record()
+    ctx.set_pushdown_split_event(m)
+    ctx.pushdown_async(p, T, proj, n, outs, ids, cnt)
+    ctx.set_pushdown_split_event(None)
+    b.record()
+    torch.cuda.synchronize()
+    assert int(cnt.item()) == n
+    assert 0.0 < a.elapsed_time(m) <= a.elapsed_time(b)
+    assert np.array_equal(ids.cpu().numpy(), oracle.select(ot, tree, threads=THREADS))
+    # the one-pass method leaves the event where it was
+    m2 = torch.cuda.Event(enable_timing=True)
+    m2.record()
+    torch.cuda.synchronize()
+    a.record()
+    ctx.set_pushdown_method(sel.SEL_PD_ONE_PASS)
+    ctx.set_pushdown_split_event(m2)
+    ctx.pushdown_async(p, T, proj, n, outs, ids, cnt)
+    ctx.set_pushdown_split_event(None)
+    torch.cuda.synchronize()
+    assert a.elapsed_time(m2) < 0.0
