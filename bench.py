@@ -252,6 +252,7 @@ class OurStep:
         self.out_ids = torch.empty(cap, dtype=torch.int64, device=dev)
         self.events = []            # (kind, start, end[, split]) of the timed steps
         self.host_out = None
+        self.next_preds = None
         # the batch plan (autotuned, graph-captured) is created and cached by the first call
         preds = [sel.Predicate(self.T, t) for t in w.trees]
         t0 = time.perf_counter()
@@ -262,7 +263,10 @@ class OurStep:
     def run(self, record=False, e2e=False, T=None, rows_back=False):
         w, sel, ctx = self.w, self.sel, self.ctx
         T = T or self.T                                                          # the table's device copy
-        preds = [sel.Predicate(T, t) for t in w.trees]                          # a1
+        # a1: this step's predicates, compiled while the previous step's batched
+        # count ran (a predicate fits every table of the same columns)
+        preds = self.next_preds or [sel.Predicate(T, t) for t in w.trees]
+        self.next_preds = None
         ev = lambda: torch.cuda.Event(enable_timing=True) if record else None
         e0, e1 = ev(), ev()
         if record:
@@ -273,6 +277,7 @@ class OurStep:
         if record:
             e1.record()
             self.events.append(("count", e0, e1))
+        self.next_preds = [sel.Predicate(T, t) for t in w.trees]               # a1 of the next step
         counts = self.counts_dev.tolist()                                       # exact counts on the host
         accepted = [i for i, c in enumerate(counts) if c <= w.max_rows]         # a3
         d2h = 8 * len(counts)

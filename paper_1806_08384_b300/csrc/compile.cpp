@@ -18,6 +18,7 @@
 #include <cstring>
 #include <limits>
 #include <map>
+#include <mutex>
 #include <sstream>
 
 #include "internal.h"
@@ -819,6 +820,25 @@ void build_blob(const std::vector<const Program*>& progs, const std::vector<std:
     pad16();
 }
 
+// A non-blocking stream per device for the predicate uploads: a copy on the
+// legacy default stream would wait for every kernel queued before it (the
+// caller's earlier scans), and the host with it.
+static cudaStream_t upload_stream(cudaError_t* err) {
+    static std::mutex mu;
+    static std::map<int, cudaStream_t> streams;
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = streams.find(dev);
+    if (it != streams.end()) return it->second;
+    cudaStream_t st = nullptr;
+    *err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (*err != cudaSuccess) return nullptr;
+    streams[dev] = st;
+    return st;
+}
+
 sel_status pred_upload(const sel_pred* cp) {
     sel_pred* p = const_cast<sel_pred*>(cp);
     std::lock_guard<std::mutex> g(p->mu);
@@ -833,10 +853,13 @@ sel_status pred_upload(const sel_pred* cp) {
         set_error("predicate upload: cudaMalloc: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? SEL_ERR_OOM : SEL_ERR_CUDA;
     }
-    e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    // the copy is complete when this returns: later launches on any stream read it
+    cudaStream_t st = upload_stream(&e);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaFree(d);
-        set_error("predicate upload: cudaMemcpy: %s", cudaGetErrorString(e));
+        set_error("predicate upload: %s", cudaGetErrorString(e));
         return SEL_ERR_CUDA;
     }
     p->blob_bytes = (uint32_t)blob.size();
