@@ -284,8 +284,8 @@ sel_status sel_ctx_set_scan_shape(sel_ctx* ctx, int32_t tile_rows, int32_t stage
 /* Count-scan kernel variant for sel_count / sel_count_async (both 0 = the
  * library default): consumer_warps 8 or 16 (plus one producer warp per CTA)
  * and chunks_per_pass 1 or 2 (256-row chunks a warp evaluates with one pass
- * over the program's instructions), or 8 warps with 4 chunks per pass.  Any
- * other pair: SEL_ERR_INVALID_ARG.
+ * over the program's instructions), 8 warps with 4 chunks per pass, or 15
+ * warps with 2 or 3 chunks per pass.  Any other pair: SEL_ERR_INVALID_ARG.
  * The same pair selects the persistent push-down kernel's consumer warps and
  * chunks per pass where that kernel has the variant (8, 12 or 16 warps, 1 or
  * 2 chunks, and 12 x 3; default 12 x 3, or 12 x 2 for a requested tile that is

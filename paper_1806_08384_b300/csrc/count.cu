@@ -234,11 +234,17 @@ cudaError_t scan_kernel_max_smem(int optin, int* dyn_max) {
     if (e == cudaSuccess) e = set_smem_limit<16, 1>(optin, dyn_max);
     if (e == cudaSuccess) e = set_smem_limit<16, 2>(optin, dyn_max);
     if (e == cudaSuccess) e = set_smem_limit<8, 4>(optin, dyn_max);
+    if (e == cudaSuccess) e = set_smem_limit<15, 2>(optin, dyn_max);
+    if (e == cudaSuccess) e = set_smem_limit<15, 3>(optin, dyn_max);
     return e;
 }
 
+// 16 consumer warps and the producer put 5 warps on one scheduler, which caps
+// a thread at 96 registers (the 2-chunk pass spills a few words); 15 consumer
+// warps make 4 a scheduler and 128 registers, room for 3 chunks a pass.
 bool scan_variant_ok(int warps, int group) {
-    return ((warps == 8 || warps == 16) && (group == 1 || group == 2)) || (warps == 8 && group == 4);
+    return ((warps == 8 || warps == 16) && (group == 1 || group == 2)) || (warps == 8 && group == 4) ||
+           (warps == 15 && (group == 2 || group == 3));
 }
 
 template <bool MASK>
@@ -254,6 +260,10 @@ static cudaError_t launch_scan_count_1(const ScanArgs& a, int grid, size_t smem,
         scan_count_kernel<16, 2, MASK><<<grid, 17 * 32, smem, st>>>(a);
     else if (warps == 8 && group == 4)
         scan_count_kernel<8, 4, MASK><<<grid, 9 * 32, smem, st>>>(a);
+    else if (warps == 15 && group == 2)
+        scan_count_kernel<15, 2, MASK><<<grid, 16 * 32, smem, st>>>(a);
+    else if (warps == 15 && group == 3)
+        scan_count_kernel<15, 3, MASK><<<grid, 16 * 32, smem, st>>>(a);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();

@@ -9,11 +9,11 @@ namespace sel {
 
 constexpr int kMaxTables = 8;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any device wait
-// Count-scan variants: consumer warps (8 or 16, plus one producer warp) and
-// chunks evaluated per instruction pass (1 or 2).
-constexpr int kScanDefaultWarps = 16;
+// Count-scan variants: consumer warps (8, 15 or 16, plus one producer warp)
+// and chunks evaluated per instruction pass (1, 2, 3 or 4; scan_variant_ok).
+constexpr int kScanDefaultWarps = 15;
 constexpr int kMaxTileRows = 16384;
-constexpr int kScanDefaultGroup = 2;
+constexpr int kScanDefaultGroup = 3;
 
 // One table of a scan launch: its referenced columns ("slots"), its tiles in
 // the launch's global tile sequence and the programs evaluated on it.
@@ -60,7 +60,7 @@ cudaError_t scan_kernel_max_smem(int optin, int* dyn_max);
 // Batched count over the column-bucket form of the probes (bucket.h): a.blob
 // is the bucket blob (staged in shared memory), a.n_progs its counter count.
 // gb_bytes_per_warp: shared bytes of one warp's bucket-index buffer.  Variants:
-// 8 or 16 consumer warps, 1 or 2 chunks per pass.
+// 8, 11, 15 or 16 consumer warps, 1 or 2 chunks per pass (bucket_variant_ok).
 size_t bucket_layout(ScanArgs& a, int warps, uint32_t gb_bytes_per_warp);
 bool bucket_variant_ok(int warps, int group);
 cudaError_t launch_bucket_count(const ScanArgs& a, int grid, size_t smem, cudaStream_t st, int warps, int group);

@@ -45,7 +45,7 @@ def test_scan_shapes_config2(ctx, medium, shape):
         assert ctx.count(p, T) == oracle.count(ot, tree, threads=8)
 
 
-VARIANTS = [(8, 1), (8, 2), (16, 1), (16, 2), (8, 4)]
+VARIANTS = [(8, 1), (8, 2), (16, 1), (16, 2), (8, 4), (15, 2), (15, 3)]
 
 
 @pytest.mark.parametrize("variant", VARIANTS)

@@ -247,7 +247,7 @@ def test_bad_method_is_rejected(ctx):
             ctx.set_pushdown_method(m)
 
 
-@pytest.mark.parametrize("variant", [(16, 2), (16, 1), (8, 2), (8, 1), (8, 4)])
+@pytest.mark.parametrize("variant", [(16, 2), (16, 1), (8, 2), (8, 1), (8, 4), (15, 2), (15, 3)])
 def test_two_pass_count_variants(ctx, dev, medium, variant):
     """The two-pass method's first pass is the count scan: every variant of it
     leaves the same masks and counts."""
