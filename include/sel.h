@@ -464,8 +464,15 @@ void sel_mlp_free(sel_mlp* m);
 sel_status sel_mlp_featurize(sel_ctx* ctx, sel_mlp* m, const sel_pred* const* preds, int32_t n, void* dev_features,
                              uint8_t* dev_ok);
 /* a7: dev_out (device FP32, n x 2) = (mu, raw log-variance) per feature row.
- * dev_features 16-byte aligned.  Enqueued on the context's stream. */
+ * dev_features 16-byte aligned.  Enqueued on the context's stream.  One
+ * kernel runs the three hidden layers and the head for 128 rows per CTA
+ * (activations in shared memory, accumulators in TMEM). */
 sel_status sel_mlp_forward(sel_ctx* ctx, sel_mlp* m, const void* dev_features, int32_t n, float* dev_out);
+/* Debug: on = 0 makes the model's inference (sel_mlp_forward,
+ * sel_mlp_estimate) run layer by layer like the training pass (three GEMM
+ * launches and a head kernel, activations through global memory) instead of
+ * the fused kernel; 1 restores the default.  Both give the same bits. */
+sel_status sel_debug_mlp_fused(sel_mlp* m, int32_t on);
 /* a8: one minibatch (n rows, a multiple of 8) of features and targets
  * y = ln(1 + count) (device FP32): gradients of the mean Gaussian NLL, then
  * an Adam step when cfg->apply_update.  *loss_out = the batch's mean loss.

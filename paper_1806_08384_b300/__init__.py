@@ -130,6 +130,7 @@ def _load():
         "sel_mlp_free": (None, [V]),
         "sel_mlp_featurize": (C.c_int, [V, V, P(V), C.c_int32, V, V]),
         "sel_mlp_forward": (C.c_int, [V, V, V, C.c_int32, V]),
+        "sel_debug_mlp_fused": (C.c_int, [V, C.c_int32]),
         "sel_mlp_train_step": (C.c_int, [V, V, V, V, C.c_int32, P(TrainCfg), P(C.c_float)]),
         "sel_mlp_train": (C.c_int, [V, V, P(V), P(C.c_uint64), C.c_int64, P(TrainCfg), P(C.c_float)]),
         "sel_mlp_estimate": (C.c_int, [V, V, P(V), P(sel_table), C.c_int32, C.c_float, P(C.c_double),
@@ -586,6 +587,10 @@ class Estimator:
         _check(lib.sel_mlp_forward(self.ctx.h, self.h, C.c_void_p(feat.data_ptr()), feat.shape[0],
                                    C.c_void_p(out.data_ptr())), "sel_mlp_forward")
         return out
+
+    def set_fused(self, on: bool):
+        """sel_debug_mlp_fused: inference in one kernel (default) or layer by layer."""
+        _check(lib.sel_debug_mlp_fused(self.h, 1 if on else 0), "sel_debug_mlp_fused")
 
     def train_step(self, feat: torch.Tensor, y: torch.Tensor, cfg: TrainCfg) -> float:
         loss = C.c_float()

@@ -182,6 +182,189 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(const __grid_constant__ Ge
     if (warp == 0) tc_dealloc(tmem, 256);
 }
 
+// ---------------------------------------------------------------------------
+// The estimator's inference pass fused into one kernel (a7).  One CTA of 4
+// warps owns 128 rows.  Their activations stay in one 64 KiB shared buffer H
+// (4 K blocks of 128 rows x 64 bf16 in the swizzled layout the MMA reads),
+// which is the A operand of every layer: the features are copied into it
+// first (144 columns, zero-filled to 192), and each layer's epilogue writes
+// relu(acc + b) back over it once that layer's MMAs have completed.  The
+// weights stream through two 32 KiB stages, one 64-column K block of all 256
+// rows at a time, the next block loading while the tensor core multiplies
+// the current one.  The accumulator (128 x 256 FP32) lives in TMEM; thread t
+// reads row t's columns back.  After the third layer each thread finishes
+// its row's two outputs with the 256 -> 2 head in FP32, in the same order
+// and roundings as the layer-by-layer path.
+namespace {
+
+constexpr int kMlpIn = 144, kMlpHid = 256;
+constexpr uint32_t kHBlock = BM * BK * 2;           // 16 KiB: one K block of H
+constexpr uint32_t kHBytes = 4 * kHBlock;           // 64 KiB
+constexpr uint32_t kWStage = kMlpHid * BK * 2;      // 32 KiB: one K block of a weight matrix
+
+__device__ __forceinline__ void mlp_load_x(const MlpFwdArgs& a, uint32_t H, int m0, uint32_t tid) {
+    for (uint32_t kb = 0; kb < 3; ++kb)
+        for (uint32_t i = tid; i < BM * 8; i += 128) {
+            const uint32_t r = i >> 3, c = i & 7u;
+            const int row = m0 + (int)r, col = (int)(kb * BK + c * 8);
+            const bool ok = row < a.n && col < kMlpIn;
+            const __nv_bfloat16* src = ok ? a.x + (size_t)row * kMlpIn + col : a.x;
+            cp_async16(H + kb * kHBlock + sw128_offset(r, c), src, ok ? 16u : 0u);
+        }
+}
+
+// K block k0 .. k0 + 63 of W (256 rows, row stride and width K) into a stage; commits.
+__device__ __forceinline__ void mlp_load_w(const __nv_bfloat16* W, int K, uint32_t dst, int k0, uint32_t tid) {
+    for (uint32_t i = tid; i < kMlpHid * 8; i += 128) {
+        const uint32_t r = i >> 3, c = i & 7u;
+        const int col = k0 + (int)c * 8;
+        const bool ok = col < K;
+        const __nv_bfloat16* src = ok ? W + (size_t)r * K + col : W;
+        cp_async16(dst + sw128_offset(r, c), src, ok ? 16u : 0u);
+    }
+    cp_async_commit();
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) mlp_forward_kernel(const __grid_constant__ MlpFwdArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ uint64_t mma_done[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t s_fail;
+    __shared__ float s_b[3][kMlpHid];
+    __shared__ float s_w4[2][kMlpHid];
+    const uint32_t tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    uint8_t* const hgen = smem_raw + (base - smem_u32(smem_raw));   // H through a generic pointer
+    const uint32_t H = base, S0 = base + kHBytes;                    // stage s at S0 + s * kWStage
+    const int m0 = blockIdx.x * BM;
+
+    if (warp == 0) tc_alloc(&tmem_base, 256);
+    if (tid == 0) {
+        mbar_init(&mma_done[0], 1);
+        mbar_init(&mma_done[1], 1);
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    for (uint32_t k = tid; k < (uint32_t)kMlpHid; k += 128) {
+        s_b[0][k] = a.b[0][k];
+        s_b[1][k] = a.b[1][k];
+        s_b[2][k] = a.b[2][k];
+        s_w4[0][k] = __bfloat162float(a.w4[k]);
+        s_w4[1][k] = __bfloat162float(a.w4[kMlpHid + k]);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = idesc_bf16(BM, kMlpHid);
+
+    mlp_load_x(a, H, m0, tid);                    // joins the commit group of W1's first K block
+    mlp_load_w(a.w[0], kMlpIn, S0, 0, tid);
+    uint32_t it = 0;   // K blocks multiplied so far: block `it` uses stage it & 1 and commits phase (it >> 1) & 1
+    float o0 = 0.f, o1 = 0.f;
+    for (int L = 0; L < 3; ++L) {
+        const int K = L == 0 ? kMlpIn : kMlpHid;
+        const int nkb = L == 0 ? 3 : 4;
+        const __nv_bfloat16* W = a.w[L];
+        // the first K block's stage was last read two blocks ago, before the last layer's epilogue
+        if (L > 0) mlp_load_w(W, K, S0 + (it & 1u) * kWStage, 0, tid);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const uint32_t i = it + (uint32_t)kb, s = i & 1u;
+            if (kb + 1 < nkb) {
+                if (kb >= 1) {   // the other stage was read by block i - 1 of this layer
+                    const bool ok = mbar_wait_bounded(&mma_done[s ^ 1u], ((i - 1u) >> 1) & 1u);
+                    if (!ok) atomicOr(&s_fail, 1u);
+                }
+                mlp_load_w(W, K, S0 + (s ^ 1u) * kWStage, (kb + 1) * BK, tid);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            fence_proxy_async();   // the copied tiles (and H) visible to the tensor core
+            __syncthreads();
+            if (s_fail) break;
+            if (tid == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    tc_mma(tmem, sw128_desc(H + (uint32_t)kb * kHBlock + 32u * kk),
+                           sw128_desc(S0 + s * kWStage + 32u * kk), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                tc_commit(&mma_done[s]);
+            }
+        }
+        if (s_fail) break;
+        const uint32_t last = it + (uint32_t)nkb - 1u;
+        if (!mbar_wait_bounded(&mma_done[last & 1u], (last >> 1) & 1u)) atomicOr(&s_fail, 1u);
+        it += (uint32_t)nkb;
+        __syncthreads();
+        if (s_fail) break;
+        tc_fence_after();
+        // epilogue: row tid of the tile, 32 columns at a time
+#pragma unroll 1
+        for (int cc = 0; cc < kMlpHid / 32; ++cc) {
+            float f[32];
+            tc_ld32(tmem + ((warp * 32u) << 16) + (uint32_t)cc * 32u, f);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) f[j] = fmaxf(f[j] + s_b[L][cc * 32 + j], 0.f);
+            if (L < 2) {   // the next layer's input, over this layer's (all its MMAs have completed)
+                uint8_t* hb = hgen + (uint32_t)(cc >> 1) * kHBlock;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[8 * q + 2 * e], f[8 * q + 2 * e + 1]);
+                        w[e] = *reinterpret_cast<const uint32_t*>(&h2);
+                    }
+                    *reinterpret_cast<uint4*>(hb + sw128_offset(tid, (uint32_t)((cc & 1) * 4 + q))) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            } else {       // the head, on the BF16-rounded activations
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float h = __bfloat162float(__float2bfloat16_rn(f[j]));
+                    o0 = fmaf(h, s_w4[0][cc * 32 + j], o0);
+                    o1 = fmaf(h, s_w4[1][cc * 32 + j], o1);
+                }
+            }
+        }
+        tc_fence_before();
+        fence_proxy_async();   // H's new contents visible to the next layer's MMAs
+        __syncthreads();
+        tc_fence_after();
+    }
+    cp_async_wait<0>();   // nothing of ours lands after the exit (a failed wait can leave copies in flight)
+    if (s_fail) {
+        if (tid == 0) atomicOr(a.err, 1u);
+    } else {
+        const int row = m0 + (int)tid;
+        if (row < a.n) {
+            a.out[2 * (size_t)row] = o0 + a.b4[0];
+            a.out[2 * (size_t)row + 1] = o1 + a.b4[1];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tmem, 256);
+}
+
+size_t mlp_forward_smem_bytes() { return (size_t)kHBytes + 2 * (size_t)kWStage + 1024; }
+
+cudaError_t launch_mlp_forward(const MlpFwdArgs& a, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(mlp_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)mlp_forward_smem_bytes());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    if (a.n <= 0) return cudaSuccess;
+    mlp_forward_kernel<<<(a.n + BM - 1) / BM, 128, mlp_forward_smem_bytes(), st>>>(a);
+    return cudaGetLastError();
+}
+
 size_t gemm_smem_bytes() { return 2 * (size_t)kStage + 1024; }
 
 cudaError_t launch_gemm(const GemmArgs& g, int k_splits, cudaStream_t st) {

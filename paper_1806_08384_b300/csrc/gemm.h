@@ -34,4 +34,21 @@ struct GemmArgs {
 size_t gemm_smem_bytes();
 cudaError_t launch_gemm(const GemmArgs& g, int k_splits, cudaStream_t st);
 
+// The estimator's whole inference pass in one kernel: per 128-row tile,
+// h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2), h3 = relu(h2 W3^T + b3)
+// (BF16 activations, FP32 accumulation in TMEM; the activations never leave
+// shared memory) and out = h3 W4^T + b4 on the CUDA cores.
+struct MlpFwdArgs {
+    const __nv_bfloat16* x;      // n x 144, rows contiguous, 16-byte aligned
+    const __nv_bfloat16* w[3];   // W1 256 x 144, W2 and W3 256 x 256 (K contiguous)
+    const float* b[3];           // b1, b2, b3: 256 each
+    const __nv_bfloat16* w4;     // 2 x 256
+    const float* b4;             // 2
+    float* out;                  // n x 2: (mu, raw log-variance)
+    int n;
+    unsigned int* err;           // set when a bounded wait gave up
+};
+size_t mlp_forward_smem_bytes();
+cudaError_t launch_mlp_forward(const MlpFwdArgs& a, cudaStream_t st);
+
 }  // namespace sel

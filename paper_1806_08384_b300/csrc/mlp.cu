@@ -349,6 +349,7 @@ struct sel_mlp {
     __nv_bfloat16 *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *a1t = nullptr, *a2t = nullptr, *xt = nullptr;
     __nv_bfloat16 *dz1 = nullptr, *dz2 = nullptr, *dz3 = nullptr, *dz1t = nullptr, *dz2t = nullptr, *dz3t = nullptr;
     float* out = nullptr;
+    bool fused = true;   // inference in one kernel (gemm.cu); false: layer by layer as in training
     std::vector<void*> owned;
     // featurize staging: pinned host block -> device block, reused across calls;
     // stage_done marks the end of the last copy out of the host block
@@ -440,8 +441,27 @@ sel_status run_gemm(const GemmArgs& g, int splits, cudaStream_t st) {
 }
 
 // a7: activations a1..a3 (and a1t, a2t when training) and out for n rows of features x.
+// Inference (the default) runs as one kernel that keeps the activations in
+// shared memory and writes only out.
 sel_status forward(sel_mlp* m, const __nv_bfloat16* x, int n, bool training, cudaStream_t st) {
     MLP_TRY(ensure_batch(m, n));
+    if (!training && m->fused) {
+        MlpFwdArgs f{};
+        f.x = x;
+        f.w[0] = m->w1b;
+        f.w[1] = m->w2b;
+        f.w[2] = m->w3b;
+        f.b[0] = m->p + oB1;
+        f.b[1] = m->p + oB2;
+        f.b[2] = m->p + oB3;
+        f.w4 = m->w4b;
+        f.b4 = m->p + oB4;
+        f.out = m->out;
+        f.n = n;
+        f.err = m->err;
+        ++thread_launches();
+        return cuda_ok(launch_mlp_forward(f, st), "fused estimator forward launch");
+    }
     GemmArgs g = gemm(x, kFeat, m->w1b, kFeat, n, kHid, kFeat, EPI_BIAS_RELU, m->err);
     g.bias = m->p + oB1;
     g.out = m->a1;
@@ -823,6 +843,15 @@ extern "C" sel_status sel_mlp_forward(sel_ctx* ctx, sel_mlp* m, const void* dev_
     cudaStream_t st = ctx_stream(ctx);
     MLP_TRY(forward(m, static_cast<const __nv_bfloat16*>(dev_features), n, false, st));
     return cuda_ok(cudaMemcpyAsync(dev_out, m->out, (size_t)n * 8, cudaMemcpyDeviceToDevice, st), "sel_mlp_forward");
+}
+
+extern "C" sel_status sel_debug_mlp_fused(sel_mlp* m, int32_t on) {
+    if (!m || (on != 0 && on != 1)) {
+        set_error("sel_debug_mlp_fused: bad arguments");
+        return SEL_ERR_INVALID_ARG;
+    }
+    m->fused = on == 1;
+    return SEL_OK;
 }
 
 static sel_status check_cfg(const sel_train_cfg* cfg) {

@@ -80,6 +80,35 @@ def test_forward_matches_oracle(setup):
     assert np.all(np.abs(out - ref) <= 2e-2 * (1 + np.abs(ref))), float(np.abs(out - ref).max())
 
 
+def test_fused_forward_equals_layer_by_layer(setup):
+    """The one-kernel inference pass and the layer-by-layer pass of training
+    (three GEMM launches, activations through global memory, the head kernel)
+    round and sum alike: the same bits, on a ragged batch of several
+    128-row tiles and on a batch of one row; both within the oracle's
+    tolerance."""
+    est = setup[3]
+    P = om.init_params(9)
+    rng = np.random.default_rng(3)
+    for k in ("b1", "b2", "b3", "b4"):
+        P[k] = (rng.standard_normal(P[k].shape) * 0.05).astype(np.float32)
+    est.set_params(sel.flatten(P))
+    feat, X = _features(setup, 611)
+    try:
+        for rows in (611, 1):
+            f = feat[:rows].contiguous()
+            est.set_fused(True)
+            fused = est.forward(f)
+            est.set_fused(False)
+            layered = est.forward(f)
+            torch.cuda.synchronize()
+            assert torch.equal(fused, layered), float((fused - layered).abs().max())
+            ref = om.forward(P, X[:rows])["out"]
+            out = fused.cpu().numpy()
+            assert np.all(np.abs(out - ref) <= 2e-2 * (1 + np.abs(ref))), float(np.abs(out - ref).max())
+    finally:
+        est.set_fused(True)
+
+
 def test_gradients_and_adam_match_oracle(setup):
     est = setup[3]
     P = om.init_params(11)
@@ -232,9 +261,10 @@ def test_repeated_featurize_reuses_the_staged_records(setup):
 
 def test_launch_count_includes_the_estimator(setup):
     """sel_ctx_launch_count counts every kernel the context launches, the
-    estimator's included: featurize is one kernel, the forward pass three
-    GEMMs and the head, and a training step a whole number of launches that is
-    the same every time; a training run made of steps counts each step once."""
+    estimator's included: featurize is one kernel, the forward pass one fused
+    kernel (three GEMMs and the head layer by layer), and a training step a
+    whole number of launches that is the same every time; a training run made
+    of steps counts each step once."""
     t, T, ctx, est, cdfs, dicts, trees = setup
     preds = [sel.Predicate(T, tr) for tr in trees[:64]]
     l0 = ctx.launches
@@ -242,7 +272,14 @@ def test_launch_count_includes_the_estimator(setup):
     assert ctx.launches - l0 == 1
     l1 = ctx.launches
     est.forward(feat)
-    assert ctx.launches - l1 == 4
+    assert ctx.launches - l1 == 1
+    est.set_fused(False)
+    try:
+        l1 = ctx.launches
+        est.forward(feat)
+        assert ctx.launches - l1 == 4
+    finally:
+        est.set_fused(True)
     y = torch.zeros(64, dtype=torch.float32, device=feat.device)
     cfg = sel.train_cfg(batch=64, lr=0.0, apply_update=0)
     l2 = ctx.launches
