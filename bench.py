@@ -957,10 +957,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the config 1/2/3 and extra config 5 measurements")
     ap.add_argument("--estimator-curve", action="store_true",
                     help="config 4's learning curve (20k / 200k / 2M labelled pairs); prints its own JSON")
-    ap.add_argument("--kernel-case", choices=["batch-cfg5", "batch-cfg2", "pushdown-cfg5"],
+    ap.add_argument("--kernel-case", choices=["batch-cfg5", "batch-cfg2", "pushdown-cfg5", "mlp-forward"],
                     help="run one kernel case twice (for an ncu capture) and exit: the batched count of config 5's "
                          "256 probes or of config 2's 5 probes, or the push-down of the config 5 probe nearest "
-                         "selectivity --case-s, over a --rows-row table")
+                         "selectivity --case-s, over a --rows-row table; or the estimator's inference pass over "
+                         "4096 random OR-of-AND probes of a 1M-row config 2 table")
     ap.add_argument("--case-s", type=float, default=1e-3)
     ap.add_argument("--clock-interval-ms", type=float, default=50.0, help="NVML clock sampling interval")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -1115,6 +1116,19 @@ def main():
 
 def kernel_case(sel, dev, args):
     """One kernel case launched twice (the profiles' captures take the second)."""
+    if args.kernel_case == "mlp-forward":
+        t = dg.gen_table("cfg2", dg.config2_specs(), 1_000_000, dev)
+        T = sel.Table(t.columns)
+        ctx = sel.Context()
+        est = sel.Estimator(ctx, T, sample_rows=4096, seed=dg.MASTER_SEED)
+        rng = np.random.default_rng(5)
+        preds = [sel.Predicate(T, dg.random_dnf_predicate(dg.config2_specs(), rng)) for _ in range(4096)]
+        feat, _ = est.featurize(preds)
+        for _ in range(2):
+            out = est.forward(feat)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.kernel_case, "probes": len(preds), "out": out[:2].tolist()}))
+        return
     if args.kernel_case == "batch-cfg2":
         t = dg.gen_table("cfg2", dg.config2_specs(), args.rows, dev)
         trees = [dg.config2_predicate(s) for s in dg.CONFIG2_TARGETS]
